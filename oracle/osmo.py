@@ -1,0 +1,57 @@
+"""Optimiser and loss readings, in plain numpy (test infrastructure only).
+
+Sec. 2.7 runs the object-space model optimisation (OSMO) of Rackson et al. with the
+Radon transform and its inverse replaced by the ray-traced operators, and stops when the
+absolute relative error between target and simulated dose falls below 0.5 %.  OSMO's
+own equations are in that reference, not in the paper, so this file follows a stated
+reading (parity unpinned beyond its properties):
+
+  m^0 = f_T
+  g^k = max(0, P m^k)                 P: projection (the adjoint operator)
+  d^k = A g^k                         A: dose operator
+  dn^k = d^k / max(d^k)               max over the grid
+  E^k = sum |dn^k - f_T| / sum f_T    "absolute relative error"
+  m^{k+1} = max(0, m^k + (f_T - dn^k))
+  stop after the update once E^k < tol, or after n_iter iterations.
+
+The thresholded dose loss (differentiable path; not in the paper):
+  L(D) = mean_{v in P} relu(d_h - D_v)^2 + mean_{v in Q} relu(D_v - d_l)^2
+with P = {f_T = 1}, Q = {f_T = 0}, and its gradient dL/dD.
+"""
+import numpy as np
+
+
+def osmo(target, project, dose, n_iter, tol=0.005):
+    """Returns (g, dn, m, errors) after the iterations; project/dose are FP64 callables."""
+    f = np.asarray(target, dtype=np.float64)
+    fsum = f.sum()
+    m = f.copy()
+    errors = []
+    g = dn = None
+    for _ in range(n_iter):
+        g = np.maximum(0.0, project(m))
+        d = dose(g)
+        dmax = d.max()
+        if not dmax > 0.0:
+            raise FloatingPointError("dose is zero everywhere")
+        dn = d / dmax
+        err = np.abs(dn - f).sum() / fsum
+        errors.append(err)
+        m = np.maximum(0.0, m + (f - dn))
+        if err < tol:
+            break
+    return g, dn, m, np.array(errors)
+
+
+def threshold_loss(dose, target, d_l, d_h):
+    """(L, dL/dD) of the thresholded dose loss in FP64."""
+    D = np.asarray(dose, dtype=np.float64)
+    f = np.asarray(target)
+    P = f > 0.5
+    Q = ~P
+    nP, nQ = max(int(P.sum()), 1), max(int(Q.sum()), 1)
+    under = np.where(P, np.maximum(d_h - D, 0.0), 0.0)
+    over = np.where(Q, np.maximum(D - d_l, 0.0), 0.0)
+    L = (under ** 2).sum() / nP + (over ** 2).sum() / nQ
+    grad = -2.0 * under / nP + 2.0 * over / nQ
+    return L, grad

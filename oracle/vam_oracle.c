@@ -1,0 +1,262 @@
+/*
+ * FP64 CPU oracle for the 3D ray-traced tomographic projection and dose operators of
+ * "Versatile volumetric additive manufacturing with 3D ray tracing" (Webber et al.).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call this file:
+ * only the tests, the package's smoke check and the benchmark's CPU-baseline leg do.
+ * It shares no code, header or constant with the CUDA library; both are written from
+ * the paper's description.
+ *
+ * What is computed, in the paper's order (every loop is plain and sequential):
+ *   Sec. 2.1  ray generation: for each pixel, rays leave points of the aperture stop
+ *             and converge on the pixel's image point in the best-focus plane; the
+ *             chief ray leaves the centre of the stop.  Vector Snell's law at each
+ *             cylinder surface (air/glass, glass/resin); tracing stops at the inner
+ *             wall on the far side of the vial.
+ *   Sec. 2.2  anti-aliasing: each sample on the ray interacts with the neighbouring
+ *             voxels with weight (1-dx)(1-dy)(1-dz) (trilinear weights).
+ *   Sec. 2.4  projection: pixel value = sum over its rays of the weighted voxel values
+ *             along the ray.  With the Beer-Lambert and Fresnel factors of Sec. 2.5 it
+ *             is the exact transpose (adjoint) of the dose operator below.
+ *   Sec. 2.5  dose: every sample adds pixel intensity x anti-aliasing weight x Fresnel
+ *             transmission (unpolarised) x Beer-Lambert transmission to its voxels.
+ *             Repeated for all rays of all pixels and all rotation angles.
+ * Readings where the paper is silent: samples are midpoints s_j = (j+1/2) ell/K with
+ * K = ceil(ell/ds) (the per-ray step makes the sample sum of a unit field equal to the
+ * chord length); voxel centres sit at (i-(N-1)/2) h; corners outside the grid count
+ * as zero; Fresnel losses at both the outer and inner surfaces; the vial rotates by
+ * theta_k about z, applied to the traced path as x' = R(theta_k) x.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double h;               /* voxel pitch, mm */
+    int32_t nu, nv;
+    double pu, pv;          /* pixel pitch in the best-focus plane y = 0, mm */
+    double pupil;           /* distance of the aperture stop from the axis; INFINITY = telecentric */
+    double fnum;            /* f-number: stop diameter = pupil / fnum; INFINITY = chief ray only */
+    int32_t m;              /* rays per pixel */
+    const double *pupil_xy; /* m points (xi, eta) in the unit disk */
+    double r_in, wall;      /* vial inner radius and wall thickness, mm */
+    double n_out, n_glass, n_resin;
+    double mu;              /* absorption coefficient, 1/mm */
+    int32_t n_angles;
+    const double *angles;   /* radians */
+    double step_vox;        /* nominal sample spacing in voxels */
+} orc_geom;
+
+typedef struct {
+    int32_t status;         /* 2 reaches the resin, 1 only crosses the wall, 0 misses, -1 total internal reflection */
+    int32_t k;              /* samples on the in-resin segment */
+    double origin[3], d0[3];/* ray leaving the projector */
+    double p1[3], d1[3];    /* outer-surface hit, direction in the glass */
+    double e[3], d2[3];     /* resin entry point, direction in the resin */
+    double exit[3];         /* far-side inner-wall point */
+    double ell;             /* in-resin length, mm */
+    double t1, t2;          /* Fresnel transmissions at the outer and inner surface */
+} orc_ray;
+
+/* Intersections of the line o + t d with the infinite cylinder x^2 + y^2 = r^2.
+ * Returns 0 when the line misses it (or runs parallel to the axis). */
+static int cylinder_roots(const double o[3], const double d[3], double r, double *t_near, double *t_far)
+{
+    double a = d[0] * d[0] + d[1] * d[1];
+    double b = 2.0 * (o[0] * d[0] + o[1] * d[1]);
+    double c = o[0] * o[0] + o[1] * o[1] - r * r;
+    if (a <= 0.0) return 0;
+    double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) return 0;
+    double q = -0.5 * (b + (b >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+    if (q == 0.0) return 0;
+    double r1 = q / a, r2 = c / q;
+    *t_near = r1 < r2 ? r1 : r2;
+    *t_far = r1 < r2 ? r2 : r1;
+    return 1;
+}
+
+/* Vector form of Snell's law at a cylinder surface point p (radius r) for unit
+ * direction d going from index n1 to n2.  Writes the refracted direction and the
+ * unpolarised Fresnel transmission.  Returns 0 on total internal reflection. */
+static int refract(const double p[3], double r, const double d[3], double n1, double n2,
+                   double out[3], double *trans)
+{
+    double n[3] = {p[0] / r, p[1] / r, 0.0};
+    double cn = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+    if (cn > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; cn = -cn; }
+    double c1 = -cn;                         /* cosine of the incidence angle */
+    double eta = n1 / n2;
+    double k = 1.0 - eta * eta * (1.0 - c1 * c1);
+    if (k < 0.0) return 0;
+    double c2 = sqrt(k);                     /* cosine of the refraction angle */
+    for (int i = 0; i < 3; ++i) out[i] = eta * d[i] + (eta * c1 - c2) * n[i];
+    double rs = (n1 * c1 - n2 * c2) / (n1 * c1 + n2 * c2);
+    double rp = (n1 * c2 - n2 * c1) / (n1 * c2 + n2 * c1);
+    *trans = 1.0 - 0.5 * (rs * rs + rp * rp);
+    return 1;
+}
+
+/* Trace one ray (pixel u, v, aperture sample a) in the vial frame at theta = 0. */
+int orc_trace(const orc_geom *g, int32_t u, int32_t v, int32_t a, orc_ray *ray)
+{
+    memset(ray, 0, sizeof(*ray));
+    double r_out = g->r_in + g->wall;
+    double qx = (u - 0.5 * (g->nu - 1)) * g->pu;   /* image point Q = (qx, 0, qz) */
+    double qz = (v - 0.5 * (g->nv - 1)) * g->pv;
+    double xi = g->pupil_xy[2 * a], eta = g->pupil_xy[2 * a + 1];
+    double *o = ray->origin, *d = ray->d0;
+    if (isinf(g->pupil)) {
+        /* telecentric: every ray crosses Q; the cone half-angle is atan(1/(2N)) */
+        double ta = isinf(g->fnum) ? 0.0 : 1.0 / (2.0 * g->fnum);
+        double dx = -xi * ta, dy = 1.0, dz = -eta * ta;
+        double nrm = sqrt(dx * dx + dy * dy + dz * dz);
+        d[0] = dx / nrm; d[1] = dy / nrm; d[2] = dz / nrm;
+        double back = (r_out + 1.0) / d[1];
+        o[0] = qx - back * d[0]; o[1] = -back * d[1]; o[2] = qz - back * d[2];
+    } else {
+        /* aperture stop at y = -L, diameter D = L / N, centred on the optical axis */
+        double L = g->pupil;
+        double D = isinf(g->fnum) ? 0.0 : L / g->fnum;
+        o[0] = 0.5 * D * xi; o[1] = -L; o[2] = 0.5 * D * eta;
+        double dx = qx - o[0], dy = 0.0 - o[1], dz = qz - o[2];
+        double nrm = sqrt(dx * dx + dy * dy + dz * dz);
+        d[0] = dx / nrm; d[1] = dy / nrm; d[2] = dz / nrm;
+    }
+    /* air -> glass at the outer surface */
+    double tn, tf;
+    if (!cylinder_roots(o, d, r_out, &tn, &tf) || tn <= 0.0) { ray->status = 0; return 0; }
+    for (int i = 0; i < 3; ++i) ray->p1[i] = o[i] + tn * d[i];
+    if (!refract(ray->p1, r_out, d, g->n_out, g->n_glass, ray->d1, &ray->t1)) { ray->status = -1; return -1; }
+    /* glass -> resin at the inner surface */
+    if (!cylinder_roots(ray->p1, ray->d1, g->r_in, &tn, &tf) || tn <= 0.0) { ray->status = 1; return 1; }
+    for (int i = 0; i < 3; ++i) ray->e[i] = ray->p1[i] + tn * ray->d1[i];
+    if (!refract(ray->e, g->r_in, ray->d1, g->n_glass, g->n_resin, ray->d2, &ray->t2)) { ray->status = -1; return -1; }
+    /* far-side inner wall: the chord from a point on the circle along d2 */
+    const double *e = ray->e, *d2 = ray->d2;
+    double ell = -2.0 * (e[0] * d2[0] + e[1] * d2[1]) / (d2[0] * d2[0] + d2[1] * d2[1]);
+    if (!(ell > 0.0)) { ray->status = 1; return 1; }
+    ray->ell = ell;
+    for (int i = 0; i < 3; ++i) ray->exit[i] = e[i] + ell * d2[i];
+    double ds = g->step_vox * g->h;
+    int32_t k = (int32_t)ceil(ell / ds - 1e-9);
+    ray->k = k < 1 ? 1 : k;
+    ray->status = 2;
+    return 2;
+}
+
+/* Trilinear corners (Sec. 2.2) of a point given in index coordinates. */
+typedef struct { int64_t idx[8]; double w[8]; int n; } corners8;
+
+static void trilinear(const orc_geom *g, const double q[3], corners8 *c)
+{
+    double f[3]; int64_t i0[3];
+    for (int ax = 0; ax < 3; ++ax) { double fl = floor(q[ax]); i0[ax] = (int64_t)fl; f[ax] = q[ax] - fl; }
+    int64_t n[3] = {g->nx, g->ny, g->nz};
+    c->n = 0;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                int64_t ix = i0[0] + cx, iy = i0[1] + cy, iz = i0[2] + cz;
+                if (ix < 0 || iy < 0 || iz < 0 || ix >= n[0] || iy >= n[1] || iz >= n[2]) continue;
+                double w = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) * (cz ? f[2] : 1.0 - f[2]);
+                c->idx[c->n] = (iz * n[1] + iy) * n[0] + ix;
+                c->w[c->n] = w;
+                c->n++;
+            }
+}
+
+/* Position of sample j of a traced ray after rotating the vial by theta, in index
+ * coordinates, and the sample's factor w_a T1 T2 exp(-mu s_j) delta. */
+static void sample(const orc_geom *g, const orc_ray *ray, int32_t j, double ct, double st,
+                   double q[3], double *factor)
+{
+    double delta = ray->ell / ray->k;
+    double s = (j + 0.5) * delta;
+    double x = ray->e[0] + s * ray->d2[0];
+    double y = ray->e[1] + s * ray->d2[1];
+    double z = ray->e[2] + s * ray->d2[2];
+    double xr = ct * x - st * y;
+    double yr = st * x + ct * y;
+    q[0] = xr / g->h + 0.5 * (g->nx - 1);
+    q[1] = yr / g->h + 0.5 * (g->ny - 1);
+    q[2] = z / g->h + 0.5 * (g->nz - 1);
+    *factor = (ray->t1 * ray->t2 / g->m) * exp(-g->mu * s) * delta;
+}
+
+/* One projection pixel: y[k][v][u] = sum_a sum_j factor_j sum_corners w_c V[c]. */
+double orc_adjoint_pixel(const orc_geom *g, const double *vol, int32_t k, int32_t v, int32_t u)
+{
+    double ct = cos(g->angles[k]), st = sin(g->angles[k]);
+    double acc = 0.0;
+    for (int32_t a = 0; a < g->m; ++a) {
+        orc_ray ray;
+        if (orc_trace(g, u, v, a, &ray) != 2) continue;
+        for (int32_t j = 0; j < ray.k; ++j) {
+            double q[3], fac;
+            sample(g, &ray, j, ct, st, q, &fac);
+            corners8 c;
+            trilinear(g, q, &c);
+            for (int i = 0; i < c.n; ++i) acc += fac * c.w[i] * vol[c.idx[i]];
+        }
+    }
+    return acc;
+}
+
+/* Projection operator (Sec. 2.4 with Sec. 2.5's factors): volume -> projections [k][v][u]. */
+void orc_adjoint(const orc_geom *g, const double *vol, double *proj)
+{
+    for (int32_t k = 0; k < g->n_angles; ++k)
+        for (int32_t v = 0; v < g->nv; ++v)
+            for (int32_t u = 0; u < g->nu; ++u)
+                proj[((int64_t)k * g->nv + v) * g->nu + u] = orc_adjoint_pixel(g, vol, k, v, u);
+}
+
+/* Dose operator (Sec. 2.5): projections [k][v][u] -> dose [z][y][x], overwriting dose. */
+void orc_forward(const orc_geom *g, const double *proj, double *dose)
+{
+    memset(dose, 0, sizeof(double) * (size_t)g->nx * g->ny * g->nz);
+    for (int32_t k = 0; k < g->n_angles; ++k) {
+        double ct = cos(g->angles[k]), st = sin(g->angles[k]);
+        for (int32_t v = 0; v < g->nv; ++v)
+            for (int32_t u = 0; u < g->nu; ++u) {
+                double intensity = proj[((int64_t)k * g->nv + v) * g->nu + u];
+                if (intensity == 0.0) continue;   /* adds exactly zero */
+                for (int32_t a = 0; a < g->m; ++a) {
+                    orc_ray ray;
+                    if (orc_trace(g, u, v, a, &ray) != 2) continue;
+                    for (int32_t j = 0; j < ray.k; ++j) {
+                        double q[3], fac;
+                        sample(g, &ray, j, ct, st, q, &fac);
+                        corners8 c;
+                        trilinear(g, q, &c);
+                        for (int i = 0; i < c.n; ++i) dose[c.idx[i]] += intensity * fac * c.w[i];
+                    }
+                }
+            }
+    }
+}
+
+/* Samples per pass whose trilinear footprint reaches the grid (-1 < q_z < nz); the
+ * rotation is about z, so the count is the same for every angle. */
+uint64_t orc_sample_count(const orc_geom *g)
+{
+    uint64_t per_angle = 0;
+    for (int32_t v = 0; v < g->nv; ++v)
+        for (int32_t u = 0; u < g->nu; ++u)
+            for (int32_t a = 0; a < g->m; ++a) {
+                orc_ray ray;
+                if (orc_trace(g, u, v, a, &ray) != 2) continue;
+                double delta = ray.ell / ray.k;
+                for (int32_t j = 0; j < ray.k; ++j) {
+                    double s = (j + 0.5) * delta;
+                    double qz = (ray.e[2] + s * ray.d2[2]) / g->h + 0.5 * (g->nz - 1);
+                    if (qz > -1.0 && qz < (double)g->nz) per_angle++;
+                }
+            }
+    return per_angle * (uint64_t)g->n_angles;
+}
+
+int32_t orc_sizeof_geom(void) { return (int32_t)sizeof(orc_geom); }
+int32_t orc_sizeof_ray(void) { return (int32_t)sizeof(orc_ray); }

@@ -1,0 +1,330 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle's callers.
+
+This module holds workload descriptions (printer, vial and grid parameters), binary
+target volumes, aperture-stop sample patterns and random fields.  It contains none of
+the ray-tracing or dose arithmetic: it only produces the numbers that both the CUDA
+path and the CPU oracle are fed with.
+
+The paper's own parts (a 3DBenchy, a 9-fin part, a lettered part) are not available;
+seeded constructive-solid-geometry targets of the same kind (solid bodies with thin
+features, placed inside the region the refracted rays reach from every angle) stand in
+for them.  Every generator is a pure function of its arguments and seed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+INF = float("inf")
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One printer + vial + grid configuration (units: mm, radians, 1/mm).
+
+    Grid: nx*ny*nz voxels of pitch ``voxel_mm``, centred on the vial axis (z).
+    Pixel array: nu*nv pixels of pitch pixel_u_mm x pixel_v_mm in the best-focus plane
+    y = 0, which contains the rotation axis (Sec. 2.8).  The aperture stop sits
+    ``pupil_mm`` in front of the axis on the -y side (INF = telecentric, Sec. 2.6);
+    its diameter is pupil_mm / f_number (telecentric: cone half-angle atan(1/(2N))).
+    """
+
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    voxel_mm: float
+    nu: int
+    nv: int
+    pixel_u_mm: float
+    pixel_v_mm: float
+    n_angles: int
+    pupil_mm: float
+    f_number: float
+    pupil_pattern: str  # chief | stratified4x4 | sunflower | hex13 | stratified<n>x<n>
+    rays_per_pixel: int
+    r_inner_mm: float
+    wall_mm: float
+    n_outside: float
+    n_glass: float
+    n_resin: float
+    mu_per_mm: float
+    step_vox: float = 0.5
+    target: str = "sphere_cube"
+    seed: int = 0
+    osmo_iters: int = 10
+
+    def scaled(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def proj_shape(self):
+        return (self.n_angles, self.nv, self.nu)
+
+
+# The five workloads of the benchmark spec, named by what they are.  Values the task leaves open
+# (c3 vial, c4 pitch/vial, pixel pitch = voxel pitch) follow the readings listed in the
+# design notes.
+WORKLOADS = {
+    "tiny_64cube_90ang_chief": Workload(
+        name="tiny_64cube_90ang_chief", nx=64, ny=64, nz=64, voxel_mm=0.2,
+        nu=64, nv=64, pixel_u_mm=0.2, pixel_v_mm=0.2, n_angles=90,
+        pupil_mm=150.0, f_number=INF, pupil_pattern="chief", rays_per_pixel=1,
+        r_inner_mm=6.0, wall_mm=1.0, n_outside=1.0, n_glass=1.47, n_resin=1.50,
+        mu_per_mm=0.05, target="sphere_cube", seed=0, osmo_iters=10),
+    "mid_256cube_360ang_16rays": Workload(
+        name="mid_256cube_360ang_16rays", nx=256, ny=256, nz=256, voxel_mm=0.1,
+        nu=256, nv=256, pixel_u_mm=0.1, pixel_v_mm=0.1, n_angles=360,
+        pupil_mm=120.0, f_number=4.0, pupil_pattern="stratified4x4", rays_per_pixel=16,
+        r_inner_mm=12.5, wall_mm=1.2, n_outside=1.0, n_glass=1.47, n_resin=1.50,
+        mu_per_mm=0.03, target="spheres_tori12", seed=0, osmo_iters=30),
+    "tall_384x384x512_720ang_8rays": Workload(
+        name="tall_384x384x512_720ang_8rays", nx=384, ny=384, nz=512, voxel_mm=0.08,
+        nu=384, nv=512, pixel_u_mm=0.08, pixel_v_mm=0.08, n_angles=720,
+        pupil_mm=80.0, f_number=4.0, pupil_pattern="sunflower", rays_per_pixel=8,
+        r_inner_mm=15.0, wall_mm=1.2, n_outside=1.0, n_glass=1.47, n_resin=1.50,
+        mu_per_mm=0.03, target="strut_lattice", seed=0, osmo_iters=30),
+    "warmstart_128cube_180ang_4rays": Workload(
+        name="warmstart_128cube_180ang_4rays", nx=128, ny=128, nz=128, voxel_mm=0.1,
+        nu=128, nv=128, pixel_u_mm=0.1, pixel_v_mm=0.1, n_angles=180,
+        pupil_mm=100.0, f_number=4.0, pupil_pattern="sunflower", rays_per_pixel=4,
+        r_inner_mm=6.0, wall_mm=1.0, n_outside=1.0, n_glass=1.47, n_resin=1.50,
+        mu_per_mm=0.05, target="csg", seed=0, osmo_iters=40),
+    "large_768x768x1024_1000ang_4rays": Workload(
+        name="large_768x768x1024_1000ang_4rays", nx=768, ny=768, nz=1024, voxel_mm=0.05,
+        nu=1024, nv=1024, pixel_u_mm=0.05, pixel_v_mm=0.05, n_angles=1000,
+        pupil_mm=100.0, f_number=2.8, pupil_pattern="sunflower", rays_per_pixel=4,
+        r_inner_mm=19.0, wall_mm=1.5, n_outside=1.0, n_glass=1.47, n_resin=1.50,
+        mu_per_mm=0.02, target="csg_shells", seed=0, osmo_iters=30),
+}
+
+TINY = WORKLOADS["tiny_64cube_90ang_chief"]
+MID = WORKLOADS["mid_256cube_360ang_16rays"]
+
+
+# ----------------------------------------------------------------------------------
+# aperture-stop sample patterns (points in the unit disk, one set shared by all pixels)
+# ----------------------------------------------------------------------------------
+def _concentric_disk(a: np.ndarray, b: np.ndarray):
+    """Shirley-Chiu concentric map of [-1,1]^2 onto the unit disk."""
+    x = np.zeros_like(a)
+    y = np.zeros_like(a)
+    for i in range(a.size):
+        p, q = a.flat[i], b.flat[i]
+        if p == 0.0 and q == 0.0:
+            r, phi = 0.0, 0.0
+        elif abs(p) > abs(q):
+            r, phi = p, (math.pi / 4.0) * (q / p)
+        else:
+            r, phi = q, (math.pi / 2.0) - (math.pi / 4.0) * (p / q)
+        x.flat[i] = r * math.cos(phi)
+        y.flat[i] = r * math.sin(phi)
+    return x, y
+
+
+def pupil_samples(pattern: str, m: int, seed: int = 0) -> np.ndarray:
+    """(m, 2) float64 array of aperture-stop positions (xi, eta) in the unit disk.
+
+    chief          : the single point (0, 0), a zero-etendue pixel.
+    stratified<n>x<n>: one jittered point per cell of an n x n grid on [-1,1]^2, mapped
+                     to the disk by the concentric map.
+    sunflower      : golden-angle spiral r = sqrt((a+1/2)/m), phase jittered by one
+                     seeded rotation.
+    hex13          : hexagonal filling (Sec. 2.1): centre, 6 points at r=1/2, 6 at
+                     r=sqrt(3)/2 (a hex lattice of spacing 1/2 clipped to the disk).
+    """
+    rng = np.random.default_rng(seed)
+    if pattern == "chief":
+        if m != 1:
+            raise ValueError("chief pattern has exactly one ray")
+        return np.zeros((1, 2))
+    if pattern.startswith("stratified"):
+        n = int(pattern[len("stratified"):].split("x")[0])
+        if n * n != m:
+            raise ValueError(f"{pattern} needs {n*n} rays, got {m}")
+        i, k = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        j = rng.random((2, n, n))
+        a = 2.0 * (i + j[0]) / n - 1.0
+        b = 2.0 * (k + j[1]) / n - 1.0
+        x, y = _concentric_disk(a.ravel(), b.ravel())
+        return np.stack([x, y], axis=1)
+    if pattern == "sunflower":
+        golden = math.pi * (3.0 - math.sqrt(5.0))
+        phase = 2.0 * math.pi * rng.random()
+        a = np.arange(m)
+        r = np.sqrt((a + 0.5) / m)
+        phi = a * golden + phase
+        return np.stack([r * np.cos(phi), r * np.sin(phi)], axis=1)
+    if pattern == "hex13":
+        if m != 13:
+            raise ValueError("hex13 has 13 rays")
+        pts = [(0.0, 0.0)]
+        for k in range(6):
+            t = k * math.pi / 3.0
+            pts.append((0.5 * math.cos(t), 0.5 * math.sin(t)))
+        for k in range(6):
+            t = math.pi / 6.0 + k * math.pi / 3.0
+            r = math.sqrt(3.0) / 2.0
+            pts.append((r * math.cos(t), r * math.sin(t)))
+        return np.array(pts)
+    raise ValueError(f"unknown pupil pattern {pattern!r}")
+
+
+def workload_pupil(w: Workload) -> np.ndarray:
+    return pupil_samples(w.pupil_pattern, w.rays_per_pixel, w.seed)
+
+
+def default_angles(n_angles: int) -> np.ndarray:
+    """theta_k = 2*pi*k/N (a full turn in equal steps, Sec. 2.5)."""
+    return 2.0 * np.pi * np.arange(n_angles, dtype=np.float64) / n_angles
+
+
+# ----------------------------------------------------------------------------------
+# binary targets (float32 {0,1}, layout [nz][ny][nx], voxel centres at (i-(N-1)/2)*h)
+# ----------------------------------------------------------------------------------
+def voxel_centres(w: Workload):
+    h = w.voxel_mm
+    x = (np.arange(w.nx) - (w.nx - 1) / 2.0) * h
+    y = (np.arange(w.ny) - (w.ny - 1) / 2.0) * h
+    z = (np.arange(w.nz) - (w.nz - 1) / 2.0) * h
+    return np.meshgrid(z, y, x, indexing="ij")  # Z, Y, X each [nz][ny][nx]
+
+
+def reach_radius(w: Workload, margin_mm: float = 0.3) -> float:
+    """Radius inside which every direction is available to some ray (target placement)."""
+    r_o = w.r_inner_mm + w.wall_mm
+    b_max = min(w.nu * w.pixel_u_mm / 2.0, r_o, w.n_glass * w.r_inner_mm / w.n_outside)
+    return b_max * w.n_outside / w.n_resin - margin_mm
+
+
+def _sphere(Z, Y, X, c, r):
+    return (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 <= r * r
+
+
+def _box(Z, Y, X, c, half):
+    return (np.abs(X - c[0]) <= half[0]) & (np.abs(Y - c[1]) <= half[1]) & (np.abs(Z - c[2]) <= half[2])
+
+
+def _torus(Z, Y, X, c, axis, R, r):
+    px, py, pz = X - c[0], Y - c[1], Z - c[2]
+    along = px * axis[0] + py * axis[1] + pz * axis[2]
+    radial2 = np.maximum(px * px + py * py + pz * pz - along * along, 0.0)
+    return (np.sqrt(radial2) - R) ** 2 + along * along <= r * r
+
+
+def _rand_axis(rng):
+    v = rng.normal(size=3)
+    return v / np.linalg.norm(v)
+
+
+def _rand_centre(rng, w: Workload, extent: float, reach: float):
+    """Centre such that a primitive of bounding radius `extent` stays in reach and grid."""
+    rmax = max(reach - extent, 0.0)
+    rad = rmax * math.sqrt(rng.random())
+    phi = 2.0 * math.pi * rng.random()
+    zmax = max(w.nz * w.voxel_mm / 2.0 - extent - 2.0 * w.voxel_mm, 0.0)
+    return (rad * math.cos(phi), rad * math.sin(phi), rng.uniform(-zmax, zmax))
+
+
+def make_target(w: Workload, kind: Optional[str] = None, seed: Optional[int] = None) -> np.ndarray:
+    kind = kind or w.target
+    seed = w.seed if seed is None else seed
+    rng = np.random.default_rng(seed + 1000)
+    Z, Y, X = voxel_centres(w)
+    reach = reach_radius(w)
+    if kind == "sphere_cube":
+        # sphere r = 4 mm centred (0,0,-1.5) united with a 3 mm cube centred (1,1,3.5)
+        m = _sphere(Z, Y, X, (0.0, 0.0, -1.5), 4.0) | _box(Z, Y, X, (1.0, 1.0, 3.5), (1.5, 1.5, 1.5))
+    elif kind == "spheres_tori12":
+        m = np.zeros(X.shape, dtype=bool)
+        for k in range(12):
+            if k % 2 == 0:
+                r = rng.uniform(1.0, 5.0)
+                c = _rand_centre(rng, w, r, reach)
+                m |= _sphere(Z, Y, X, c, r)
+            else:
+                R = rng.uniform(1.0, 5.0)
+                r = rng.uniform(0.35, 0.3 * R + 0.35)
+                c = _rand_centre(rng, w, R + r, reach)
+                m |= _torus(Z, Y, X, c, _rand_axis(rng), R, r)
+    elif kind == "strut_lattice":
+        cell, beam = 4.0, 0.5
+        off = rng.uniform(0.0, cell, size=3)
+        keep = 0.75
+        m = np.zeros(X.shape, dtype=bool)
+        # beams along x, y and z through the lattice points; each beam family keeps a
+        # seeded random subset of the lines
+        gx = np.mod(X - off[0] + cell / 2, cell) - cell / 2
+        gy = np.mod(Y - off[1] + cell / 2, cell) - cell / 2
+        gz = np.mod(Z - off[2] + cell / 2, cell) - cell / 2
+        ix = np.floor((X - off[0] + cell / 2) / cell).astype(np.int64)
+        iy = np.floor((Y - off[1] + cell / 2) / cell).astype(np.int64)
+        iz = np.floor((Z - off[2] + cell / 2) / cell).astype(np.int64)
+        salt = rng.integers(1, 2**31 - 1, size=3)
+
+        def keep_line(a, b, s):
+            hsh = (a * 73856093) ^ (b * 19349663) ^ s
+            return (hsh % 1000) < int(keep * 1000)
+
+        hb = beam / 2
+        m |= (np.abs(gy) <= hb) & (np.abs(gz) <= hb) & keep_line(iy, iz, salt[0])
+        m |= (np.abs(gx) <= hb) & (np.abs(gz) <= hb) & keep_line(ix, iz, salt[1])
+        m |= (np.abs(gx) <= hb) & (np.abs(gy) <= hb) & keep_line(ix, iy, salt[2])
+        m &= X * X + Y * Y <= min(10.0, reach) ** 2
+        zlim = w.nz * w.voxel_mm / 2.0 - 1.0
+        m &= np.abs(Z) <= zlim
+    elif kind in ("csg", "csg_shells"):
+        n_prim = 40 if kind == "csg_shells" else int(rng.integers(3, 7))
+        scale = min(reach, w.nz * w.voxel_mm / 2.0)
+        m = np.zeros(X.shape, dtype=bool)
+        for k in range(n_prim):
+            t = rng.integers(0, 3)
+            if t == 0:
+                r = rng.uniform(0.12, 0.35) * scale
+                c = _rand_centre(rng, w, r, reach)
+                p = _sphere(Z, Y, X, c, r)
+            elif t == 1:
+                half = rng.uniform(0.08, 0.3, size=3) * scale
+                c = _rand_centre(rng, w, float(np.linalg.norm(half)), reach)
+                p = _box(Z, Y, X, c, half)
+            else:
+                R = rng.uniform(0.15, 0.35) * scale
+                r = rng.uniform(0.25, 0.5) * R
+                c = _rand_centre(rng, w, R + r, reach)
+                p = _torus(Z, Y, X, c, _rand_axis(rng), R, r)
+            if kind == "csg_shells" and k % 4 == 3 and t == 0:
+                # thin-walled shell of 0.3 mm
+                inner = _sphere(Z, Y, X, c, max(r - 0.3, 0.0))
+                p = p & ~inner
+            if k > 0 and rng.random() < 0.25:
+                m &= ~p  # difference
+            else:
+                m |= p
+        m &= X * X + Y * Y <= reach * reach
+    else:
+        raise ValueError(f"unknown target {kind!r}")
+    return m.astype(np.float32)
+
+
+def random_volume(w: Workload, seed: int = 1) -> np.ndarray:
+    return np.random.default_rng(seed).random(w.vol_shape, dtype=np.float32)
+
+
+def random_projections(w: Workload, seed: int = 2) -> np.ndarray:
+    return np.random.default_rng(seed).random(w.proj_shape, dtype=np.float32)
+
+
+def sparse_projections(w: Workload, n_nonzero: int, seed: int = 3) -> np.ndarray:
+    """Projections that are zero except at n_nonzero seeded pixels (values in [0.5, 1.5))."""
+    rng = np.random.default_rng(seed)
+    g = np.zeros(w.proj_shape, dtype=np.float32)
+    flat = rng.choice(g.size, size=n_nonzero, replace=False)
+    g.flat[flat] = 0.5 + rng.random(n_nonzero, dtype=np.float32)
+    return g

@@ -1,0 +1,380 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: closed forms in the
+limits where the method reduces to a textbook result (parallel-beam Radon chords,
+linear fields, Beer-Lambert sums), the invariants of Snell's law across coaxial
+cylinders, the textbook angle form of the Fresnel equations, the transpose relation
+between the projection and dose operators, a fine-step integration with a library
+interpolator, and numbers printed in the paper.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.ndimage import map_coordinates
+
+from oracle import optics as OP
+from oracle import osmo as OS
+from oracle import vam_oracle as O
+from paper_2211_03516_gb300.inputs import INF, Workload, default_angles, pupil_samples, voxel_centres
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_w(**kw):
+    base = dict(name="pin", nx=24, ny=24, nz=24, voxel_mm=0.5, nu=21, nv=7, pixel_u_mm=0.55,
+                pixel_v_mm=0.5, n_angles=7, pupil_mm=INF, f_number=INF, pupil_pattern="chief",
+                rays_per_pixel=1, r_inner_mm=5.0, wall_mm=1.0, n_outside=1.0, n_glass=1.0,
+                n_resin=1.0, mu_per_mm=0.0, step_vox=0.5)
+    base.update(kw)
+    return Workload(**base)
+
+
+def refracting_w(**kw):
+    base = dict(pupil_mm=60.0, f_number=3.0, pupil_pattern="sunflower", rays_per_pixel=5,
+                n_glass=1.47, n_resin=1.50, mu_per_mm=0.15)
+    base.update(kw)
+    return small_w(**base)
+
+
+def pixel_x(w):
+    return (np.arange(w.nu) - (w.nu - 1) / 2.0) * w.pixel_u_mm
+
+
+def pixel_z(w):
+    return (np.arange(w.nv) - (w.nv - 1) / 2.0) * w.pixel_v_mm
+
+
+CHIEF = pupil_samples("chief", 1)
+
+
+# --- a1-a4: parallel-beam (Radon) limit ------------------------------------------------
+def test_radon_limit_chord_lengths():
+    """Telecentric, zero etendue, index matched, mu = 0, unit field: y = 2 sqrt(R^2 - b^2)."""
+    w = small_w()
+    y = O.adjoint(w, np.ones(w.vol_shape), CHIEF)
+    xu = pixel_x(w)
+    R = w.r_inner_mm
+    chord = np.where(np.abs(xu) < R, 2.0 * np.sqrt(np.maximum(R * R - xu * xu, 0.0)), 0.0)
+    assert (chord == 0).sum() == 2  # the two outer columns only cross the glass wall
+    np.testing.assert_allclose(y, np.broadcast_to(chord, y.shape), rtol=1e-12, atol=1e-12)
+
+
+def test_linear_field_fixes_rotation_axes_and_centre():
+    """Trilinear weights reproduce a linear field exactly and the midpoint rule integrates
+    it exactly, so each pixel equals chord x field(segment midpoint).  The midpoint of the
+    pixel's chord at angle theta sits at R(theta)(x_u, 0, z_v): this fixes the rotation
+    sense, the axis order and the voxel-centre convention."""
+    w = small_w(n_angles=9)
+    Z, Y, X = voxel_centres(w)
+    al, be, ga, ze = 0.7, 0.31, -0.23, 0.17
+    V = al + be * X + ga * Y + ze * Z
+    y = O.adjoint(w, V, CHIEF)
+    th = default_angles(w.n_angles)[:, None, None]
+    xu = pixel_x(w)[None, None, :]
+    zv = pixel_z(w)[None, :, None]
+    R = w.r_inner_mm
+    chord = np.where(np.abs(xu) < R, 2.0 * np.sqrt(np.maximum(R * R - xu * xu, 0.0)), 0.0)
+    expect = chord * (al + be * np.cos(th) * xu + ga * np.sin(th) * xu + ze * zv)
+    np.testing.assert_allclose(y, expect, rtol=1e-11, atol=1e-11)
+
+
+def test_beer_lambert_sum_closed_form_and_midpoint_bound():
+    """Unit field, mu > 0: sum_j delta exp(-mu (j+1/2) delta) is a geometric series, and
+    it lies within the midpoint-rule bound mu^2 delta^2 ell / 24 of (1 - exp(-mu ell))/mu."""
+    mu = 0.35
+    w = small_w(mu_per_mm=mu)
+    y = O.adjoint(w, np.ones(w.vol_shape), CHIEF)
+    R, ds = w.r_inner_mm, w.step_vox * w.voxel_mm
+    for u, x in enumerate(pixel_x(w)):
+        if abs(x) >= R:
+            assert np.all(y[:, :, u] == 0.0)
+            continue
+        ell = 2.0 * math.sqrt(R * R - x * x)
+        K = math.ceil(ell / ds - 1e-9)
+        dl = ell / K
+        geo = dl * math.exp(-mu * dl / 2) * (1 - math.exp(-mu * ell)) / (1 - math.exp(-mu * dl))
+        np.testing.assert_allclose(y[:, :, u], geo, rtol=1e-12)
+        exact = (1 - math.exp(-mu * ell)) / mu
+        assert abs(y[0, 0, u] - exact) <= mu * mu * dl * dl * ell / 24 * (1 + 1e-9)
+
+
+def test_sample_count_closed_form_with_z_clip():
+    """Telecentric chief rays stay at height z_v; rows whose footprint misses the grid
+    (q_z outside (-1, nz)) add no samples; the others add K = ceil(ell/ds) each."""
+    w = small_w(nv=40, n_angles=5)
+    ds = w.step_vox * w.voxel_mm
+    R = w.r_inner_mm
+    per_row = sum(math.ceil(2 * math.sqrt(R * R - x * x) / ds - 1e-9) for x in pixel_x(w) if abs(x) < R)
+    qz = pixel_z(w) / w.voxel_mm + (w.nz - 1) / 2.0
+    rows = int(np.sum((qz > -1) & (qz < w.nz)))
+    assert 0 < rows < w.nv
+    assert O.sample_count(w, CHIEF) == w.n_angles * rows * per_row
+
+
+# --- a1: ray generator ------------------------------------------------------------------
+def test_ray_generator_definition_non_telecentric():
+    w = refracting_w()
+    P = pupil_samples("sunflower", 5, seed=3)
+    D = w.pupil_mm / w.f_number
+    for (u, v, a) in [(0, 0, 0), (10, 3, 2), (20, 6, 4), (7, 1, 1)]:
+        r = O.trace(w, P, u, v, a)
+        C = np.array([P[a, 0] * D / 2, -w.pupil_mm, P[a, 1] * D / 2])
+        Q = np.array([pixel_x(w)[u], 0.0, pixel_z(w)[v]])
+        np.testing.assert_allclose(r["origin"], C, atol=1e-14)
+        np.testing.assert_allclose(r["d0"], (Q - C) / np.linalg.norm(Q - C), atol=1e-15)
+
+
+def test_ray_generator_telecentric_cone_matches_paper_divergence():
+    """Sec. 3.2 / Sec. 4: a 16 mm iris gives a 12.2 degree full divergence.  With the
+    working f-number from tan(6.1 deg) = 1/(2N), a telecentric ray from the stop's edge
+    makes 6.1 degrees with the chief ray, and every ray of the pixel crosses its image point."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_optics.json")))["telecentric_printer"]
+    half = math.radians(gold["full_divergence_large_deg"] / 2)
+    N = OP.f_number_for_half_angle(half)
+    w = small_w(f_number=N)
+    P = np.array([[1.0, 0.0], [0.0, -1.0], [0.0, 0.0]])
+    for a in range(3):
+        r = O.trace(w, P, 4, 2, a)
+        ang = math.degrees(math.acos(r["d0"][1]))
+        assert abs(ang - (0.0 if a == 2 else gold["full_divergence_large_deg"] / 2)) < 1e-9
+        Q = np.array([pixel_x(w)[4], 0.0, pixel_z(w)[2]])
+        t = (Q[1] - r["origin"][1]) / r["d0"][1]
+        np.testing.assert_allclose(r["origin"] + t * r["d0"], Q, atol=1e-12)
+
+
+# --- a2: refraction stage -----------------------------------------------------------------
+def _rays(w, P):
+    out = []
+    for v in range(w.nv):
+        for u in range(w.nu):
+            for a in range(P.shape[0]):
+                out.append(O.trace(w, P, u, v, a))
+    return out
+
+
+def test_snell_invariants_across_coaxial_cylinders():
+    """For cylinders about z, n d_z and n (x d_y - y d_x) are conserved by refraction and
+    along straight segments; hit points lie on the surfaces and on the incoming lines."""
+    # a thick wall (R_in = 3, R_o = 6): rays with n_glass R_in < b < R_o only cross the glass
+    w = refracting_w(nu=15, pixel_u_mm=0.9, nv=5, pixel_v_mm=1.3, n_glass=1.52, n_resin=1.43,
+                     r_inner_mm=3.0, wall_mm=3.0)
+    P = pupil_samples("sunflower", 5, seed=9)
+    Ro, Ri = w.r_inner_mm + w.wall_mm, w.r_inner_mm
+    n0, n1, n2 = w.n_outside, w.n_glass, w.n_resin
+    seen = {-1: 0, 0: 0, 1: 0, 2: 0}
+    for r in _rays(w, P):
+        seen[r["status"]] += 1
+        if r["status"] == -1:
+            # total internal reflection at the glass/resin surface (n_glass > n_resin):
+            # the ray is dropped; it must really be beyond the critical angle
+            p1, d1 = r["p1"], r["d1"]
+            t_near = None
+            o2 = p1[:2]
+            dd = d1[:2]
+            a2, b2, c2 = dd @ dd, 2 * o2 @ dd, o2 @ o2 - Ri * Ri
+            t_near = (-b2 - math.sqrt(b2 * b2 - 4 * a2 * c2)) / (2 * a2)
+            e = p1 + t_near * d1
+            cos_i = abs(e[0] * d1[0] + e[1] * d1[1]) / Ri
+            assert n1 * math.sqrt(1 - cos_i ** 2) > n2
+            continue
+        if r["status"] < 1:
+            continue
+        o, d0, p1, d1 = r["origin"], r["d0"], r["p1"], r["d1"]
+        assert abs(np.linalg.norm(d1) - 1) < 1e-14
+        assert abs(math.hypot(p1[0], p1[1]) - Ro) < 1e-12
+        t = np.dot(p1 - o, d0)
+        np.testing.assert_allclose(o + t * d0, p1, atol=1e-12)
+        assert abs(n0 * d0[2] - n1 * d1[2]) < 1e-14
+        Lz = lambda p, d: p[0] * d[1] - p[1] * d[0]
+        assert abs(n0 * Lz(o, d0) - n1 * Lz(p1, d1)) < 1e-12
+        if r["status"] != 2:
+            continue
+        e, d2, ex = r["e"], r["d2"], r["exit"]
+        assert abs(np.linalg.norm(d2) - 1) < 1e-14
+        assert abs(math.hypot(e[0], e[1]) - Ri) < 1e-12
+        assert abs(math.hypot(ex[0], ex[1]) - Ri) < 1e-12
+        t = np.dot(e - p1, d1)
+        assert t > 0
+        np.testing.assert_allclose(p1 + t * d1, e, atol=1e-12)
+        np.testing.assert_allclose(e + r["ell"] * d2, ex, atol=1e-12)
+        assert abs(n1 * d1[2] - n2 * d2[2]) < 1e-14
+        assert abs(n0 * Lz(o, d0) - n2 * Lz(e, d2)) < 1e-12
+        assert e[0] * d2[0] + e[1] * d2[1] < 0          # heads into the resin
+        assert r["k"] == math.ceil(r["ell"] / (w.step_vox * w.voxel_mm) - 1e-9)
+    assert seen[-1] > 0 and seen[0] > 0 and seen[1] > 0 and seen[2] > 0
+
+
+def _fresnel_angles(ti, tt):
+    """Textbook angle form of the unpolarised Fresnel transmission."""
+    if ti == 0.0:
+        return None
+    rs = (math.sin(ti - tt) / math.sin(ti + tt)) ** 2
+    rp = (math.tan(ti - tt) / math.tan(ti + tt)) ** 2
+    return 1.0 - 0.5 * (rs + rp)
+
+
+def test_fresnel_matches_angle_form_and_scalar_snell():
+    w = refracting_w(nu=15, pixel_u_mm=0.8, n_glass=1.52, n_resin=1.43)
+    P = pupil_samples("sunflower", 5, seed=9)
+    Ro, Ri = w.r_inner_mm + w.wall_mm, w.r_inner_mm
+    checked = 0
+    for r in _rays(w, P):
+        if r["status"] != 2:
+            continue
+        for (p, R, din, dout, n1, n2, T) in [(r["p1"], Ro, r["d0"], r["d1"], w.n_outside, w.n_glass, r["t1"]),
+                                              (r["e"], Ri, r["d1"], r["d2"], w.n_glass, w.n_resin, r["t2"])]:
+            nrm = np.array([p[0] / R, p[1] / R, 0.0])
+            ti = math.atan2(np.linalg.norm(np.cross(din, nrm)), abs(np.dot(din, nrm)))
+            tt = math.atan2(np.linalg.norm(np.cross(dout, nrm)), abs(np.dot(dout, nrm)))
+            assert abs(n1 * math.sin(ti) - n2 * math.sin(tt)) < 1e-12
+            # refracted ray stays in the plane of incidence
+            assert abs(np.dot(np.cross(din, nrm), dout)) < 1e-12
+            ref = _fresnel_angles(ti, tt)
+            if ref is not None and ti > 1e-3:
+                assert abs(T - ref) < 1e-9
+                checked += 1
+    assert checked > 50
+
+
+def test_fresnel_normal_incidence():
+    """The ray through the axis meets both surfaces head-on: T = 1 - ((n1-n2)/(n1+n2))^2."""
+    w = refracting_w(pupil_mm=100.0, f_number=INF, pupil_pattern="chief", rays_per_pixel=1)
+    r = O.trace(w, CHIEF, (w.nu - 1) // 2, (w.nv - 1) // 2, 0)
+    n0, n1, n2 = w.n_outside, w.n_glass, w.n_resin
+    assert r["status"] == 2
+    assert abs(r["t1"] - (1 - ((n0 - n1) / (n0 + n1)) ** 2)) < 1e-15
+    assert abs(r["t2"] - (1 - ((n1 - n2) / (n1 + n2)) ** 2)) < 1e-15
+    np.testing.assert_allclose(r["d2"], [0, 1, 0], atol=1e-15)
+    np.testing.assert_allclose(r["e"], [0, -w.r_inner_mm, 0], atol=1e-14)
+    assert abs(r["ell"] - 2 * w.r_inner_mm) < 1e-13
+
+
+# --- a4/a5: operators ---------------------------------------------------------------------
+def test_adjoint_identity_refracting_finite_etendue():
+    """<A g, V> = <g, P V>: the dose operator is the exact transpose of the projection."""
+    w = refracting_w(nx=17, ny=16, nz=9, nu=11, nv=5, pixel_u_mm=0.9, pixel_v_mm=0.7, n_angles=5,
+                     r_inner_mm=3.0, wall_mm=0.8)
+    P = pupil_samples("sunflower", 5, seed=4)
+    rng = np.random.default_rng(0)
+    V = rng.random(w.vol_shape)
+    g = rng.random(w.proj_shape)
+    lhs = np.sum(O.forward(w, g, P) * V)
+    rhs = np.sum(g * O.adjoint(w, V, P))
+    assert abs(lhs - rhs) <= 1e-13 * abs(rhs)
+
+
+def test_dose_matrix_is_transpose_of_projection_matrix():
+    w = refracting_w(nx=8, ny=8, nz=4, nu=5, nv=3, pixel_u_mm=0.5, pixel_v_mm=0.5, n_angles=3,
+                     r_inner_mm=1.2, wall_mm=0.3, rays_per_pixel=2, pupil_pattern="sunflower", voxel_mm=0.5)
+    P = pupil_samples("sunflower", 2, seed=1)
+    nvox, npix = int(np.prod(w.vol_shape)), int(np.prod(w.proj_shape))
+    At = np.zeros((npix, nvox))
+    for i in range(nvox):
+        e = np.zeros(nvox)
+        e[i] = 1.0
+        At[:, i] = O.adjoint(w, e.reshape(w.vol_shape), P).ravel()
+    A = np.zeros((nvox, npix))
+    for i in range(npix):
+        e = np.zeros(npix)
+        e[i] = 1.0
+        A[:, i] = O.forward(w, e.reshape(w.proj_shape), P).ravel()
+    assert np.count_nonzero(At) > 100
+    np.testing.assert_allclose(A, At.T, rtol=0, atol=1e-15)
+
+
+def _brute_pixel(w, V, P, theta, v, u, sub=256):
+    """Independent fine-step integral of trilinear(V) along each traced in-resin segment,
+    interpolated with scipy's map_coordinates (order 1, zero outside the grid)."""
+    h = w.voxel_mm
+    total = 0.0
+    for a in range(P.shape[0]):
+        r = O.trace(w, P, u, v, a)
+        if r["status"] != 2:
+            continue
+        ell = r["ell"]
+        K = int(math.ceil(ell / (h / sub)))
+        dl = ell / K
+        s = (np.arange(K) + 0.5) * dl
+        pts = r["e"][None, :] + s[:, None] * r["d2"][None, :]
+        c, sn = math.cos(theta), math.sin(theta)
+        xr = c * pts[:, 0] - sn * pts[:, 1]
+        yr = sn * pts[:, 0] + c * pts[:, 1]
+        coords = [pts[:, 2] / h + (w.nz - 1) / 2, yr / h + (w.ny - 1) / 2, xr / h + (w.nx - 1) / 2]
+        vals = map_coordinates(V, coords, order=1, mode="grid-constant", cval=0.0)
+        total += r["t1"] * r["t2"] / P.shape[0] * np.sum(np.exp(-w.mu_per_mm * s) * vals) * dl
+    return total
+
+
+def test_brute_force_fine_step_convergence():
+    w0 = refracting_w(nx=12, ny=12, nz=10, nu=8, nv=6, pixel_u_mm=0.45, pixel_v_mm=0.45, n_angles=4,
+                      r_inner_mm=2.2, wall_mm=0.5, pupil_mm=30.0, f_number=3.0, rays_per_pixel=3,
+                      mu_per_mm=0.3)
+    P = pupil_samples("sunflower", 3, seed=2)
+    V = np.random.default_rng(5).random(w0.vol_shape)
+    th = default_angles(w0.n_angles)
+    pix = [(0, 3, 3), (1, 2, 4), (2, 4, 1), (3, 1, 6), (1, 5, 3)]
+    ref = np.array([_brute_pixel(w0, V, P, th[k], v, u) for (k, v, u) in pix])
+    assert np.all(ref > 0)
+    errs = []
+    for step in (0.5, 0.125, 1.0 / 64):
+        w = w0.scaled(step_vox=step)
+        got = O.adjoint_pixels(w, V, P, pix)
+        errs.append(np.max(np.abs(got - ref) / ref))
+    # midpoint sums converge on the fine integral as the step shrinks
+    assert errs[2] < 2e-5
+    assert errs[1] < 5e-4
+    assert errs[0] < 5e-3
+    assert errs[2] < errs[1] < errs[0]
+
+
+# --- paper numbers ------------------------------------------------------------------------
+def test_paper_printed_optics_numbers():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_optics.json")))
+    nt = gold["non_telecentric_printer"]
+    m = OP.magnification(nt["image_pixel_mm"], nt["dmd_pitch_mm"])
+    assert abs(m - 5.0) < 1e-12
+    assert abs(OP.thin_lens_image_distance(nt["focal_length_mm"], m) - nt["focus_distance_mm"]) < 0.05
+    width = nt["dmd_columns"] * nt["image_pixel_mm"]
+    assert abs(nt["focus_distance_mm"] / nt["throw_ratio"] - width) / width < 1e-3
+    assert abs(nt["downsample"] * nt["image_pixel_mm"] - nt["min_voxel_mm"]) < 1e-12
+    tc = gold["telecentric_printer"]
+    assert abs(tc["downsample"] * tc["pixel_mm"] - tc["min_voxel_mm"]) < 1e-12
+    # both printed divergences come from one stop-to-image distance
+    d = tc["iris_large_mm"] / (2 * math.tan(math.radians(tc["full_divergence_large_deg"] / 2)))
+    assert abs(OP.full_divergence_deg(tc["iris_small_mm"], d) - tc["full_divergence_small_deg"]) < 0.05
+    et = gold["etendue"]
+    got = OP.etendue_sr_mm2(et["pixel_mm"], et["full_divergence_deg"])
+    assert abs(got - et["etendue_sr_mm2"]) / et["etendue_sr_mm2"] < 1e-3
+
+
+# --- optimiser and loss (readings) ---------------------------------------------------------
+def test_osmo_fixed_point_and_nonnegativity():
+    f = np.array([1.0, 0.0, 1.0, 1.0, 0.0])
+    ident = lambda x: x.copy()
+    g, dn, m, err = OS.osmo(f, ident, ident, n_iter=5)
+    assert len(err) == 1 and err[0] == 0.0
+    np.testing.assert_array_equal(m, f)
+    rng = np.random.default_rng(0)
+    M = rng.random((4, 5))
+    g, dn, m, err = OS.osmo(f, lambda x: M @ x - 0.8, lambda y: M.T @ y, n_iter=6)
+    assert np.all(m >= 0) and np.all(g >= 0) and dn.max() == 1.0
+    assert np.all(np.isfinite(err))
+
+
+def test_threshold_loss_gradient_central_differences():
+    rng = np.random.default_rng(1)
+    D = rng.random(200) * 1.4
+    f = (rng.random(200) < 0.4).astype(np.float64)
+    L, g = OS.threshold_loss(D, f, 0.9, 1.0)
+    eps = 1e-6
+    for i in range(0, 200, 7):
+        Dp, Dm = D.copy(), D.copy()
+        Dp[i] += eps
+        Dm[i] -= eps
+        fd = (OS.threshold_loss(Dp, f, 0.9, 1.0)[0] - OS.threshold_loss(Dm, f, 0.9, 1.0)[0]) / (2 * eps)
+        assert abs(fd - g[i]) < 1e-7
+    L0, g0 = OS.threshold_loss(np.where(f > 0, 1.2, 0.5), f, 0.9, 1.0)
+    assert L0 == 0.0 and np.all(g0 == 0.0)
