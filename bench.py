@@ -1,0 +1,319 @@
+"""Benchmark: ray-voxel samples/s of the projection (A^T) + dose (A) operators inside the
+plain FP32 projection optimiser, on the 256^3 finite-etendue workload.
+
+One step = one optimiser iteration over the whole volume: g = max(0, A^T m),
+d = A g, normalise, error, model update (all in the CUDA library, called through the
+C ABI).  Units per step = 2 x samples_per_pass (one adjoint and one forward pass).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vamrt|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of this
+path) on the host cores, on a bounded sample of the same workload.  With N > 1 each
+rank runs an independent replica (the operator pair does not exchange data in this
+library); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ray-voxel samples/s fwd+adjoint; time-to-target dose error vs plain, 1 GB300"
+UNIT = "samples/s"
+WORKLOAD = "mid_256cube_360ang_16rays"
+BYTES_PER_SAMPLE = 32          # 8 trilinear corners x 4 B (FP32 gathers / reductions)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_threads() -> int:
+    return 1   # the oracle is single-threaded
+
+
+def oracle_sample(w, pupil, target, rows, angle=0):
+    """Oracle A^T and A over pixel rows `rows` of one angle: returns (samples, seconds)."""
+    from oracle import vam_oracle as O
+    pix = [(angle, v, u) for v in rows for u in range(w.nu)]
+    # samples the chosen pixels visit: per traced ray, the midpoints whose footprint reaches the grid
+    n = 0
+    for v in rows:
+        for u in range(w.nu):
+            for a in range(pupil.shape[0]):
+                r = O.trace(w, pupil, u, v, a)
+                if r["status"] != 2:
+                    continue
+                dl = r["ell"] / r["k"]
+                j = np.arange(r["k"])
+                qz = (r["e"][2] + (j + 0.5) * dl * r["d2"][2]) / w.voxel_mm + 0.5 * (w.nz - 1)
+                n += int(np.count_nonzero((qz > -1) & (qz < w.nz)))
+    g = np.zeros(w.proj_shape)
+    t0 = time.perf_counter()
+    y = O.adjoint_pixels(w, target, pupil, pix)
+    for (k, v, u), val in zip(pix, y):
+        g[k, v, u] = max(val, 0.0)
+    O.forward(w, g, pupil)
+    dt = time.perf_counter() - t0
+    return 2 * n, dt
+
+
+def run_reference(args, rank, world):
+    from paper_2211_03516_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    pupil = I.workload_pupil(w)
+    target = I.make_target(w)
+    mid = w.nv // 2
+    rows = list(range(mid - args.ref_rows // 2, mid - args.ref_rows // 2 + args.ref_rows))
+    for _ in range(args.warmup):
+        oracle_sample(w, pupil, target, rows[:1])
+    tot_n, tot_t = 0, 0.0
+    for s in range(args.steps):
+        n, dt = oracle_sample(w, pupil, target, rows, angle=(s * 37) % w.n_angles)
+        tot_n += n
+        tot_t += dt
+    value = tot_n / tot_t
+    sample = (f"{args.ref_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of one angle per step, "
+              f"projection then dose, FP64 oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "samples_per_step": tot_n // args.steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2211_03516_gb300 import inputs as I
+    from paper_2211_03516_gb300 import vamrt
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vamrt.lib()
+
+    w = I.WORKLOADS[args.workload]
+    pupil = I.workload_pupil(w)
+    target_np = I.make_target(w)
+    t0 = time.perf_counter()
+    P = vamrt.Projector.from_workload(w, pupil)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    spp = P.sample_count()
+    units_per_step = 2 * spp
+
+    target = torch.from_numpy(target_np).to(dev)
+    model = target.clone()
+    proj = torch.empty(w.proj_shape, device=dev)
+    dose = torch.empty(w.vol_shape, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(timing=False):
+        return P.optimize(target, model=model, max_iter=1, tol=0.0, proj=proj, dose=dose, timing=timing)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM (model/target/proj/dose > L2) ----
+    launches0 = vamrt.vamrt_launch_count()
+    adj_ms = fwd_ms = upd_ms = 0.0
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step(timing=True)
+            adj_ms += r["adjoint_ms"]
+            fwd_ms += r["forward_ms"]
+            upd_ms += r["update_ms"]
+        ev1.record(stream)
+        barrier()
+    launches = vamrt.vamrt_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    t_local = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * units_per_step * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    host_target = torch.from_numpy(target_np).pin_memory()
+    host_proj = torch.empty(w.proj_shape, dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        target.copy_(host_target, non_blocking=True)
+        r = step()
+        host_proj.copy_(proj, non_blocking=True)
+        torch.cuda.synchronize()
+        _ = r["final_error"]
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_local = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
+    e2e_value = world * units_per_step * e2e_steps / float(e2e_local.item())
+
+    # ---- roofline of the dominant kernel (CUDA events around it, inside the library) ----
+    hbm, peak_kind = peaks()
+    dom = "forward" if fwd_ms >= adj_ms else "adjoint"
+    dom_ms = (fwd_ms if dom == "forward" else adj_ms) / args.steps
+    achieved = spp * BYTES_PER_SAMPLE / (dom_ms / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get(f"{w.name}:{dom}")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt = oracle_sample(w, pupil, target_np, list(range(w.nv // 2, w.nv // 2 + args.cpu_rows)))
+        cpu = {"value": n / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{args.cpu_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of angle 0, "
+                         f"projection then dose ({n} samples, {dt:.1f} s)"}
+
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "grid": list(w.vol_shape), "angles": w.n_angles,
+                   "pixels": [w.nv, w.nu], "rays_per_pixel": w.rays_per_pixel,
+                   "step": "one optimiser iteration: projection (A^T) + clamp + dose (A) + normalise/update",
+                   "samples_per_pass": spp, "units_per_step": units_per_step,
+                   "l2": "inputs larger than L2 (model, target, projections, dose, scratch: 0.36 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "setup_s": round(setup_s, 3)},
+        "phase_ms_per_step": {"adjoint": adj_ms / args.steps, "forward": fwd_ms / args.steps,
+                              "update": upd_ms / args.steps},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "bytes_per_sample": BYTES_PER_SAMPLE},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": host_target.numel() * 4,
+                "d2h_bytes_per_step": host_proj.numel() * 4 + 8},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vamrt", choices=["vamrt", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-rows", type=int, default=48)
+    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

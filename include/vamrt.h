@@ -1,0 +1,200 @@
+/*
+ * vamrt — GB300-native 3D ray-traced projection and dose operators for tomographic
+ * volumetric additive manufacturing (Webber et al., "Versatile volumetric additive
+ * manufacturing with 3D ray tracing", arXiv 2211.03516).
+ *
+ * C ABI.  Every entry point takes plain pointers and sizes, returns a vamrt_status and
+ * never lets an exception or exit() cross the boundary.  Device buffers are owned by
+ * the caller unless stated otherwise; the library owns only a projector handle (its ray
+ * table, angle table and one scratch volume) and small reduction buffers.
+ *
+ * Conventions (shared by every call):
+ *   - Volume layout [nz][ny][nx], x fastest; voxel (i,j,k) has its centre at
+ *     ((i-(nx-1)/2) h, (j-(ny-1)/2) h, (k-(nz-1)/2) h) in the vial frame; z is the vial
+ *     (rotation) axis.  Values outside the grid count as zero.
+ *   - Projection layout [n_angles][nv][nu], u fastest; pixel (u,v) images to the point
+ *     ((u-(nu-1)/2) pu, 0, (v-(nv-1)/2) pv) of the best-focus plane y = 0, which contains
+ *     the rotation axis (Sec. 2.8).  Light travels +y.
+ *   - At angle theta_k a point x of the fixed (projector) frame sits at R_z(theta_k) x
+ *     in the vial frame, R_z(t) = [[cos t, -sin t], [sin t, cos t]].
+ *   - Calls are stream-ordered and asynchronous unless stated.  A projector may be used
+ *     by one stream at a time (its scratch volume is shared by the operators).
+ *   - On error the outputs are unspecified but no access outside the caller's buffers
+ *     happens; vamrt_last_error() gives a one-line reason for the calling thread.
+ */
+#ifndef VAMRT_H
+#define VAMRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VAMRT_OK = 0,
+    VAMRT_EINVAL = 1,          /* an argument is out of range, NULL or inconsistent */
+    VAMRT_EUNSUPPORTED = 2,    /* a valid request this build does not implement */
+    VAMRT_ECUDA = 3,           /* a CUDA runtime call failed (message in vamrt_last_error) */
+    VAMRT_ENOMEM = 4,          /* device allocation failed */
+    VAMRT_NOT_CONVERGED = 5,   /* the optimiser hit its iteration cap above tolerance */
+    VAMRT_NUMERIC = 6          /* NaN/Inf or an all-zero dose met in a reduction */
+} vamrt_status;
+
+typedef enum {
+    VAMRT_F32 = 0,             /* float */
+    VAMRT_BF16 = 1             /* bfloat16 storage; all sums are FP32 */
+} vamrt_dtype;
+
+/* Operator flags */
+#define VAMRT_ACCUMULATE   1u  /* add into the output instead of overwriting it */
+#define VAMRT_CLAMP_NONNEG 2u  /* adjoint only: write max(0, result) (OSMO's clamp, Sec. 2.7) */
+
+/*
+ * Printer, vial and grid description (Sec. 2.1, 2.5, 2.6).  All lengths in mm.
+ *   pupil_mm    distance from the rotation axis to the aperture stop, which sits on the
+ *               -y side.  INFINITY selects a telecentric projector.  Non-telecentric:
+ *               ray a of pixel (u,v) leaves the stop point (xi_a D/2, -pupil_mm, eta_a D/2),
+ *               D = pupil_mm / f_number, and passes through the pixel's image point.
+ *               Telecentric: the ray crosses the image point with direction proportional
+ *               to (-xi_a t, 1, -eta_a t), t = 1/(2 f_number).
+ *   f_number    INFINITY = zero etendue (all rays of a pixel are its chief ray).
+ *   pupil_xy    HOST array of rays_per_pixel points (xi, eta) in the unit disk, copied
+ *               during vamrt_make_projector.  NULL means one chief ray (0, 0).
+ *   vial        inner radius r_inner_mm, glass wall wall_mm, refractive indices outside,
+ *               glass, resin; Fresnel losses (unpolarised) at the outer and inner surface;
+ *               tracing stops at the inner wall on the far side (Sec. 2.1).
+ *   mu_per_mm   Beer-Lambert absorption coefficient of the resin (Sec. 2.5).
+ *   angles_rad  HOST array of n_angles angles, copied; NULL = 2 pi k / n_angles.
+ *   step_vox    nominal spacing of the samples on a ray, in voxels (0 = 0.5, the 2x
+ *               super-sampling of Sec. 2.2).  Each in-resin segment of length ell gets
+ *               K = ceil(ell / (step_vox h) - 1e-9) midpoint samples s_j = (j+1/2) ell/K.
+ * The grid must enclose the resin cylinder: r_inner_mm / voxel_mm < (min(nx,ny)+1)/2.
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    double voxel_mm;
+    int32_t nu, nv;
+    double pixel_u_mm, pixel_v_mm;
+    double pupil_mm;
+    double f_number;
+    int32_t rays_per_pixel;
+    const double *pupil_xy;
+    double r_inner_mm, wall_mm;
+    double n_outside, n_glass, n_resin;
+    double mu_per_mm;
+    int32_t n_angles;
+    const double *angles_rad;
+    double step_vox;
+} vamrt_geometry;
+
+typedef struct vamrt_projector vamrt_projector;   /* opaque */
+
+typedef struct {
+    int64_t n_rays;            /* nu * nv * rays_per_pixel */
+    int64_t rays_in_resin;     /* rays that reach the resin */
+    uint64_t samples_per_pass; /* n_angles * sum over rays of samples reaching the grid */
+    uint64_t scratch_bytes;    /* device bytes owned by the handle (table + scratch) */
+} vamrt_info;
+
+/*
+ * Build a projector: validates the geometry on the host, then traces every
+ * (pixel, aperture-sample) ray through the vial once, in FP64 on the device (Sec. 2.1:
+ * ray generation, vector Snell's law and Fresnel transmission at both cylinder surfaces,
+ * the in-resin segment).  The vial is rotationally symmetric about z, so the segment at
+ * angle theta_k is the theta = 0 segment rotated; only the theta = 0 table is stored
+ * (40 B per ray, FP32).  Synchronises `stream` (a cudaStream_t, NULL = legacy default)
+ * before returning.  *out receives a handle to release with vamrt_destroy_projector.
+ * Errors: EINVAL (bad geometry), ENOMEM, ECUDA.
+ */
+vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamrt_projector **out);
+
+/* Release a projector and its device memory (synchronises the device first). NULL is a no-op. */
+void vamrt_destroy_projector(vamrt_projector *p);
+
+/* Sizes, ray counts and the exact number of ray-voxel samples one operator pass visits. */
+vamrt_status vamrt_get_info(const vamrt_projector *p, vamrt_info *info);
+
+/* Samples per pass (same as vamrt_get_info's samples_per_pass). */
+vamrt_status vamrt_sample_count(const vamrt_projector *p, uint64_t *samples_per_pass);
+
+/*
+ * Projection operator, the adjoint A^T (Sec. 2.4, with Sec. 2.5's transmission factors):
+ *   proj[k][v][u] = sum_a sum_j c_j sum_{8 corners} w_c vol[c],
+ *   c_j = (T1 T2 / M) exp(-mu s_j) delta,  w_c = trilinear weight (Sec. 2.2).
+ * vol: device [nz][ny][nx] of vol_dtype; proj: device [n_angles][nv][nu] of proj_dtype.
+ * flags: VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG.  Uses the handle's scratch volume.
+ * Errors: EINVAL (NULL pointers, unknown dtype/flags), ECUDA.
+ */
+vamrt_status vamrt_adjoint(vamrt_projector *p, const void *vol, vamrt_dtype vol_dtype,
+                           void *proj, vamrt_dtype proj_dtype, uint32_t flags, void *stream);
+
+/*
+ * Dose operator A (Sec. 2.5): every sample of every ray adds
+ *   proj[k][v][u] * c_j * w_c
+ * to each of its 8 trilinear corner voxels, over all angles; A is exactly the transpose
+ * of vamrt_adjoint.  Sums run in an FP32 scratch volume owned by the handle (summation
+ * order is not deterministic); dose gets the result in dose_dtype.
+ * flags: VAMRT_ACCUMULATE.  Errors: EINVAL, ECUDA.
+ */
+vamrt_status vamrt_forward_dose(vamrt_projector *p, const void *proj, vamrt_dtype proj_dtype,
+                                void *dose, vamrt_dtype dose_dtype, uint32_t flags, void *stream);
+
+/*
+ * Projection optimisation (Sec. 2.7).  The paper runs the object-space model
+ * optimisation of Rackson et al. with both operators replaced by the ray-traced ones
+ * and stops once the absolute relative dose error is below 0.5 %.  Iteration, per the
+ * reading this library implements:
+ *   g = max(0, A^T m);  d = A g;  dn = d / max(d);
+ *   E = sum |dn - f| / sum f;  m <- max(0, m + f - dn);  stop once E < tol.
+ * target: device f32 [nz][ny][nx] (the binary part f).  model: device f32, in = m0
+ * (copy the target there for OSMO's start), out = the updated model.  proj: device
+ * [n_angles][nv][nu] in proj_dtype, out = g of the last iteration.  dose: device
+ * [nz][ny][nx] in dose_dtype, out = dn of the last iteration.
+ * Synchronises `stream` once every check_every iterations to read E.
+ */
+typedef struct {
+    int32_t max_iter;          /* 1 .. 4096 */
+    double tol;                /* stop once E < tol (0.005 in the paper) */
+    int32_t check_every;       /* read E on the host every this many iterations (>= 1) */
+    vamrt_dtype proj_dtype;    /* storage of g */
+    vamrt_dtype dose_dtype;    /* storage of dn */
+    int32_t timing;            /* nonzero: time each phase with CUDA events on `stream` */
+} vamrt_opt_params;
+
+typedef struct {
+    int32_t iterations;        /* iterations run */
+    double final_error;        /* E of the last iteration */
+    double *error_history;     /* optional HOST array of max_iter entries (E per iteration) */
+    double adjoint_ms;         /* with timing: summed device time of the projection kernels */
+    double forward_ms;         /* with timing: summed device time of the dose kernels */
+    double update_ms;          /* with timing: summed device time of normalise/update/error */
+} vamrt_opt_report;
+
+vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *model, void *proj,
+                            void *dose, const vamrt_opt_params *params, vamrt_opt_report *report,
+                            void *stream);
+
+/*
+ * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index
+ * r = (a nv + v) nu + u):  a4[r] = (e_x, e_y, e_z, delta) in voxel units (entry point
+ * relative to the axis, sample spacing);  b4[r] = (d_x, d_y, d_z, T1 T2 delta_mm / M);
+ * j2[r] = (j_lo, j_hi), the samples whose footprint reaches the grid (-1 < q_z < nz).
+ * Any pointer may be NULL.  Synchronous.
+ */
+vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4, int32_t *j2);
+
+/* Number of kernels this library has launched in the process (all devices). */
+uint64_t vamrt_launch_count(void);
+
+/* Static description of a status code. */
+const char *vamrt_status_string(vamrt_status s);
+
+/* Detail of the last error on the calling thread ("" if none). */
+const char *vamrt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VAMRT_H */

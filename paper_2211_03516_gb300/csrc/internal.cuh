@@ -1,0 +1,85 @@
+// Internal declarations shared by the vamrt CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vamrt.h"
+
+namespace vamrt {
+
+// Largest optimiser run whose error history the handle keeps on the device.
+constexpr int kMaxHistory = 4096;
+// Partial-sum slots for the deterministic two-pass reductions.
+constexpr int kRedBlocks = 1024;
+
+// Per-launch constants of the two operators.  Positions are in padded index
+// coordinates: the scratch volume has one zero voxel of halo on every face, so the
+// voxel (i,j,k) of the caller's grid sits at (i+1, j+1, k+1).
+struct OpParams {
+    const float4 *A;      // (e_x, e_y, e_z, delta) in voxels, theta = 0 frame
+    const float4 *B;      // (d_x, d_y, d_z, T1 T2 delta_mm / M)
+    const int2 *J;        // [j_lo, j_hi) samples whose footprint reaches the grid
+    const float2 *cs;     // (cos theta_k, sin theta_k)
+    int nu, nv, M, n_angles;
+    int px, py, pz;       // padded extents
+    float cx, cy, cz;     // axis position in padded index coordinates
+    float neg_mu_vox_log2e;  // -mu h log2(e): attenuation = exp2(this * s_vox)
+};
+
+// Per-ray constants of the FP64 tracer.
+struct TraceParams {
+    const double *pupil_xy;   // device, M pairs
+    int nu, nv, M, nz;
+    double pu, pv;
+    double pupil_mm, f_number;
+    int telecentric, chief_only;
+    double r_in, r_out, n_out, n_glass, n_resin;
+    double h, ds;
+};
+
+}  // namespace vamrt
+
+struct vamrt_projector {
+    vamrt_geometry g;          // copy; host pointers cleared
+    int device;
+    int num_sms;
+    int64_t n_rays;
+    int64_t rays_in_resin;
+    uint64_t samples_per_angle;
+    uint64_t device_bytes;
+    float4 *tabA;
+    float4 *tabB;
+    int2 *tabJ;
+    float2 *cs;
+    float *scratch;            // padded (nx+2)(ny+2)(nz+2) FP32 volume
+    int64_t pad_elems;
+    double *red;               // kRedBlocks partials + scalars
+    double *hist;              // kMaxHistory errors
+    float *dmax;               // one float, max of the dose
+    double *host_err;          // pinned, one double
+    vamrt::OpParams op;
+};
+
+namespace vamrt {
+
+// Count of kernel launches issued by the library (vamrt_launch_count).
+void count_launches(unsigned n);
+
+// raytable.cu
+cudaError_t launch_raytable(const TraceParams &T, float4 *A, float4 *B, int2 *J,
+                            unsigned long long *counters, cudaStream_t s);
+
+// operators.cu
+cudaError_t launch_pad(const vamrt_projector *p, const void *vol, vamrt_dtype dt, cudaStream_t s);
+cudaError_t launch_adjoint(const vamrt_projector *p, vamrt_dtype vol_dt, void *proj, vamrt_dtype proj_dt,
+                           uint32_t flags, cudaStream_t s);
+cudaError_t launch_forward(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, cudaStream_t s);
+cudaError_t launch_unpad(const vamrt_projector *p, void *dose, vamrt_dtype dt, uint32_t flags, cudaStream_t s);
+
+// osmo.cu
+cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
+cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
+                             vamrt_dtype dose_dt, const double *fsum, double *err_out, cudaStream_t s);
+
+}  // namespace vamrt

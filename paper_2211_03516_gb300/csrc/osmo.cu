@@ -1,0 +1,136 @@
+// Elementwise and reduction kernels of the projection optimiser (Sec. 2.7).
+//
+// Per iteration, after the two operators: the dose maximum (order-free, so exact), then
+// one fused pass that normalises the dose, writes it out, updates the model and emits
+// per-block FP64 partial sums of |dn - f|; a single block adds the partials in a fixed
+// order, so the error E is deterministic.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace vamrt {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void st_dose(float *p, float x) { *p = x; }
+__device__ __forceinline__ void st_dose(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+
+template <typename T>
+__device__ T block_sum(T x, T *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = x;
+    __syncthreads();
+    T r = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    __syncthreads();
+    return r;
+}
+
+__global__ void sum_partials_kernel(const float *__restrict__ x, int64_t n, double *__restrict__ partials)
+{
+    __shared__ double sh[kThreads / 32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)x[i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// out = scale * sum(partials[0..n)), or NaN when scale is not finite / the sum is not.
+__global__ void finish_sum_kernel(const double *__restrict__ partials, int n, const double *__restrict__ divisor,
+                                  double *__restrict__ out)
+{
+    __shared__ double sh[kThreads / 32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) *out = divisor ? s / *divisor : s;
+}
+
+__global__ void interior_max_kernel(const float *__restrict__ acc, int nx, int ny, int nz, float *__restrict__ out)
+{
+    const int64_t total = (int64_t)nx * ny * nz;
+    const int px = nx + 2, py = ny + 2;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / ((int64_t)nx * ny));
+        m = fmaxf(m, acc[((int64_t)(z + 1) * py + (y + 1)) * px + (x + 1)]);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    // dose values are >= 0, so their bit patterns order like the values
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
+}
+
+template <typename DT>
+__global__ void osmo_update_kernel(const float *__restrict__ acc, const float *__restrict__ dmax,
+                                   const float *__restrict__ target, float *__restrict__ model,
+                                   DT *__restrict__ dose, int nx, int ny, int nz, double *__restrict__ partials)
+{
+    __shared__ double sh[kThreads / 32];
+    const int64_t total = (int64_t)nx * ny * nz;
+    const int px = nx + 2, py = ny + 2;
+    const float inv = 1.0f / *dmax;
+    double err = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / ((int64_t)nx * ny));
+        const float dn = acc[((int64_t)(z + 1) * py + (y + 1)) * px + (x + 1)] * inv;
+        const float f = target[i];
+        st_dose(dose + i, dn);
+        model[i] = fmaxf(0.f, model[i] + (f - dn));
+        err += fabs((double)dn - (double)f);
+    }
+    const double s = block_sum(err, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+inline int red_grid(int64_t n)
+{
+    int64_t g = (n + kThreads - 1) / kThreads;
+    if (g > kRedBlocks) g = kRedBlocks;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s)
+{
+    const int64_t n = (int64_t)p->g.nx * p->g.ny * p->g.nz;
+    const int G = red_grid(n);
+    sum_partials_kernel<<<G, kThreads, 0, s>>>(x, n, p->red);
+    finish_sum_kernel<<<1, kThreads, 0, s>>>(p->red, G, nullptr, out);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
+                             vamrt_dtype dose_dt, const double *fsum, double *err_out, cudaStream_t s)
+{
+    const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
+    const int64_t n = (int64_t)nx * ny * nz;
+    cudaError_t e = cudaMemsetAsync(p->dmax, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    int gm = (int)((n + kThreads - 1) / kThreads);
+    if (gm > p->num_sms * 8) gm = p->num_sms * 8;
+    interior_max_kernel<<<gm, kThreads, 0, s>>>(p->scratch, nx, ny, nz, p->dmax);
+    const int G = red_grid(n);
+    if (dose_dt == VAMRT_F32)
+        osmo_update_kernel<float><<<G, kThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,
+                                                         nx, ny, nz, p->red);
+    else
+        osmo_update_kernel<__nv_bfloat16><<<G, kThreads, 0, s>>>(p->scratch, p->dmax, target, model,
+                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, p->red);
+    finish_sum_kernel<<<1, kThreads, 0, s>>>(p->red, G, fsum, err_out);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+}  // namespace vamrt

@@ -1,0 +1,140 @@
+// Ray generation and refraction through the vial (Sec. 2.1), once per projector, FP64.
+//
+// One thread per (pixel, aperture sample).  The ray leaves the aperture stop (or, for a
+// telecentric projector, arrives parallel to its cone direction), meets the outer
+// cylinder, refracts into the glass by the vector form of Snell's law with the
+// unpolarised Fresnel transmission, does the same at the inner cylinder, and runs
+// straight through the resin to the inner wall on the far side.  Everything up to the
+// stored segment is FP64: the quadratic near grazing incidence and the refraction are
+// where FP32 would lose the geometry.  The segment is stored in FP32, in voxel units.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace vamrt {
+namespace {
+
+struct d3 { double x, y, z; };
+
+__device__ inline d3 operator+(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ inline d3 operator*(double s, d3 a) { return {s * a.x, s * a.y, s * a.z}; }
+
+// Line o + t d against x^2 + y^2 = R^2.  Near and far parameters, false on a miss.
+__device__ bool hit_cylinder(d3 o, d3 d, double R, double &tn, double &tf)
+{
+    const double a = d.x * d.x + d.y * d.y;
+    const double b = 2.0 * (o.x * d.x + o.y * d.y);
+    const double c = o.x * o.x + o.y * o.y - R * R;
+    if (!(a > 0.0)) return false;
+    const double disc = b * b - 4.0 * a * c;
+    if (disc < 0.0) return false;
+    // numerically stable pair of roots
+    const double q = -0.5 * (b + copysign(sqrt(disc), b));
+    if (q == 0.0) return false;
+    const double r1 = q / a, r2 = c / q;
+    tn = fmin(r1, r2);
+    tf = fmax(r1, r2);
+    return true;
+}
+
+// Snell's law in vector form at point p of the cylinder of radius R, index n1 -> n2.
+// Returns false on total internal reflection; T = unpolarised Fresnel transmission.
+__device__ bool snell(d3 p, double R, d3 d, double n1, double n2, d3 &out, double &T)
+{
+    d3 n = {p.x / R, p.y / R, 0.0};
+    double cosi = -(n.x * d.x + n.y * d.y);
+    if (cosi < 0.0) { n = -1.0 * n; cosi = -cosi; }      // normal faces the incoming ray
+    const double eta = n1 / n2;
+    const double k = 1.0 - eta * eta * (1.0 - cosi * cosi);
+    if (k < 0.0) return false;
+    const double cost = sqrt(k);
+    out = eta * d + (eta * cosi - cost) * n;
+    const double rs = (n1 * cosi - n2 * cost) / (n1 * cosi + n2 * cost);
+    const double rp = (n1 * cost - n2 * cosi) / (n1 * cost + n2 * cosi);
+    T = 1.0 - 0.5 * (rs * rs + rp * rp);
+    return true;
+}
+
+__global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *__restrict__ B,
+                                int2 *__restrict__ J, unsigned long long *__restrict__ counters)
+{
+    const int64_t n_rays = (int64_t)P.nu * P.nv * P.M;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int u = (int)(r % P.nu);
+    const int v = (int)((r / P.nu) % P.nv);
+    const int a = (int)(r / ((int64_t)P.nu * P.nv));
+
+    A[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    B[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    J[r] = make_int2(0, 0);
+
+    // image point of the pixel in the best-focus plane y = 0
+    const d3 Q = {(u - 0.5 * (P.nu - 1)) * P.pu, 0.0, (v - 0.5 * (P.nv - 1)) * P.pv};
+    const double xi = P.pupil_xy[2 * a], et = P.pupil_xy[2 * a + 1];
+    d3 o, d;
+    if (P.telecentric) {
+        const double t = P.chief_only ? 0.0 : 1.0 / (2.0 * P.f_number);
+        d = {-xi * t, 1.0, -et * t};
+        d = (1.0 / sqrt(d.x * d.x + d.y * d.y + d.z * d.z)) * d;
+        const double back = (P.r_out + 1.0) / d.y;        // start in front of the vial
+        o = Q + (-back) * d;
+    } else {
+        const double D = P.chief_only ? 0.0 : P.pupil_mm / P.f_number;
+        o = {0.5 * D * xi, -P.pupil_mm, 0.5 * D * et};
+        d = {Q.x - o.x, Q.y - o.y, Q.z - o.z};
+        d = (1.0 / sqrt(d.x * d.x + d.y * d.y + d.z * d.z)) * d;
+    }
+    double tn, tf, T1, T2;
+    if (!hit_cylinder(o, d, P.r_out, tn, tf) || !(tn > 0.0)) return;         // misses the vial
+    const d3 p1 = o + tn * d;
+    d3 dg;
+    if (!snell(p1, P.r_out, d, P.n_out, P.n_glass, dg, T1)) return;
+    if (!hit_cylinder(p1, dg, P.r_in, tn, tf) || !(tn > 0.0)) return;       // wall only
+    const d3 e = p1 + tn * dg;
+    d3 dr;
+    if (!snell(e, P.r_in, dg, P.n_glass, P.n_resin, dr, T2)) return;        // TIR: dropped
+    // far side: chord of the circle from e along dr
+    const double ell = -2.0 * (e.x * dr.x + e.y * dr.y) / (dr.x * dr.x + dr.y * dr.y);
+    if (!(ell > 0.0)) return;
+    int K = (int)ceil(ell / P.ds - 1e-9);
+    if (K < 1) K = 1;
+    const double delta = ell / K;
+
+    // samples whose trilinear footprint reaches the grid in z: -1 < q_z < nz.  q_z is
+    // linear in j, so they form one run.  The expression is evaluated without fused
+    // multiply-adds so that it rounds like a plain FP64 evaluation.
+    const double zc = 0.5 * (P.nz - 1);
+    int jlo = K, jhi = 0;
+    for (int j = 0; j < K; ++j) {
+        const double s = __dmul_rn((double)j + 0.5, delta);
+        const double qz = __dadd_rn(__ddiv_rn(__dadd_rn(e.z, __dmul_rn(s, dr.z)), P.h), zc);
+        if (qz > -1.0 && qz < (double)P.nz) {
+            if (j < jlo) jlo = j;
+            jhi = j + 1;
+        }
+    }
+    if (jhi <= jlo) { jlo = 0; jhi = 0; }
+
+    const double inv_h = 1.0 / P.h;
+    A[r] = make_float4((float)(e.x * inv_h), (float)(e.y * inv_h), (float)(e.z * inv_h), (float)(delta * inv_h));
+    B[r] = make_float4((float)dr.x, (float)dr.y, (float)dr.z, (float)(T1 * T2 * delta / P.M));
+    J[r] = make_int2(jlo, jhi);
+    atomicAdd(&counters[0], 1ull);
+    atomicAdd(&counters[1], (unsigned long long)(jhi - jlo));
+}
+
+}  // namespace
+
+cudaError_t launch_raytable(const TraceParams &T, float4 *A, float4 *B, int2 *J,
+                            unsigned long long *counters, cudaStream_t s)
+{
+    const int64_t n = (int64_t)T.nu * T.nv * T.M;
+    const int threads = 128;
+    const int64_t blocks = (n + threads - 1) / threads;
+    raytable_kernel<<<(unsigned)blocks, threads, 0, s>>>(T, A, B, J, counters);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace vamrt

@@ -1,0 +1,358 @@
+// C-ABI entry points: argument validation, the projector handle, dispatch, and the
+// optimiser's host loop.  No exception or exit() crosses this boundary.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<uint64_t> g_launches{0};
+
+vamrt_status fail(vamrt_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+vamrt_status cuda_fail(cudaError_t e, const char *where)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(VAMRT_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(VAMRT_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);  \
+    } while (0)
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+vamrt_status validate(const vamrt_geometry *g)
+{
+    if (!g) return fail(VAMRT_EINVAL, "geometry is NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(VAMRT_EINVAL, "grid extents must be >= 1");
+    if (g->nu < 1 || g->nv < 1) return fail(VAMRT_EINVAL, "pixel array extents must be >= 1");
+    if (g->n_angles < 1 || g->n_angles > 65535) return fail(VAMRT_EINVAL, "n_angles must be in 1..65535");
+    if (g->nv > 4 * 65535) return fail(VAMRT_EINVAL, "nv too large");
+    if (!finite_pos(g->voxel_mm)) return fail(VAMRT_EINVAL, "voxel_mm must be finite and > 0");
+    if (!finite_pos(g->pixel_u_mm) || !finite_pos(g->pixel_v_mm))
+        return fail(VAMRT_EINVAL, "pixel pitches must be finite and > 0");
+    if (!(g->pupil_mm > 0.0) || isnan(g->pupil_mm)) return fail(VAMRT_EINVAL, "pupil_mm must be > 0 or INFINITY");
+    if (!(g->f_number > 0.0) || isnan(g->f_number)) return fail(VAMRT_EINVAL, "f_number must be > 0 or INFINITY");
+    if (g->rays_per_pixel < 1 || g->rays_per_pixel > 4096) return fail(VAMRT_EINVAL, "rays_per_pixel must be 1..4096");
+    if (!g->pupil_xy && g->rays_per_pixel != 1)
+        return fail(VAMRT_EINVAL, "pupil_xy may be NULL only with one ray per pixel");
+    if (g->pupil_xy)
+        for (int a = 0; a < g->rays_per_pixel; ++a) {
+            const double x = g->pupil_xy[2 * a], y = g->pupil_xy[2 * a + 1];
+            if (!isfinite(x) || !isfinite(y) || x * x + y * y > 1.0 + 1e-12)
+                return fail(VAMRT_EINVAL, "pupil sample %d is not in the unit disk", a);
+        }
+    if (!finite_pos(g->r_inner_mm)) return fail(VAMRT_EINVAL, "r_inner_mm must be finite and > 0");
+    if (!isfinite(g->wall_mm) || g->wall_mm < 0.0) return fail(VAMRT_EINVAL, "wall_mm must be finite and >= 0");
+    if (!finite_pos(g->n_outside) || !finite_pos(g->n_glass) || !finite_pos(g->n_resin))
+        return fail(VAMRT_EINVAL, "refractive indices must be finite and > 0");
+    if (!isfinite(g->mu_per_mm) || g->mu_per_mm < 0.0) return fail(VAMRT_EINVAL, "mu_per_mm must be finite and >= 0");
+    if (g->step_vox != 0.0 && (!finite_pos(g->step_vox) || g->step_vox > 8.0))
+        return fail(VAMRT_EINVAL, "step_vox must be in (0, 8] (0 = default 0.5)");
+    if (g->angles_rad)
+        for (int k = 0; k < g->n_angles; ++k)
+            if (!isfinite(g->angles_rad[k])) return fail(VAMRT_EINVAL, "angle %d is not finite", k);
+    const int nmin = g->nx < g->ny ? g->nx : g->ny;
+    if (!(g->r_inner_mm / g->voxel_mm < 0.5 * (nmin + 1) - 1e-6))
+        return fail(VAMRT_EINVAL, "grid (%d x %d voxels of %g mm) does not enclose the resin radius %g mm",
+                    g->nx, g->ny, g->voxel_mm, g->r_inner_mm);
+    const int64_t pad = (int64_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2);
+    if (pad >= (int64_t)1 << 31) return fail(VAMRT_EINVAL, "grid too large (padded voxels must fit int32)");
+    const int64_t rays = (int64_t)g->nu * g->nv * g->rays_per_pixel;
+    if (rays >= (int64_t)1 << 31) return fail(VAMRT_EINVAL, "too many rays");
+    // rays of up to ~2 R / step samples; keep j and (j + 1/2) exact in FP32
+    const double step = g->step_vox == 0.0 ? 0.5 : g->step_vox;
+    if (2.0 * g->r_inner_mm / (step * g->voxel_mm) > 4.0e6) return fail(VAMRT_EINVAL, "too many samples per ray");
+    return VAMRT_OK;
+}
+
+vamrt_status check_dtype(vamrt_dtype d)
+{
+    if (d != VAMRT_F32 && d != VAMRT_BF16) return fail(VAMRT_EINVAL, "unknown dtype %d", (int)d);
+    return VAMRT_OK;
+}
+
+void release(vamrt_projector *p)
+{
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->tabA);
+    cudaFree(p->tabB);
+    cudaFree(p->tabJ);
+    cudaFree(p->cs);
+    cudaFree(p->scratch);
+    cudaFree(p->red);
+    cudaFree(p->hist);
+    cudaFree(p->dmax);
+    if (p->host_err) cudaFreeHost(p->host_err);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+struct Guard {
+    vamrt_projector *p;
+    ~Guard() { release(p); }
+};
+
+}  // namespace
+
+namespace vamrt {
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace vamrt
+
+extern "C" {
+
+uint64_t vamrt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *vamrt_status_string(vamrt_status s)
+{
+    switch (s) {
+    case VAMRT_OK: return "ok";
+    case VAMRT_EINVAL: return "invalid argument";
+    case VAMRT_EUNSUPPORTED: return "unsupported";
+    case VAMRT_ECUDA: return "CUDA error";
+    case VAMRT_ENOMEM: return "out of device memory";
+    case VAMRT_NOT_CONVERGED: return "not converged";
+    case VAMRT_NUMERIC: return "numeric error (NaN/Inf or zero dose)";
+    }
+    return "unknown status";
+}
+
+const char *vamrt_last_error(void) { return g_err; }
+
+vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamrt_projector **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(VAMRT_EINVAL, "out is NULL");
+    *out = nullptr;
+    vamrt_status st = validate(geom);
+    if (st != VAMRT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    vamrt_projector *p = new (std::nothrow) vamrt_projector();
+    if (!p) return fail(VAMRT_ENOMEM, "host allocation failed");
+    Guard guard{p};
+    p->g = *geom;
+    p->g.pupil_xy = nullptr;
+    p->g.angles_rad = nullptr;
+    if (p->g.step_vox == 0.0) p->g.step_vox = 0.5;
+    const vamrt_geometry &g = p->g;
+    const int M = g.rays_per_pixel;
+
+    CK(cudaGetDevice(&p->device), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device), "cudaDeviceGetAttribute");
+    p->n_rays = (int64_t)g.nu * g.nv * M;
+    p->pad_elems = (int64_t)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+
+    CK(cudaMalloc(&p->tabA, sizeof(float4) * p->n_rays), "cudaMalloc(ray table)");
+    CK(cudaMalloc(&p->tabB, sizeof(float4) * p->n_rays), "cudaMalloc(ray table)");
+    CK(cudaMalloc(&p->tabJ, sizeof(int2) * p->n_rays), "cudaMalloc(ray table)");
+    CK(cudaMalloc(&p->cs, sizeof(float2) * g.n_angles), "cudaMalloc(angles)");
+    CK(cudaMalloc(&p->scratch, sizeof(float) * p->pad_elems), "cudaMalloc(scratch volume)");
+    CK(cudaMalloc(&p->red, sizeof(double) * (vamrt::kRedBlocks + 8)), "cudaMalloc(reduction)");
+    CK(cudaMalloc(&p->hist, sizeof(double) * vamrt::kMaxHistory), "cudaMalloc(history)");
+    CK(cudaMalloc(&p->dmax, sizeof(float) * 4), "cudaMalloc(dmax)");
+    CK(cudaMallocHost(&p->host_err, sizeof(double)), "cudaMallocHost");
+    p->device_bytes = (sizeof(float4) * 2 + sizeof(int2)) * (uint64_t)p->n_rays + sizeof(float2) * g.n_angles +
+                      sizeof(float) * (uint64_t)p->pad_elems;
+
+    // angle table, FP64 on the host then rounded
+    float2 *hcs = (float2 *)malloc(sizeof(float2) * g.n_angles);
+    if (!hcs) return fail(VAMRT_ENOMEM, "host allocation failed");
+    for (int k = 0; k < g.n_angles; ++k) {
+        const double th = geom->angles_rad ? geom->angles_rad[k] : 2.0 * M_PI * k / g.n_angles;
+        hcs[k] = make_float2((float)cos(th), (float)sin(th));
+    }
+    cudaError_t e = cudaMemcpyAsync(p->cs, hcs, sizeof(float2) * g.n_angles, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(hcs);
+    if (e != cudaSuccess) return cuda_fail(e, "angle table upload");
+
+    // pupil samples and counters in one temporary device block
+    const size_t pupil_bytes = sizeof(double) * 2 * M;
+    void *tmp = nullptr;
+    CK(cudaMalloc(&tmp, pupil_bytes + 2 * sizeof(unsigned long long)), "cudaMalloc(tmp)");
+    double *d_pupil = (double *)tmp;
+    unsigned long long *d_cnt = (unsigned long long *)((char *)tmp + pupil_bytes);
+    double chief[2] = {0.0, 0.0};
+    e = cudaMemcpyAsync(d_pupil, geom->pupil_xy ? geom->pupil_xy : chief, pupil_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s);
+
+    vamrt::TraceParams T;
+    T.pupil_xy = d_pupil;
+    T.nu = g.nu; T.nv = g.nv; T.M = M; T.nz = g.nz;
+    T.pu = g.pixel_u_mm; T.pv = g.pixel_v_mm;
+    T.pupil_mm = g.pupil_mm; T.f_number = g.f_number;
+    T.telecentric = isinf(g.pupil_mm) ? 1 : 0;
+    T.chief_only = isinf(g.f_number) ? 1 : 0;
+    T.r_in = g.r_inner_mm; T.r_out = g.r_inner_mm + g.wall_mm;
+    T.n_out = g.n_outside; T.n_glass = g.n_glass; T.n_resin = g.n_resin;
+    T.h = g.voxel_mm; T.ds = g.step_vox * g.voxel_mm;
+    if (e == cudaSuccess) e = vamrt::launch_raytable(T, p->tabA, p->tabB, p->tabJ, d_cnt, s);
+    unsigned long long cnt[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "ray table build");
+    p->rays_in_resin = (int64_t)cnt[0];
+    p->samples_per_angle = cnt[1];
+
+    vamrt::OpParams &P = p->op;
+    P.A = p->tabA; P.B = p->tabB; P.J = p->tabJ; P.cs = p->cs;
+    P.nu = g.nu; P.nv = g.nv; P.M = M; P.n_angles = g.n_angles;
+    P.px = g.nx + 2; P.py = g.ny + 2; P.pz = g.nz + 2;
+    P.cx = (float)(0.5 * (g.nx - 1) + 1.0);
+    P.cy = (float)(0.5 * (g.ny - 1) + 1.0);
+    P.cz = (float)(0.5 * (g.nz - 1) + 1.0);
+    P.neg_mu_vox_log2e = (float)(-g.mu_per_mm * g.voxel_mm * M_LOG2E);
+
+    guard.p = nullptr;
+    *out = p;
+    return VAMRT_OK;
+}
+
+void vamrt_destroy_projector(vamrt_projector *p) { release(p); }
+
+vamrt_status vamrt_get_info(const vamrt_projector *p, vamrt_info *info)
+{
+    if (!p || !info) return fail(VAMRT_EINVAL, "NULL argument");
+    info->n_rays = p->n_rays;
+    info->rays_in_resin = p->rays_in_resin;
+    info->samples_per_pass = p->samples_per_angle * (uint64_t)p->g.n_angles;
+    info->scratch_bytes = p->device_bytes;
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_sample_count(const vamrt_projector *p, uint64_t *n)
+{
+    if (!p || !n) return fail(VAMRT_EINVAL, "NULL argument");
+    *n = p->samples_per_angle * (uint64_t)p->g.n_angles;
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_adjoint(vamrt_projector *p, const void *vol, vamrt_dtype vol_dtype, void *proj,
+                           vamrt_dtype proj_dtype, uint32_t flags, void *stream)
+{
+    if (!p || !vol || !proj) return fail(VAMRT_EINVAL, "NULL argument");
+    if (check_dtype(vol_dtype) || check_dtype(proj_dtype)) return VAMRT_EINVAL;
+    if (flags & ~(VAMRT_ACCUMULATE | VAMRT_CLAMP_NONNEG)) return fail(VAMRT_EINVAL, "unknown flags 0x%x", flags);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(vamrt::launch_pad(p, vol, vol_dtype, s), "pad kernel");
+    CK(vamrt::launch_adjoint(p, vol_dtype, proj, proj_dtype, flags, s), "adjoint kernel");
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_forward_dose(vamrt_projector *p, const void *proj, vamrt_dtype proj_dtype, void *dose,
+                                vamrt_dtype dose_dtype, uint32_t flags, void *stream)
+{
+    if (!p || !proj || !dose) return fail(VAMRT_EINVAL, "NULL argument");
+    if (check_dtype(proj_dtype) || check_dtype(dose_dtype)) return VAMRT_EINVAL;
+    if (flags & ~VAMRT_ACCUMULATE) return fail(VAMRT_EINVAL, "unknown flags 0x%x", flags);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(vamrt::launch_forward(p, proj, proj_dtype, s), "forward kernel");
+    CK(vamrt::launch_unpad(p, dose, dose_dtype, flags, s), "unpad kernel");
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *model, void *proj, void *dose,
+                            const vamrt_opt_params *params, vamrt_opt_report *report, void *stream)
+{
+    if (!p || !target || !model || !proj || !dose || !params) return fail(VAMRT_EINVAL, "NULL argument");
+    if (params->max_iter < 1 || params->max_iter > vamrt::kMaxHistory)
+        return fail(VAMRT_EINVAL, "max_iter must be in 1..%d", vamrt::kMaxHistory);
+    if (params->check_every < 1) return fail(VAMRT_EINVAL, "check_every must be >= 1");
+    if (!(params->tol >= 0.0)) return fail(VAMRT_EINVAL, "tol must be >= 0");
+    if (check_dtype(params->proj_dtype) || check_dtype(params->dose_dtype)) return VAMRT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *fsum = p->red + vamrt::kRedBlocks;
+    // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double t_adj = 0.0, t_fwd = 0.0, t_upd = 0.0;
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() { for (int i = 0; i < 4; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+    } evguard{ev};
+    if (params->timing)
+        for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]), "cudaEventCreate");
+    CK(vamrt::launch_sum(p, target, fsum, s), "target sum");
+    int it = 0;
+    double err = NAN;
+    bool converged = false;
+    for (; it < params->max_iter;) {
+        if (params->timing) CK(cudaEventRecord(ev[0], s), "cudaEventRecord");
+        // g = max(0, A^T m)
+        CK(vamrt::launch_pad(p, model, VAMRT_F32, s), "pad kernel");
+        CK(vamrt::launch_adjoint(p, VAMRT_F32, proj, params->proj_dtype, VAMRT_CLAMP_NONNEG, s), "adjoint kernel");
+        if (params->timing) CK(cudaEventRecord(ev[1], s), "cudaEventRecord");
+        // d = A g (left in the scratch volume), then normalise, update, error
+        CK(vamrt::launch_forward(p, proj, params->proj_dtype, s), "forward kernel");
+        if (params->timing) CK(cudaEventRecord(ev[2], s), "cudaEventRecord");
+        CK(vamrt::launch_osmo_step(p, target, model, dose, params->dose_dtype, fsum, p->hist + it, s), "osmo step");
+        if (params->timing) {
+            CK(cudaEventRecord(ev[3], s), "cudaEventRecord");
+            CK(cudaEventSynchronize(ev[3]), "cudaEventSynchronize");
+            float ms[3];
+            for (int i = 0; i < 3; ++i) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]), "cudaEventElapsedTime");
+            t_adj += ms[0];
+            t_fwd += ms[1];
+            t_upd += ms[2];
+        }
+        ++it;
+        if (it % params->check_every == 0 || it == params->max_iter) {
+            CK(cudaMemcpyAsync(p->host_err, p->hist + it - 1, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+            err = *p->host_err;
+            if (!isfinite(err)) {
+                if (report) { report->iterations = it; report->final_error = err; }
+                return fail(VAMRT_NUMERIC, "dose error is not finite at iteration %d (zero or NaN dose)", it);
+            }
+            if (err < params->tol) { converged = true; break; }
+        }
+    }
+    if (report) {
+        report->iterations = it;
+        report->final_error = err;
+        report->adjoint_ms = t_adj;
+        report->forward_ms = t_fwd;
+        report->update_ms = t_upd;
+        if (report->error_history) {
+            CK(cudaMemcpyAsync(report->error_history, p->hist, sizeof(double) * it, cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+        }
+    }
+    return converged ? VAMRT_OK : VAMRT_NOT_CONVERGED;
+}
+
+vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4, int32_t *j2)
+{
+    if (!p) return fail(VAMRT_EINVAL, "NULL projector");
+    CK(cudaDeviceSynchronize(), "sync");
+    if (a4) CK(cudaMemcpy(a4, p->tabA, sizeof(float4) * p->n_rays, cudaMemcpyDeviceToHost), "copy");
+    if (b4) CK(cudaMemcpy(b4, p->tabB, sizeof(float4) * p->n_rays, cudaMemcpyDeviceToHost), "copy");
+    if (j2) CK(cudaMemcpy(j2, p->tabJ, sizeof(int2) * p->n_rays, cudaMemcpyDeviceToHost), "copy");
+    return VAMRT_OK;
+}
+
+}  // extern "C"

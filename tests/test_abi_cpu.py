@@ -1,0 +1,103 @@
+"""The C-ABI library loads, exports what include/vamrt.h declares, and rejects bad
+arguments on the host (no GPU needed, no compute call)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vamrt.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2211_03516_gb300 import build
+    build.build()
+    from paper_2211_03516_gb300 import vamrt
+    return vamrt.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vamrt_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for need in ("vamrt_make_projector", "vamrt_destroy_projector", "vamrt_adjoint", "vamrt_forward_dose",
+                 "vamrt_optimize", "vamrt_sample_count", "vamrt_status_string"):
+        assert need in syms
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [s for s in declared_symbols() if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_status_strings(L):
+    L.vamrt_status_string.restype = ctypes.c_char_p
+    assert L.vamrt_status_string(0) == b"ok"
+    assert L.vamrt_status_string(1) == b"invalid argument"
+    assert L.vamrt_status_string(99) == b"unknown status"
+
+
+def _spec(**kw):
+    from paper_2211_03516_gb300 import inputs as I
+    from paper_2211_03516_gb300.vamrt import GeometrySpec
+    w = I.TINY.scaled(**kw) if kw else I.TINY
+    return GeometrySpec.from_workload(w, I.pupil_samples("chief", 1))
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("nx", 0, "grid extents"),
+    ("nu", 0, "pixel array"),
+    ("voxel_mm", -0.2, "voxel_mm"),
+    ("voxel_mm", float("nan"), "voxel_mm"),
+    ("r_inner_mm", 0.0, "r_inner_mm"),
+    ("wall_mm", -1.0, "wall_mm"),
+    ("n_glass", 0.0, "refractive"),
+    ("mu_per_mm", -0.1, "mu_per_mm"),
+    ("pupil_mm", 0.0, "pupil_mm"),
+    ("f_number", -2.0, "f_number"),
+    ("r_inner_mm", 7.0, "enclose"),
+    ("step_vox", 100.0, "step_vox"),
+])
+def test_make_projector_rejects_bad_geometry(L, field, value, msg):
+    from paper_2211_03516_gb300 import vamrt
+    spec = _spec()
+    setattr(spec, field, value)
+    with pytest.raises(vamrt.VamrtError) as ei:
+        vamrt.vamrt_make_projector(spec)
+    assert ei.value.status == vamrt.VAMRT_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_make_projector_rejects_pupil_outside_disk(L):
+    from paper_2211_03516_gb300 import vamrt
+    spec = _spec()
+    spec.pupil_xy = np.array([[0.9, 0.9]])
+    with pytest.raises(vamrt.VamrtError, match="unit disk"):
+        vamrt.vamrt_make_projector(spec)
+
+
+def test_null_arguments_are_einval(L):
+    from paper_2211_03516_gb300 import vamrt
+    L.vamrt_last_error.restype = ctypes.c_char_p
+    assert L.vamrt_adjoint(None, None, 0, None, 0, 0, None) == vamrt.VAMRT_EINVAL
+    assert L.vamrt_forward_dose(None, None, 0, None, 0, 0, None) == vamrt.VAMRT_EINVAL
+    assert L.vamrt_optimize(None, None, None, None, None, None, None, None) == vamrt.VAMRT_EINVAL
+    assert L.vamrt_sample_count(None, None) == vamrt.VAMRT_EINVAL
+    assert L.vamrt_make_projector(None, None, None) == vamrt.VAMRT_EINVAL
+    L.vamrt_destroy_projector(None)  # no-op
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    from paper_2211_03516_gb300 import vamrt
+    monkeypatch.setattr(vamrt, "_lib", None)
+    monkeypatch.setattr(vamrt, "LIB_PATH", os.path.join(ROOT, "does-not-exist.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        vamrt.lib()

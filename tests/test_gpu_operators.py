@@ -1,0 +1,252 @@
+"""GPU parity of the CUDA operators (through the C ABI) against the FP64 oracle.
+
+Tolerance: 1e-5 relative L2 for the FP32 path; BF16 storage 2e-3 (dose) and 1e-3
+(projections / gradient), the bounds stated for the reduced-precision path.  Integer
+results (sample counts, per-ray sample ranges) are compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import osmo as OS
+from oracle import vam_oracle as O
+from paper_2211_03516_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+BF16_DOSE_TOL = 2e-3
+BF16_PROJ_TOL = 1e-3
+
+DEV = torch.device("cuda:0")
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def vamrt():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2211_03516_gb300 import vamrt as V
+    return V
+
+
+def gpu(x, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV, dtype)
+
+
+# A mid-size crop with the finite-etendue optics of the 256^3 workload (pupil 120 mm,
+# f/4, 4x4 stratified jitter, vial 12.5/1.2 mm, mu 0.03) on a coarser, ragged grid:
+# several warp/block tiles with ragged tails in u, v and every grid axis.
+MID_CROP = I.MID.scaled(nx=73, ny=72, nz=41, voxel_mm=0.36, nu=71, nv=45, pixel_u_mm=0.36, pixel_v_mm=0.36,
+                        n_angles=24)
+REFRACT_SMALL = I.TINY.scaled(nx=33, ny=34, nz=23, voxel_mm=0.4, nu=37, nv=23, pixel_u_mm=0.38,
+                              pixel_v_mm=0.41, n_angles=10, f_number=3.5, pupil_pattern="sunflower",
+                              rays_per_pixel=4, pupil_mm=60.0)
+
+
+def _oracle_table(w, pupil):
+    M = pupil.shape[0]
+    n = w.nu * w.nv * M
+    A = np.zeros((n, 4))
+    B = np.zeros((n, 4))
+    J = np.zeros((n, 2), np.int64)
+    h = w.voxel_mm
+    for a in range(M):
+        for v in range(w.nv):
+            for u in range(w.nu):
+                r = (a * w.nv + v) * w.nu + u
+                t = O.trace(w, pupil, u, v, a)
+                if t["status"] != 2:
+                    continue
+                delta = t["ell"] / t["k"]
+                A[r] = [*(t["e"] / h), delta / h]
+                B[r] = [*t["d2"], t["t1"] * t["t2"] * delta / M]
+                js = [j for j in range(t["k"])
+                      if -1 < (t["e"][2] + (j + 0.5) * delta * t["d2"][2]) / h + 0.5 * (w.nz - 1) < w.nz]
+                if js:
+                    J[r] = [js[0], js[-1] + 1]
+    return A, B, J
+
+
+@pytest.mark.parametrize("w", [REFRACT_SMALL, REFRACT_SMALL.scaled(pupil_mm=math.inf, f_number=5.0),
+                               I.TINY], ids=["nontelecentric", "telecentric", "tiny"])
+def test_ray_table_matches_oracle_trace(vamrt, w):
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    a4, b4, j2 = P.ray_table()
+    A, B, J = _oracle_table(w, pupil)
+    np.testing.assert_array_equal(j2, J)
+    np.testing.assert_allclose(a4, A, rtol=2e-7, atol=2e-6)
+    np.testing.assert_allclose(b4, B, rtol=2e-7, atol=2e-7)
+    assert P.sample_count() == O.sample_count(w, pupil)
+    assert P.info()["rays_in_resin"] == int(np.count_nonzero(J[:, 1] > J[:, 0]) + np.count_nonzero(
+        (J[:, 1] == J[:, 0]) & (B[:, 3] > 0)))
+
+
+@pytest.mark.parametrize("w", [I.TINY, REFRACT_SMALL, MID_CROP], ids=["tiny", "refract_small", "mid_crop"])
+def test_adjoint_and_dose_parity(vamrt, w):
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    V = I.random_volume(w, seed=11)
+    y_t = P.adjoint(gpu(f))
+    y_v = P.adjoint(gpu(V))
+    g = I.random_projections(w, seed=12)
+    d_g = P.forward_dose(gpu(g))
+    torch.cuda.synchronize()
+    assert rel_l2(y_t.cpu().numpy(), O.adjoint(w, f, pupil)) <= FP32_TOL
+    assert rel_l2(y_v.cpu().numpy(), O.adjoint(w, V, pupil)) <= FP32_TOL
+    assert rel_l2(d_g.cpu().numpy(), O.forward(w, g, pupil)) <= FP32_TOL
+
+
+def test_tiny_forward_of_projection_matches_oracle(vamrt):
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    y_ref = O.adjoint(w, f, pupil)
+    d = P.forward_dose(gpu(y_ref))
+    assert rel_l2(d.cpu().numpy(), O.forward(w, y_ref, pupil)) <= FP32_TOL
+
+
+def test_flags_accumulate_and_clamp(vamrt):
+    w = REFRACT_SMALL
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    V = I.random_volume(w, seed=3) - 0.5
+    y = P.adjoint(gpu(V))
+    y2 = P.adjoint(gpu(V), out=y.clone(), accumulate=True)
+    yc = P.adjoint(gpu(V), clamp_nonneg=True)
+    torch.testing.assert_close(y2, 2 * y, rtol=1e-6, atol=1e-6)
+    torch.testing.assert_close(yc, torch.clamp(y, min=0), rtol=0, atol=0)
+    assert (y < 0).any()
+    g = gpu(I.random_projections(w, seed=4))
+    d = P.forward_dose(g)
+    d2 = P.forward_dose(g, out=d.clone(), accumulate=True)
+    torch.testing.assert_close(d2, 2 * d, rtol=1e-6, atol=1e-6)
+
+
+def test_degenerate_cases(vamrt):
+    # one pixel, one angle, chief ray, no absorption, index matched: y = chord length
+    w = I.TINY.scaled(nu=1, nv=1, n_angles=1, n_glass=1.0, n_resin=1.0, mu_per_mm=0.0, pupil_mm=math.inf)
+    P = vamrt.Projector.from_workload(w, I.pupil_samples("chief", 1))
+    y = P.adjoint(torch.ones(w.vol_shape, device=DEV))
+    assert abs(float(y.item()) - 2 * w.r_inner_mm) < 2e-5
+    # zero input -> zero output, exactly
+    P2 = vamrt.Projector.from_workload(REFRACT_SMALL, I.workload_pupil(REFRACT_SMALL))
+    assert torch.count_nonzero(P2.adjoint(torch.zeros(REFRACT_SMALL.vol_shape, device=DEV))) == 0
+    assert torch.count_nonzero(P2.forward_dose(torch.zeros(REFRACT_SMALL.proj_shape, device=DEV))) == 0
+    # pixels wider than the vial: outer columns miss, their projections are exactly 0
+    w3 = REFRACT_SMALL.scaled(pixel_u_mm=0.6)
+    P3 = vamrt.Projector.from_workload(w3, I.workload_pupil(w3))
+    y3 = P3.adjoint(torch.ones(w3.vol_shape, device=DEV))
+    assert torch.all(y3[:, :, 0] == 0) and torch.all(y3[:, :, -1] == 0)
+    assert P3.info()["rays_in_resin"] < P3.info()["n_rays"]
+
+
+def test_bad_device_arguments(vamrt):
+    w = REFRACT_SMALL
+    P = vamrt.Projector.from_workload(w, I.workload_pupil(w))
+    with pytest.raises(ValueError):
+        P.adjoint(torch.zeros((3, 3, 3), device=DEV))
+    with pytest.raises(TypeError):
+        P.adjoint(torch.zeros(w.vol_shape))   # host tensor
+    L = vamrt.lib()
+    assert L.vamrt_adjoint(P.handle, None, 0, None, 0, 0, None) == vamrt.VAMRT_EINVAL
+    x = torch.zeros(w.vol_shape, device=DEV)
+    y = torch.zeros(w.proj_shape, device=DEV)
+    assert L.vamrt_adjoint(P.handle, x.data_ptr(), 7, y.data_ptr(), 0, 0, None) == vamrt.VAMRT_EINVAL
+    assert L.vamrt_adjoint(P.handle, x.data_ptr(), 0, y.data_ptr(), 0, 64, None) == vamrt.VAMRT_EINVAL
+
+
+def test_bf16_storage_error_bounds(vamrt):
+    w = MID_CROP
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    y_ref = O.adjoint(w, f, pupil)
+    d_ref = O.forward(w, y_ref, pupil)
+    y16 = P.adjoint(gpu(f, torch.bfloat16), proj_dtype=torch.bfloat16)
+    d16 = P.forward_dose(gpu(y_ref, torch.bfloat16), dose_dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    assert rel_l2(y16.float().cpu().numpy(), y_ref) <= BF16_PROJ_TOL
+    assert rel_l2(d16.float().cpu().numpy(), d_ref) <= BF16_DOSE_TOL
+
+
+def test_optimizer_matches_oracle_per_iteration(vamrt):
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0)
+    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                          n_iter=w.osmo_iters, tol=0.0)
+    assert res["iterations"] == w.osmo_iters and not res["converged"]
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
+    assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
+    assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL
+    assert rel_l2(res["model"].cpu().numpy(), m_ref) <= FP32_TOL
+
+
+def test_optimizer_stops_at_tolerance(vamrt):
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = gpu(I.make_target(w))
+    full = P.optimize(f, max_iter=6, tol=0.0)
+    tol = float(full["errors"][2]) * 1.0000001   # reached at the third iteration
+    res = P.optimize(f, max_iter=6, tol=tol)
+    assert res["converged"] and res["iterations"] == 3
+    res2 = P.optimize(f, max_iter=6, tol=tol, check_every=4)
+    assert res2["converged"] and res2["iterations"] == 4
+
+
+# ---- full-size workload (256^3, 360 angles, 256^2 pixels, 16 rays/pixel) -------------
+@pytest.fixture(scope="module")
+def mid_full(vamrt):
+    w = I.MID
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    return w, pupil, P
+
+
+def test_full_size_sample_count_and_adjoint_identity(vamrt, mid_full):
+    w, pupil, P = mid_full
+    n = P.sample_count()
+    assert 1.0e11 < n < 3.0e11
+    V = gpu(I.random_volume(w, seed=21))
+    g = gpu(I.random_projections(w, seed=22))
+    lhs = torch.sum(P.forward_dose(g).double() * V.double()).item()
+    rhs = torch.sum(g.double() * P.adjoint(V).double()).item()
+    assert abs(lhs - rhs) <= FP32_TOL * abs(rhs)
+
+
+def test_full_size_sampled_pixels_match_oracle(vamrt, mid_full):
+    w, pupil, P = mid_full
+    f = I.make_target(w)
+    y = P.adjoint(gpu(f)).cpu().numpy()
+    rng = np.random.default_rng(7)
+    # pixels whose rays cross the part, plus a few arbitrary ones
+    hit = np.argwhere(y > 0.05 * y.max())
+    pick = hit[rng.choice(len(hit), 40, replace=False)]
+    pick = np.concatenate([pick, np.stack([rng.integers(0, s, 8) for s in w.proj_shape], 1)])
+    ref = O.adjoint_pixels(w, f, pupil, [tuple(p) for p in pick])
+    got = y[tuple(pick.T)]
+    assert rel_l2(got, ref) <= FP32_TOL
+    big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    assert np.all(np.abs(got[big] - ref[big]) <= 1e-4 * np.abs(ref[big]))
+
+
+def test_full_size_sparse_dose_matches_oracle(vamrt, mid_full):
+    w, pupil, P = mid_full
+    g = I.sparse_projections(w, 48, seed=5)
+    d = P.forward_dose(gpu(g)).cpu().numpy()
+    ref = O.forward(w, g, pupil)
+    assert rel_l2(d, ref) <= FP32_TOL
