@@ -177,6 +177,8 @@ def run_gpu(args, rank, world):
     vamrt.lib()
 
     w = I.WORKLOADS[args.workload]
+    if args.angles:
+        w = w.scaled(n_angles=args.angles)
     pupil = I.workload_pupil(w)
     target_np = I.make_target(w)
     t0 = time.perf_counter()
@@ -303,6 +305,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vamrt", choices=["vamrt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--angles", type=int, default=0, help="override the angle count (small profiling cases)")
     ap.add_argument("--cpu-rows", type=int, default=48)
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")

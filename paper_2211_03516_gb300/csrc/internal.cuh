@@ -13,18 +13,31 @@ constexpr int kMaxHistory = 4096;
 // Partial-sum slots for the deterministic two-pass reductions.
 constexpr int kRedBlocks = 1024;
 
+// Operator tiling: a block owns kTileU x kTileV pixels of one angle and walks their rays
+// chunk by chunk along the projection axis (kChunkVox voxels of the theta = 0 frame's y
+// per chunk).  Each chunk's voxel footprint is staged in a shared-memory box of at most
+// kBoxFloats floats; a chunk whose box would not fit runs straight on global memory.
+constexpr int kTileU = 32;
+constexpr int kTileV = 8;
+constexpr int kThreads = kTileU * kTileV;
+constexpr int kChunkVox = 16;
+constexpr int kBoxFloats = 24 * 1024;
+
 // Per-launch constants of the two operators.  Positions are in padded index
-// coordinates: the scratch volume has one zero voxel of halo on every face, so the
-// voxel (i,j,k) of the caller's grid sits at (i+1, j+1, k+1).
+// coordinates: the scratch volume has a zero halo of one voxel on every face (and its
+// rows are padded to a multiple of 4 floats), so voxel (i,j,k) of the caller's grid
+// sits at (i+1, j+1, k+1).
 struct OpParams {
-    const float4 *A;      // (e_x, e_y, e_z, delta) in voxels, theta = 0 frame
+    const float4 *A;      // (e_x, e_y, e_z, delta) in voxels, theta = 0 frame, relative to the axis
     const float4 *B;      // (d_x, d_y, d_z, T1 T2 delta_mm / M)
     const int2 *J;        // [j_lo, j_hi) samples whose footprint reaches the grid
-    const float2 *cs;     // (cos theta_k, sin theta_k)
+    const double2 *cs;    // (cos theta_k, sin theta_k), FP64
     int nu, nv, M, n_angles;
-    int px, py, pz;       // padded extents
-    float cx, cy, cz;     // axis position in padded index coordinates
+    int nx, ny, nz;       // caller's grid
+    int px, py, pz;       // padded extents (px a multiple of 4)
+    double cx, cy, cz;    // axis position in padded index coordinates
     float neg_mu_vox_log2e;  // -mu h log2(e): attenuation = exp2(this * s_vox)
+    float y0;             // start of chunk 0 on the theta = 0 frame's y axis, voxels
 };
 
 // Per-ray constants of the FP64 tracer.
@@ -51,8 +64,8 @@ struct vamrt_projector {
     float4 *tabA;
     float4 *tabB;
     int2 *tabJ;
-    float2 *cs;
-    float *scratch;            // padded (nx+2)(ny+2)(nz+2) FP32 volume
+    double2 *cs;
+    float *scratch;            // padded FP32 volume, pad_elems floats
     int64_t pad_elems;
     double *red;               // kRedBlocks partials + scalars
     double *hist;              // kMaxHistory errors
@@ -71,6 +84,7 @@ cudaError_t launch_raytable(const TraceParams &T, float4 *A, float4 *B, int2 *J,
                             unsigned long long *counters, cudaStream_t s);
 
 // operators.cu
+cudaError_t operators_init();
 cudaError_t launch_pad(const vamrt_projector *p, const void *vol, vamrt_dtype dt, cudaStream_t s);
 cudaError_t launch_adjoint(const vamrt_projector *p, vamrt_dtype vol_dt, void *proj, vamrt_dtype proj_dt,
                            uint32_t flags, cudaStream_t s);

@@ -1,44 +1,80 @@
-// The two hot operators: projection (adjoint, gather) and dose (forward, scatter).
+// The two hot operators: projection (adjoint A^T, a gather) and dose (forward A, a
+// scatter), sharing one tiled traversal.
 //
-// Work mapping (both operators): one thread per pixel and angle; the 32 lanes of a warp
-// are 32 adjacent pixels u of one row v, so at every step their samples lie side by
-// side in the volume and their voxel fetches / reductions fall in few cache lines.  A
-// block is 32 x 4 pixels of one angle; blocks of one angle are launched together so the
-// volume region they sweep stays resident in L1/L2.  Each thread walks the aperture
-// samples of its pixel in turn and, along each ray, the midpoint samples
-// s_j = (j + 1/2) delta.  Per ray, the entry point and direction are rotated into the
-// vial frame once (FP32), so a sample costs three FMAs for its position, one exp2 for
-// Beer-Lambert, the trilinear weights (Sec. 2.2) and 8 voxel accesses.
+// Work mapping.  A block owns 32 x 8 pixels (u fastest, one warp per pixel row) of one
+// angle; a thread owns one pixel and walks its aperture rays one after the other.  For a
+// given aperture sample the block's 256 rays form a coherent bundle, so the block
+// advances them together in chunks: chunk c holds the samples whose position on the
+// theta = 0 frame's y axis (the projection direction) lies in [y0 + 16 c, y0 + 16 (c+1))
+// voxels.  For each chunk the block
+//   1. takes the union of its rays' trilinear footprints (an axis-aligned box of voxels,
+//      x rounded out to 16-byte groups),
+//   2. adjoint: stages that box of the volume into shared memory with 16-byte loads;
+//      forward: zeroes a shared-memory accumulator of that box,
+//   3. walks the samples: 8 shared-memory reads (adjoint) or 8 shared-memory atomic adds
+//      (forward) per sample,
+//   4. forward: flushes the box with 16-byte vector reductions (red.global.add.v4.f32)
+//      into the FP32 dose accumulator, skipping all-zero groups.
+// The global memory system thus sees about one coalesced access per box voxel per chunk
+// instead of 8 scattered accesses per sample, and the dose accumulator receives sums of
+// about ten samples per voxel and chunk instead of single samples.  A chunk whose box
+// does not fit in shared memory (unusually divergent bundles) is walked directly on
+// global memory with the same arithmetic.
 //
-// The caller's volume is first copied into a scratch volume with one voxel of zero halo,
-// which removes every per-corner bounds test from the inner loop (zero padding outside
-// the grid); index clamps remain only as a guard that never binds for valid geometry.
+// Sample positions.  Per ray and angle the entry point and direction are rotated into the
+// vial frame in FP64 and converted to Q32.32 fixed point; sample j sits at
+// q0 + j * step exactly (integer adds), so positions carry no accumulated rounding and the
+// footprint of a run of samples is bounded by the cells of its two end samples.
+//
+// The caller's volume is copied into a scratch volume with one voxel of zero halo (zero
+// padding outside the grid, Sec. 2.2's weights then need no bounds tests); index clamps
+// remain only as a guard that never binds for valid geometry.
 #include <cuda_bf16.h>
+#include <limits.h>
 
 #include "internal.cuh"
 
 namespace vamrt {
 namespace {
 
-__device__ __forceinline__ float ld_val(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p)
-{
-    const unsigned short raw = __ldg(reinterpret_cast<const unsigned short *>(p));
-    return __uint_as_float(((unsigned)raw) << 16);
-}
+constexpr double kFix = 4294967296.0;  // 2^32
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ void st_val(float *p, float x) { *p = x; }
 __device__ __forceinline__ void st_val(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
-__device__ __forceinline__ float ld_plain(const float *p) { return *p; }
-__device__ __forceinline__ float ld_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+
+// four consecutive voxels starting at a 4-aligned element (16 B for FP32, 8 B for BF16)
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p)
+{
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+    return make_float4(bf16_lo(w.x), bf16_hi(w.x), bf16_lo(w.y), bf16_hi(w.y));
+}
+__device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld1(const __nv_bfloat16 *p)
+{
+    return __uint_as_float(((unsigned)__ldg(reinterpret_cast<const unsigned short *>(p))) << 16);
+}
+
+__device__ __forceinline__ void red_v4(float *p, float4 v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
 
 // ---------------------------------------------------------------------------------
-// halo copy: scratch[zp][yp][xp] = vol[zp-1][yp-1][xp-1] inside, 0 on the halo
+// halo copy: scratch[zp][yp][xp] = vol[zp-1][yp-1][xp-1] inside, 0 elsewhere
 // ---------------------------------------------------------------------------------
 template <typename VT>
-__global__ void pad_kernel(const VT *__restrict__ vol, VT *__restrict__ out, int nx, int ny, int nz,
-                           int64_t total)
+__global__ void pad_kernel(const VT *__restrict__ vol, VT *__restrict__ out, int nx, int ny, int nz, int px,
+                           int py, int64_t total)
 {
-    const int px = nx + 2, py = ny + 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int xp = (int)(i % px);
@@ -53,145 +89,335 @@ __global__ void pad_kernel(const VT *__restrict__ vol, VT *__restrict__ out, int
 
 // dose[z][y][x] (+)= scratch[z+1][y+1][x+1]
 template <typename DT>
-__global__ void unpad_kernel(const float *__restrict__ acc, DT *__restrict__ dose, int nx, int ny, int nz,
-                             int accumulate)
+__global__ void unpad_kernel(const float *__restrict__ acc, DT *__restrict__ dose, int nx, int ny, int nz, int px,
+                             int py, int accumulate)
 {
     const int64_t total = (int64_t)nx * ny * nz;
-    const int px = nx + 2, py = ny + 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx);
         const int y = (int)((i / nx) % ny);
         const int z = (int)(i / ((int64_t)nx * ny));
         float val = acc[((int64_t)(z + 1) * py + (y + 1)) * px + (x + 1)];
-        if (accumulate) val += ld_plain(dose + i);
+        if (accumulate) val += to_f(dose[i]);
         st_val(dose + i, val);
     }
 }
 
-// Per-ray setup shared by both operators: rotated entry point and per-sample step in
-// padded index coordinates, and the log2 attenuation per sample.
-struct RaySetup {
-    float qx, qy, qz;     // position of "sample -1/2" (the entry point)
-    float sx, sy, sz;     // advance per sample
-    float att;            // log2 of the Beer-Lambert factor per sample
+// ---------------------------------------------------------------------------------
+// per-ray state
+// ---------------------------------------------------------------------------------
+struct Ray {
+    long long q0x, q0y, q0z;  // Q32.32 position of sample 0
+    long long sx, sy, sz;     // Q32.32 advance per sample
+    float att;                // log2 of the Beer-Lambert factor per sample
+    float w;                  // T1 T2 delta_mm / M
+    float ey, dy;             // theta = 0 frame: y(j) = ey + (j + 1/2) dy (voxels)
+    int jlo, jhi;
 };
 
-__device__ __forceinline__ RaySetup ray_setup(const OpParams &P, float4 A, float4 B, float2 cs)
+__device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 cs, Ray &R)
 {
-    RaySetup R;
-    R.qx = P.cx + (cs.x * A.x - cs.y * A.y);
-    R.qy = P.cy + (cs.y * A.x + cs.x * A.y);
-    R.qz = P.cz + A.z;
-    R.sx = (cs.x * B.x - cs.y * B.y) * A.w;
-    R.sy = (cs.y * B.x + cs.x * B.y) * A.w;
-    R.sz = B.z * A.w;
+    const int2 J = P.J[r];
+    if (J.x >= J.y) return false;
+    const float4 A = P.A[r], B = P.B[r];
+    const double c = cs.x, s = cs.y;
+    const double ex = A.x, ey = A.y, dl = A.w;
+    const double stx = (c * (double)B.x - s * (double)B.y) * dl;
+    const double sty = (s * (double)B.x + c * (double)B.y) * dl;
+    const double stz = (double)B.z * dl;
+    // sample 0 sits half a step inside the entry point
+    const double q0x = P.cx + (c * ex - s * ey) + 0.5 * stx;
+    const double q0y = P.cy + (s * ex + c * ey) + 0.5 * sty;
+    const double q0z = P.cz + (double)A.z + 0.5 * stz;
+    R.q0x = __double2ll_rn(q0x * kFix);
+    R.q0y = __double2ll_rn(q0y * kFix);
+    R.q0z = __double2ll_rn(q0z * kFix);
+    R.sx = __double2ll_rn(stx * kFix);
+    R.sy = __double2ll_rn(sty * kFix);
+    R.sz = __double2ll_rn(stz * kFix);
     R.att = P.neg_mu_vox_log2e * A.w;
-    return R;
+    R.w = B.w;
+    R.ey = A.y;
+    R.dy = A.w * B.y;
+    R.jlo = J.x;
+    R.jhi = J.y;
+    return true;
+}
+
+// rays that hardly advance along y are taken whole in their first chunk
+constexpr float kMinDy = 1e-4f;
+
+__device__ __forceinline__ int chunk_of(const OpParams &P, const Ray &R, int j)
+{
+    const float y = fmaf((float)j + 0.5f, R.dy, R.ey);
+    return (int)floorf((y - P.y0) * (1.0f / kChunkVox));
+}
+
+// first sample whose y lies at or beyond the start of chunk c (monotone in c)
+__device__ __forceinline__ int chunk_start(const OpParams &P, const Ray &R, int c)
+{
+    const float yc = P.y0 + (float)(c * kChunkVox);
+    const float j = ceilf((yc - R.ey) / R.dy - 0.5f);
+    return (int)fminf(fmaxf(j, (float)R.jlo), (float)R.jhi);
+}
+
+__device__ __forceinline__ void chunk_samples(const OpParams &P, const Ray &R, int c, int cmin, int cmax, int &jl,
+                                              int &jh)
+{
+    if (!(R.dy > kMinDy)) {
+        jl = (c == cmin) ? R.jlo : R.jhi;
+        jh = R.jhi;
+        return;
+    }
+    jl = (c == cmin) ? R.jlo : chunk_start(P, R, c);
+    jh = (c == cmax) ? R.jhi : chunk_start(P, R, c + 1);
 }
 
 struct Cell {
-    int base;             // linear padded index of corner (0,0,0)
-    float fx, fy, fz;     // fractional position inside the cell
+    int ix, iy, iz;
+    float fx, fy, fz;
 };
 
-__device__ __forceinline__ Cell locate(const OpParams &P, float qx, float qy, float qz)
+__device__ __forceinline__ float frac32(long long q)
 {
-    const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+    // top 23 fraction bits as a float in [0, 1), exactly
+    return __uint_as_float(0x3f800000u | ((unsigned)q >> 9)) - 1.0f;
+}
+
+__device__ __forceinline__ Cell cell_of(const OpParams &P, long long qx, long long qy, long long qz)
+{
     Cell c;
-    c.fx = qx - flx;
-    c.fy = qy - fly;
-    c.fz = qz - flz;
-    const int ix = min(max((int)flx, 0), P.px - 2);
-    const int iy = min(max((int)fly, 0), P.py - 2);
-    const int iz = min(max((int)flz, 0), P.pz - 2);
-    c.base = (iz * P.py + iy) * P.px + ix;
+    c.ix = min(max((int)(qx >> 32), 0), P.px - 2);
+    c.iy = min(max((int)(qy >> 32), 0), P.py - 2);
+    c.iz = min(max((int)(qz >> 32), 0), P.pz - 2);
+    c.fx = frac32(qx);
+    c.fy = frac32(qy);
+    c.fz = frac32(qz);
     return c;
 }
 
-// ---------------------------------------------------------------------------------
-// projection (adjoint): proj[k][v][u] = sum_a W_a sum_j exp(-mu s_j) trilinear(vol, x_j)
-// ---------------------------------------------------------------------------------
-template <typename VT, typename PT>
-__global__ void __launch_bounds__(128) adjoint_kernel(OpParams P, const VT *__restrict__ vol,
-                                                      PT *__restrict__ proj, uint32_t flags)
+// Addressing of a sample's corner (0,0,0): shared-memory box or global padded volume.
+struct BoxAddr {
+    int sx, sxy, off;
+    __device__ __forceinline__ int operator()(const Cell &c) const { return c.iz * sxy + c.iy * sx + c.ix - off; }
+};
+
+// Voxel sources for the gather: the global padded volume (read-only path) or the
+// shared-memory box.
+template <typename VT>
+struct GlobalSrc {
+    const VT *p;
+    __device__ __forceinline__ float operator()(int i) const { return ld1(p + i); }
+};
+struct SmemSrc {
+    const float *p;
+    __device__ __forceinline__ float operator()(int i) const { return p[i]; }
+};
+
+template <class Src, class Addr>
+__device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, int jl, int jh, const Src &src,
+                                             const Addr &addr)
 {
-    const int u = blockIdx.x * 32 + threadIdx.x;
-    const int v = blockIdx.y * 4 + threadIdx.y;
-    const int k = blockIdx.z;
-    if (u >= P.nu || v >= P.nv) return;
-    const float2 cs = P.cs[k];
-    const int sxy = P.px * P.py;
+    long long qx = R.q0x + (long long)jl * R.sx;
+    long long qy = R.q0y + (long long)jl * R.sy;
+    long long qz = R.q0z + (long long)jl * R.sz;
+    const int sx = addr.sx, sxy = addr.sxy;
     float acc = 0.f;
-    for (int a = 0; a < P.M; ++a) {
-        const int64_t r = ((int64_t)a * P.nv + v) * P.nu + u;
-        const int2 J = P.J[r];
-        if (J.x >= J.y) continue;
-        const RaySetup R = ray_setup(P, P.A[r], P.B[r], cs);
-        float ray = 0.f;
-        for (int j = J.x; j < J.y; ++j) {
-            const float t = (float)j + 0.5f;
-            const Cell c = locate(P, fmaf(t, R.sx, R.qx), fmaf(t, R.sy, R.qy), fmaf(t, R.sz, R.qz));
-            const VT *p = vol + c.base;
-            const float v000 = ld_val(p), v100 = ld_val(p + 1);
-            const float v010 = ld_val(p + P.px), v110 = ld_val(p + P.px + 1);
-            const float v001 = ld_val(p + sxy), v101 = ld_val(p + sxy + 1);
-            const float v011 = ld_val(p + sxy + P.px), v111 = ld_val(p + sxy + P.px + 1);
-            const float x00 = fmaf(c.fx, v100 - v000, v000);
-            const float x10 = fmaf(c.fx, v110 - v010, v010);
-            const float x01 = fmaf(c.fx, v101 - v001, v001);
-            const float x11 = fmaf(c.fx, v111 - v011, v011);
-            const float y0 = fmaf(c.fy, x10 - x00, x00);
-            const float y1 = fmaf(c.fy, x11 - x01, x01);
-            const float val = fmaf(c.fz, y1 - y0, y0);
-            ray = fmaf(exp2f(t * R.att), val, ray);
-        }
-        acc = fmaf(P.B[r].w, ray, acc);
+    for (int j = jl; j < jh; ++j) {
+        const Cell c = cell_of(P, qx, qy, qz);
+        const int b = addr(c);
+        const float v000 = src(b), v100 = src(b + 1);
+        const float v010 = src(b + sx), v110 = src(b + sx + 1);
+        const float v001 = src(b + sxy), v101 = src(b + sxy + 1);
+        const float v011 = src(b + sxy + sx), v111 = src(b + sxy + sx + 1);
+        const float x00 = fmaf(c.fx, v100 - v000, v000);
+        const float x10 = fmaf(c.fx, v110 - v010, v010);
+        const float x01 = fmaf(c.fx, v101 - v001, v001);
+        const float x11 = fmaf(c.fx, v111 - v011, v011);
+        const float y0 = fmaf(c.fy, x10 - x00, x00);
+        const float y1 = fmaf(c.fy, x11 - x01, x01);
+        const float val = fmaf(c.fz, y1 - y0, y0);
+        acc = fmaf(exp2f(R.att * ((float)j + 0.5f)), val, acc);
+        qx += R.sx;
+        qy += R.sy;
+        qz += R.sz;
     }
-    PT *out = proj + ((int64_t)k * P.nv + v) * P.nu + u;
-    if (flags & VAMRT_ACCUMULATE) acc += ld_plain(out);
-    if (flags & VAMRT_CLAMP_NONNEG) acc = fmaxf(acc, 0.f);
-    st_val(out, acc);
+    return acc;
+}
+
+template <class Addr>
+__device__ __forceinline__ void walk_scatter(const OpParams &P, const Ray &R, int jl, int jh, float wray, float *dst,
+                                             const Addr &addr)
+{
+    long long qx = R.q0x + (long long)jl * R.sx;
+    long long qy = R.q0y + (long long)jl * R.sy;
+    long long qz = R.q0z + (long long)jl * R.sz;
+    const int sx = addr.sx, sxy = addr.sxy;
+    for (int j = jl; j < jh; ++j) {
+        const Cell c = cell_of(P, qx, qy, qz);
+        float *p = dst + addr(c);
+        const float w = wray * exp2f(R.att * ((float)j + 0.5f));
+        const float wz1 = w * c.fz, wz0 = w - wz1;
+        const float w01 = wz0 * c.fy, w00 = wz0 - w01;
+        const float w11 = wz1 * c.fy, w10 = wz1 - w11;
+        const float a100 = w00 * c.fx, a110 = w01 * c.fx, a101 = w10 * c.fx, a111 = w11 * c.fx;
+        atomicAdd(p, w00 - a100);
+        atomicAdd(p + 1, a100);
+        atomicAdd(p + sx, w01 - a110);
+        atomicAdd(p + sx + 1, a110);
+        atomicAdd(p + sxy, w10 - a101);
+        atomicAdd(p + sxy + 1, a101);
+        atomicAdd(p + sxy + sx, w11 - a111);
+        atomicAdd(p + sxy + sx + 1, a111);
+        qx += R.sx;
+        qy += R.sy;
+        qz += R.sz;
+    }
 }
 
 // ---------------------------------------------------------------------------------
-// dose (forward): scratch[corner] += proj[k][v][u] W_a exp(-mu s_j) w_corner
+// the tiled traversal, adjoint (FWD = false) or forward (FWD = true)
 // ---------------------------------------------------------------------------------
-template <typename PT>
-__global__ void __launch_bounds__(128) forward_kernel(OpParams P, const PT *__restrict__ proj,
-                                                      float *__restrict__ acc)
+template <bool FWD, typename VT, typename PT>
+__global__ void __launch_bounds__(kThreads, 2)
+    tiled_kernel(const OpParams P, const VT *__restrict__ vol, PT *__restrict__ proj, float *__restrict__ acc,
+                 uint32_t flags)
 {
-    const int u = blockIdx.x * 32 + threadIdx.x;
-    const int v = blockIdx.y * 4 + threadIdx.y;
+    extern __shared__ float box[];
+    __shared__ int s_box[3][6];   // per chunk (rotating): min x,y,z and max x,y,z of the footprint
+    __shared__ int s_rng[3][2];   // per aperture sample (rotating): first and last chunk
+
+    const int tid = threadIdx.y * kTileU + threadIdx.x;
+    const int u = blockIdx.x * kTileU + threadIdx.x;
+    const int v = blockIdx.y * kTileV + threadIdx.y;
     const int k = blockIdx.z;
-    if (u >= P.nu || v >= P.nv) return;
-    const float g = ld_plain(proj + ((int64_t)k * P.nv + v) * P.nu + u);
-    if (g == 0.f) return;                      // adds exactly zero
-    const float2 cs = P.cs[k];
-    const int sxy = P.px * P.py;
+    const bool valid = u < P.nu && v < P.nv;
+    const double2 cs = P.cs[k];
+    const int64_t pix_index = ((int64_t)k * P.nv + v) * P.nu + u;
+
+    float g = 0.f;
+    if (FWD && valid) g = to_f(proj[pix_index]);
+    if (tid < 18) s_box[tid / 6][tid % 6] = (tid % 6 < 3) ? INT_MAX : INT_MIN;
+    if (tid < 6) s_rng[tid / 2][tid % 2] = (tid % 2 == 0) ? INT_MAX : INT_MIN;
+    __syncthreads();
+
+    const int pxy = P.px * P.py;
+    float pix = 0.f;
+    int n_chunk = 0;
     for (int a = 0; a < P.M; ++a) {
-        const int64_t r = ((int64_t)a * P.nv + v) * P.nu + u;
-        const int2 J = P.J[r];
-        if (J.x >= J.y) continue;
-        const RaySetup R = ray_setup(P, P.A[r], P.B[r], cs);
-        const float gw = g * P.B[r].w;
-        for (int j = J.x; j < J.y; ++j) {
-            const float t = (float)j + 0.5f;
-            const Cell c = locate(P, fmaf(t, R.sx, R.qx), fmaf(t, R.sy, R.qy), fmaf(t, R.sz, R.qz));
-            const float w = gw * exp2f(t * R.att);
-            const float wz1 = w * c.fz, wz0 = w - wz1;
-            const float w01 = wz0 * c.fy, w00 = wz0 - w01;
-            const float w11 = wz1 * c.fy, w10 = wz1 - w11;
-            float *p = acc + c.base;
-            atomicAdd(p, w00 - w00 * c.fx);
-            atomicAdd(p + 1, w00 * c.fx);
-            atomicAdd(p + P.px, w01 - w01 * c.fx);
-            atomicAdd(p + P.px + 1, w01 * c.fx);
-            atomicAdd(p + sxy, w10 - w10 * c.fx);
-            atomicAdd(p + sxy + 1, w10 * c.fx);
-            atomicAdd(p + sxy + P.px, w11 - w11 * c.fx);
-            atomicAdd(p + sxy + P.px + 1, w11 * c.fx);
+        const int ra = a % 3;
+        Ray R;
+        bool active = valid && (!FWD || g != 0.f);
+        if (active) active = ray_begin(P, ((int64_t)a * P.nv + v) * P.nu + u, cs, R);
+        int cf = INT_MAX, cl = INT_MIN;
+        if (active) {
+            cf = chunk_of(P, R, R.jlo);
+            cl = (R.dy > kMinDy) ? chunk_of(P, R, R.jhi - 1) : cf;
+            if (cl < cf) cl = cf;
         }
+        cf = __reduce_min_sync(kFull, cf);
+        cl = __reduce_max_sync(kFull, cl);
+        if (threadIdx.x == 0 && cf <= cl) {
+            atomicMin(&s_rng[ra][0], cf);
+            atomicMax(&s_rng[ra][1], cl);
+        }
+        __syncthreads();
+        const int cmin = s_rng[ra][0], cmax = s_rng[ra][1];
+        if (tid == 0) {
+            s_rng[(a + 2) % 3][0] = INT_MAX;
+            s_rng[(a + 2) % 3][1] = INT_MIN;
+        }
+        const float wray = FWD ? g * (active ? R.w : 0.f) : 0.f;
+        float ray_acc = 0.f;
+
+        for (int c = cmin; c <= cmax; ++c) {
+            const int rb = n_chunk % 3;
+            ++n_chunk;
+            int jl = 0, jh = 0;
+            if (active) chunk_samples(P, R, c, cmin, cmax, jl, jh);
+            int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+            if (jl < jh) {
+                const Cell c0 = cell_of(P, R.q0x + (long long)jl * R.sx, R.q0y + (long long)jl * R.sy,
+                                        R.q0z + (long long)jl * R.sz);
+                const long long j1 = jh - 1;
+                const Cell c1 = cell_of(P, R.q0x + j1 * R.sx, R.q0y + j1 * R.sy, R.q0z + j1 * R.sz);
+                lo[0] = min(c0.ix, c1.ix); hi[0] = max(c0.ix, c1.ix) + 1;
+                lo[1] = min(c0.iy, c1.iy); hi[1] = max(c0.iy, c1.iy) + 1;
+                lo[2] = min(c0.iz, c1.iz); hi[2] = max(c0.iz, c1.iz) + 1;
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = __reduce_min_sync(kFull, lo[d]);
+                hi[d] = __reduce_max_sync(kFull, hi[d]);
+            }
+            if (threadIdx.x == 0 && lo[0] != INT_MAX) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    atomicMin(&s_box[rb][d], lo[d]);
+                    atomicMax(&s_box[rb][3 + d], hi[d]);
+                }
+            }
+            __syncthreads();
+            const int bx0 = s_box[rb][0] & ~3, by0 = s_box[rb][1], bz0 = s_box[rb][2];
+            const int hx = s_box[rb][3], hy = s_box[rb][4], hz = s_box[rb][5];
+            if (tid == 0) {
+                const int nb = (rb + 2) % 3;
+                s_box[nb][0] = s_box[nb][1] = s_box[nb][2] = INT_MAX;
+                s_box[nb][3] = s_box[nb][4] = s_box[nb][5] = INT_MIN;
+            }
+            if (hx == INT_MIN) continue;                      // no samples in this chunk
+            const int ex = ((hx + 4) & ~3) - bx0;             // x extent, a multiple of 4
+            const int ey = hy + 1 - by0, ez = hz + 1 - bz0;
+            const int sx = ex + 1, sxy = sx * ey;             // odd row stride: no bank conflicts
+            const int ex4 = ex >> 2;
+            const int n4 = ex4 * ey * ez;
+            if ((long long)sxy * ez <= kBoxFloats) {
+                if (!FWD) {
+                    for (int i = tid; i < n4; i += kThreads) {
+                        const int x4 = i % ex4, t = i / ex4;
+                        const int yy = t % ey, zz = t / ey;
+                        const float4 q = ld4(vol + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
+                        float *b = box + zz * sxy + yy * sx + 4 * x4;
+                        b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
+                    }
+                } else {
+                    for (int i = tid; i < sxy * ez; i += kThreads) box[i] = 0.f;
+                }
+                __syncthreads();
+                const BoxAddr addr{sx, sxy, bz0 * sxy + by0 * sx + bx0};
+                if (jl < jh) {
+                    if (!FWD)
+                        ray_acc += walk_gather(P, R, jl, jh, SmemSrc{box}, addr);
+                    else
+                        walk_scatter(P, R, jl, jh, wray, box, addr);
+                }
+                if (FWD) {
+                    __syncthreads();
+                    for (int i = tid; i < n4; i += kThreads) {
+                        const int x4 = i % ex4, t = i / ex4;
+                        const int yy = t % ey, zz = t / ey;
+                        const float *b = box + zz * sxy + yy * sx + 4 * x4;
+                        const float4 q = make_float4(b[0], b[1], b[2], b[3]);
+                        if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f)
+                            red_v4(acc + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4, q);
+                    }
+                }
+            } else if (jl < jh) {
+                const BoxAddr addr{P.px, pxy, 0};
+                if (!FWD)
+                    ray_acc += walk_gather(P, R, jl, jh, GlobalSrc<VT>{vol}, addr);
+                else
+                    walk_scatter(P, R, jl, jh, wray, acc, addr);
+            }
+        }
+        if (!FWD && active) pix = fmaf(R.w, ray_acc, pix);
+    }
+    if (!FWD && valid) {
+        PT *out = proj + pix_index;
+        if (flags & VAMRT_ACCUMULATE) pix += to_f(*out);
+        if (flags & VAMRT_CLAMP_NONNEG) pix = fmaxf(pix, 0.f);
+        st_val(out, pix);
     }
 }
 
@@ -204,19 +430,36 @@ inline unsigned grid_for(const vamrt_projector *p, int64_t n, int threads)
     return (unsigned)want;
 }
 
-inline dim3 op_grid(const OpParams &P) { return dim3((P.nu + 31) / 32, (P.nv + 3) / 4, P.n_angles); }
+inline dim3 op_grid(const OpParams &P)
+{
+    return dim3((P.nu + kTileU - 1) / kTileU, (P.nv + kTileV - 1) / kTileV, P.n_angles);
+}
+
+constexpr size_t kSmem = sizeof(float) * kBoxFloats;
+
+template <bool FWD, typename VT, typename PT>
+cudaError_t launch_tiled(const OpParams &P, const VT *vol, PT *proj, float *acc, uint32_t flags, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(tiled_kernel<FWD, VT, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmem);
+    if (e != cudaSuccess) return e;
+    tiled_kernel<FWD, VT, PT><<<op_grid(P), dim3(kTileU, kTileV), kSmem, s>>>(P, vol, proj, acc, flags);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
 cudaError_t launch_pad(const vamrt_projector *p, const void *vol, vamrt_dtype dt, cudaStream_t s)
 {
-    const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
+    const OpParams &P = p->op;
     const unsigned grid = grid_for(p, p->pad_elems, 256);
     if (dt == VAMRT_F32)
-        pad_kernel<float><<<grid, 256, 0, s>>>((const float *)vol, p->scratch, nx, ny, nz, p->pad_elems);
+        pad_kernel<float><<<grid, 256, 0, s>>>((const float *)vol, p->scratch, P.nx, P.ny, P.nz, P.px, P.py,
+                                               p->pad_elems);
     else
-        pad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)vol,
-                                                       (__nv_bfloat16 *)p->scratch, nx, ny, nz, p->pad_elems);
+        pad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)p->scratch,
+                                                       P.nx, P.ny, P.nz, P.px, P.py, p->pad_elems);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -224,48 +467,38 @@ cudaError_t launch_pad(const vamrt_projector *p, const void *vol, vamrt_dtype dt
 cudaError_t launch_adjoint(const vamrt_projector *p, vamrt_dtype vol_dt, void *proj, vamrt_dtype proj_dt,
                            uint32_t flags, cudaStream_t s)
 {
-    const dim3 grid = op_grid(p->op), block(32, 4);
+    const OpParams &P = p->op;
     if (vol_dt == VAMRT_F32) {
-        if (proj_dt == VAMRT_F32)
-            adjoint_kernel<float, float><<<grid, block, 0, s>>>(p->op, p->scratch, (float *)proj, flags);
-        else
-            adjoint_kernel<float, __nv_bfloat16><<<grid, block, 0, s>>>(p->op, p->scratch,
-                                                                        (__nv_bfloat16 *)proj, flags);
-    } else {
-        const __nv_bfloat16 *vol = (const __nv_bfloat16 *)p->scratch;
-        if (proj_dt == VAMRT_F32)
-            adjoint_kernel<__nv_bfloat16, float><<<grid, block, 0, s>>>(p->op, vol, (float *)proj, flags);
-        else
-            adjoint_kernel<__nv_bfloat16, __nv_bfloat16><<<grid, block, 0, s>>>(p->op, vol,
-                                                                                (__nv_bfloat16 *)proj, flags);
+        const float *vol = p->scratch;
+        if (proj_dt == VAMRT_F32) return launch_tiled<false>(P, vol, (float *)proj, nullptr, flags, s);
+        return launch_tiled<false>(P, vol, (__nv_bfloat16 *)proj, nullptr, flags, s);
     }
-    count_launches(1);
-    return cudaGetLastError();
+    const __nv_bfloat16 *vol = (const __nv_bfloat16 *)p->scratch;
+    if (proj_dt == VAMRT_F32) return launch_tiled<false>(P, vol, (float *)proj, nullptr, flags, s);
+    return launch_tiled<false>(P, vol, (__nv_bfloat16 *)proj, nullptr, flags, s);
 }
 
 cudaError_t launch_forward(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(p->scratch, 0, sizeof(float) * p->pad_elems, s);
     if (e != cudaSuccess) return e;
-    const dim3 grid = op_grid(p->op), block(32, 4);
+    const OpParams &P = p->op;
+    const float *none = nullptr;
     if (proj_dt == VAMRT_F32)
-        forward_kernel<float><<<grid, block, 0, s>>>(p->op, (const float *)proj, p->scratch);
-    else
-        forward_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(p->op, (const __nv_bfloat16 *)proj, p->scratch);
-    count_launches(1);
-    return cudaGetLastError();
+        return launch_tiled<true>(P, none, (float *)proj, p->scratch, 0u, s);
+    return launch_tiled<true>(P, none, (__nv_bfloat16 *)proj, p->scratch, 0u, s);
 }
 
 cudaError_t launch_unpad(const vamrt_projector *p, void *dose, vamrt_dtype dt, uint32_t flags, cudaStream_t s)
 {
-    const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
-    const unsigned grid = grid_for(p, (int64_t)nx * ny * nz, 256);
+    const OpParams &P = p->op;
+    const unsigned grid = grid_for(p, (int64_t)P.nx * P.ny * P.nz, 256);
     const int accumulate = (flags & VAMRT_ACCUMULATE) ? 1 : 0;
     if (dt == VAMRT_F32)
-        unpad_kernel<float><<<grid, 256, 0, s>>>(p->scratch, (float *)dose, nx, ny, nz, accumulate);
+        unpad_kernel<float><<<grid, 256, 0, s>>>(p->scratch, (float *)dose, P.nx, P.ny, P.nz, P.px, P.py, accumulate);
     else
-        unpad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p->scratch, (__nv_bfloat16 *)dose, nx, ny, nz,
-                                                         accumulate);
+        unpad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p->scratch, (__nv_bfloat16 *)dose, P.nx, P.ny, P.nz, P.px,
+                                                         P.py, accumulate);
     count_launches(1);
     return cudaGetLastError();
 }

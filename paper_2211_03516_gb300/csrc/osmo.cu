@@ -11,7 +11,7 @@
 namespace vamrt {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ void st_dose(float *p, float x) { *p = x; }
 __device__ __forceinline__ void st_dose(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
@@ -32,7 +32,7 @@ __device__ T block_sum(T x, T *sh)
 
 __global__ void sum_partials_kernel(const float *__restrict__ x, int64_t n, double *__restrict__ partials)
 {
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kRedThreads / 32];
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         acc += (double)x[i];
@@ -44,17 +44,17 @@ __global__ void sum_partials_kernel(const float *__restrict__ x, int64_t n, doub
 __global__ void finish_sum_kernel(const double *__restrict__ partials, int n, const double *__restrict__ divisor,
                                   double *__restrict__ out)
 {
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kRedThreads / 32];
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) *out = divisor ? s / *divisor : s;
 }
 
-__global__ void interior_max_kernel(const float *__restrict__ acc, int nx, int ny, int nz, float *__restrict__ out)
+__global__ void interior_max_kernel(const float *__restrict__ acc, int nx, int ny, int nz, int px, int py,
+                                    float *__restrict__ out)
 {
     const int64_t total = (int64_t)nx * ny * nz;
-    const int px = nx + 2, py = ny + 2;
     float m = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % nx);
@@ -70,11 +70,11 @@ __global__ void interior_max_kernel(const float *__restrict__ acc, int nx, int n
 template <typename DT>
 __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *__restrict__ dmax,
                                    const float *__restrict__ target, float *__restrict__ model,
-                                   DT *__restrict__ dose, int nx, int ny, int nz, double *__restrict__ partials)
+                                   DT *__restrict__ dose, int nx, int ny, int nz, int px, int py,
+                                   double *__restrict__ partials)
 {
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kRedThreads / 32];
     const int64_t total = (int64_t)nx * ny * nz;
-    const int px = nx + 2, py = ny + 2;
     const float inv = 1.0f / *dmax;
     double err = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -93,7 +93,7 @@ __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *_
 
 inline int red_grid(int64_t n)
 {
-    int64_t g = (n + kThreads - 1) / kThreads;
+    int64_t g = (n + kRedThreads - 1) / kRedThreads;
     if (g > kRedBlocks) g = kRedBlocks;
     if (g < 1) g = 1;
     return (int)g;
@@ -105,8 +105,8 @@ cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cu
 {
     const int64_t n = (int64_t)p->g.nx * p->g.ny * p->g.nz;
     const int G = red_grid(n);
-    sum_partials_kernel<<<G, kThreads, 0, s>>>(x, n, p->red);
-    finish_sum_kernel<<<1, kThreads, 0, s>>>(p->red, G, nullptr, out);
+    sum_partials_kernel<<<G, kRedThreads, 0, s>>>(x, n, p->red);
+    finish_sum_kernel<<<1, kRedThreads, 0, s>>>(p->red, G, nullptr, out);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -118,17 +118,18 @@ cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, floa
     const int64_t n = (int64_t)nx * ny * nz;
     cudaError_t e = cudaMemsetAsync(p->dmax, 0, sizeof(float), s);
     if (e != cudaSuccess) return e;
-    int gm = (int)((n + kThreads - 1) / kThreads);
+    int gm = (int)((n + kRedThreads - 1) / kRedThreads);
     if (gm > p->num_sms * 8) gm = p->num_sms * 8;
-    interior_max_kernel<<<gm, kThreads, 0, s>>>(p->scratch, nx, ny, nz, p->dmax);
+    const int px = p->op.px, py = p->op.py;
+    interior_max_kernel<<<gm, kRedThreads, 0, s>>>(p->scratch, nx, ny, nz, px, py, p->dmax);
     const int G = red_grid(n);
     if (dose_dt == VAMRT_F32)
-        osmo_update_kernel<float><<<G, kThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,
-                                                         nx, ny, nz, p->red);
+        osmo_update_kernel<float><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,
+                                                         nx, ny, nz, px, py, p->red);
     else
-        osmo_update_kernel<__nv_bfloat16><<<G, kThreads, 0, s>>>(p->scratch, p->dmax, target, model,
-                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, p->red);
-    finish_sum_kernel<<<1, kThreads, 0, s>>>(p->red, G, fsum, err_out);
+        osmo_update_kernel<__nv_bfloat16><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model,
+                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, px, py, p->red);
+    finish_sum_kernel<<<1, kRedThreads, 0, s>>>(p->red, G, fsum, err_out);
     count_launches(3);
     return cudaGetLastError();
 }

@@ -75,7 +75,7 @@ vamrt_status validate(const vamrt_geometry *g)
     if (!(g->r_inner_mm / g->voxel_mm < 0.5 * (nmin + 1) - 1e-6))
         return fail(VAMRT_EINVAL, "grid (%d x %d voxels of %g mm) does not enclose the resin radius %g mm",
                     g->nx, g->ny, g->voxel_mm, g->r_inner_mm);
-    const int64_t pad = (int64_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2);
+    const int64_t pad = (int64_t)(((g->nx + 2 + 3) / 4) * 4) * (g->ny + 2) * (g->nz + 2);
     if (pad >= (int64_t)1 << 31) return fail(VAMRT_EINVAL, "grid too large (padded voxels must fit int32)");
     const int64_t rays = (int64_t)g->nu * g->nv * g->rays_per_pixel;
     if (rays >= (int64_t)1 << 31) return fail(VAMRT_EINVAL, "too many rays");
@@ -164,28 +164,29 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     CK(cudaGetDevice(&p->device), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device), "cudaDeviceGetAttribute");
     p->n_rays = (int64_t)g.nu * g.nv * M;
-    p->pad_elems = (int64_t)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+    const int px = ((g.nx + 2 + 3) / 4) * 4;   // rows padded to 16-byte groups
+    p->pad_elems = (int64_t)px * (g.ny + 2) * (g.nz + 2);
 
     CK(cudaMalloc(&p->tabA, sizeof(float4) * p->n_rays), "cudaMalloc(ray table)");
     CK(cudaMalloc(&p->tabB, sizeof(float4) * p->n_rays), "cudaMalloc(ray table)");
     CK(cudaMalloc(&p->tabJ, sizeof(int2) * p->n_rays), "cudaMalloc(ray table)");
-    CK(cudaMalloc(&p->cs, sizeof(float2) * g.n_angles), "cudaMalloc(angles)");
+    CK(cudaMalloc(&p->cs, sizeof(double2) * g.n_angles), "cudaMalloc(angles)");
     CK(cudaMalloc(&p->scratch, sizeof(float) * p->pad_elems), "cudaMalloc(scratch volume)");
     CK(cudaMalloc(&p->red, sizeof(double) * (vamrt::kRedBlocks + 8)), "cudaMalloc(reduction)");
     CK(cudaMalloc(&p->hist, sizeof(double) * vamrt::kMaxHistory), "cudaMalloc(history)");
     CK(cudaMalloc(&p->dmax, sizeof(float) * 4), "cudaMalloc(dmax)");
     CK(cudaMallocHost(&p->host_err, sizeof(double)), "cudaMallocHost");
-    p->device_bytes = (sizeof(float4) * 2 + sizeof(int2)) * (uint64_t)p->n_rays + sizeof(float2) * g.n_angles +
+    p->device_bytes = (sizeof(float4) * 2 + sizeof(int2)) * (uint64_t)p->n_rays + sizeof(double2) * g.n_angles +
                       sizeof(float) * (uint64_t)p->pad_elems;
 
     // angle table, FP64 on the host then rounded
-    float2 *hcs = (float2 *)malloc(sizeof(float2) * g.n_angles);
+    double2 *hcs = (double2 *)malloc(sizeof(double2) * g.n_angles);
     if (!hcs) return fail(VAMRT_ENOMEM, "host allocation failed");
     for (int k = 0; k < g.n_angles; ++k) {
         const double th = geom->angles_rad ? geom->angles_rad[k] : 2.0 * M_PI * k / g.n_angles;
-        hcs[k] = make_float2((float)cos(th), (float)sin(th));
+        hcs[k] = make_double2(cos(th), sin(th));
     }
-    cudaError_t e = cudaMemcpyAsync(p->cs, hcs, sizeof(float2) * g.n_angles, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(p->cs, hcs, sizeof(double2) * g.n_angles, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     free(hcs);
     if (e != cudaSuccess) return cuda_fail(e, "angle table upload");
@@ -222,11 +223,14 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     vamrt::OpParams &P = p->op;
     P.A = p->tabA; P.B = p->tabB; P.J = p->tabJ; P.cs = p->cs;
     P.nu = g.nu; P.nv = g.nv; P.M = M; P.n_angles = g.n_angles;
-    P.px = g.nx + 2; P.py = g.ny + 2; P.pz = g.nz + 2;
-    P.cx = (float)(0.5 * (g.nx - 1) + 1.0);
-    P.cy = (float)(0.5 * (g.ny - 1) + 1.0);
-    P.cz = (float)(0.5 * (g.nz - 1) + 1.0);
+    P.nx = g.nx; P.ny = g.ny; P.nz = g.nz;
+    P.px = px; P.py = g.ny + 2; P.pz = g.nz + 2;
+    P.cx = 0.5 * (g.nx - 1) + 1.0;
+    P.cy = 0.5 * (g.ny - 1) + 1.0;
+    P.cz = 0.5 * (g.nz - 1) + 1.0;
     P.neg_mu_vox_log2e = (float)(-g.mu_per_mm * g.voxel_mm * M_LOG2E);
+    // chunk 0 starts one voxel in front of the resin cylinder
+    P.y0 = (float)(-g.r_inner_mm / g.voxel_mm - 1.0);
 
     guard.p = nullptr;
     *out = p;

@@ -167,6 +167,9 @@ def test_bad_device_arguments(vamrt):
 
 
 def test_bf16_storage_error_bounds(vamrt):
+    """BF16-stored outputs carry BF16 rounding (~1.1e-3 RMS relative by itself), so
+    projections and dose written as BF16 get the 2e-3 bound; a result computed from
+    BF16-stored inputs and kept in FP32 (the gradient A^T dL/dD) gets 1e-3."""
     w = MID_CROP
     pupil = I.workload_pupil(w)
     P = vamrt.Projector.from_workload(w, pupil)
@@ -175,9 +178,15 @@ def test_bf16_storage_error_bounds(vamrt):
     d_ref = O.forward(w, y_ref, pupil)
     y16 = P.adjoint(gpu(f, torch.bfloat16), proj_dtype=torch.bfloat16)
     d16 = P.forward_dose(gpu(y_ref, torch.bfloat16), dose_dtype=torch.bfloat16)
+    V = I.random_volume(w, seed=8)
+    V16 = gpu(V, torch.bfloat16)
+    grad32 = P.adjoint(V16, proj_dtype=torch.float32)
+    d32 = P.forward_dose(gpu(y_ref, torch.bfloat16), dose_dtype=torch.float32)
     torch.cuda.synchronize()
-    assert rel_l2(y16.float().cpu().numpy(), y_ref) <= BF16_PROJ_TOL
+    assert rel_l2(y16.float().cpu().numpy(), y_ref) <= BF16_DOSE_TOL
     assert rel_l2(d16.float().cpu().numpy(), d_ref) <= BF16_DOSE_TOL
+    assert rel_l2(grad32.cpu().numpy(), O.adjoint(w, V, pupil)) <= BF16_PROJ_TOL
+    assert rel_l2(d32.cpu().numpy(), d_ref) <= BF16_PROJ_TOL
 
 
 def test_optimizer_matches_oracle_per_iteration(vamrt):
@@ -201,11 +210,21 @@ def test_optimizer_stops_at_tolerance(vamrt):
     P = vamrt.Projector.from_workload(w, pupil)
     f = gpu(I.make_target(w))
     full = P.optimize(f, max_iter=6, tol=0.0)
-    tol = float(full["errors"][2]) * 1.0000001   # reached at the third iteration
+    E = full["errors"]
+    assert len(E) == 6 and not full["converged"]
+    i_best = int(np.argmin(E[1:])) + 1
+    tol = float(E[i_best]) * 1.0000001
+    first = int(np.nonzero(E < tol)[0][0])        # first iteration below tol
     res = P.optimize(f, max_iter=6, tol=tol)
-    assert res["converged"] and res["iterations"] == 3
+    assert res["converged"] and res["iterations"] == first + 1
+    # the dose sums are not bitwise reproducible (atomic order); E agrees to ~1e-10
+    np.testing.assert_allclose(res["errors"], E[:first + 1], rtol=1e-7)
+    # checking every 4 iterations reads E only after iterations 4 and 6
     res2 = P.optimize(f, max_iter=6, tol=tol, check_every=4)
-    assert res2["converged"] and res2["iterations"] == 4
+    checks = [4, 6]
+    stop = next((c for c in checks if E[c - 1] < tol), None)
+    assert res2["converged"] == (stop is not None)
+    assert res2["iterations"] == (stop if stop else 6)
 
 
 # ---- full-size workload (256^3, 360 angles, 256^2 pixels, 16 rays/pixel) -------------
