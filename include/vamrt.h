@@ -70,7 +70,7 @@ typedef enum {
  *   step_vox    nominal spacing of the samples on a ray, in voxels (0 = 0.5, the 2x
  *               super-sampling of Sec. 2.2).  Each in-resin segment of length ell gets
  *               K = ceil(ell / (step_vox h) - 1e-9) midpoint samples s_j = (j+1/2) ell/K.
- * The grid must enclose the resin cylinder: r_inner_mm / voxel_mm < (min(nx,ny)+1)/2.
+ * The grid must enclose the resin cylinder: r_inner_mm / voxel_mm <= (min(nx,ny)+1)/2 - 0.01.
  */
 typedef struct {
     int32_t nx, ny, nz;

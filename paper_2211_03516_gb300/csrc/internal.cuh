@@ -21,7 +21,8 @@ constexpr int kTileU = 32;
 constexpr int kTileV = 8;
 constexpr int kThreads = kTileU * kTileV;
 constexpr int kChunkVox = 16;
-constexpr int kBoxFloats = 24 * 1024;
+constexpr int kBoxFloats = 18 * 1024;
+constexpr int kBlocksPerSm = 3;
 
 // Per-launch constants of the two operators.  Positions are in padded index
 // coordinates: the scratch volume has a zero halo of one voxel on every face (and its
@@ -38,6 +39,7 @@ struct OpParams {
     double cx, cy, cz;    // axis position in padded index coordinates
     float neg_mu_vox_log2e;  // -mu h log2(e): attenuation = exp2(this * s_vox)
     float y0;             // start of chunk 0 on the theta = 0 frame's y axis, voxels
+    float cell_bound;     // most samples of one ray whose footprint holds a given voxel
 };
 
 // Per-ray constants of the FP64 tracer.

@@ -185,11 +185,15 @@ __device__ __forceinline__ float frac32(long long q)
     return __uint_as_float(0x3f800000u | ((unsigned)q >> 9)) - 1.0f;
 }
 
+// Cell of a sample.  x and y stay inside the padded grid by construction (the grid is
+// validated to enclose the resin cylinder with a margin); z is clamped because the
+// sample range in z comes from the FP64 trace while positions here come from the FP32
+// table (a clamp that binds only for samples whose in-grid weight is ~0).
 __device__ __forceinline__ Cell cell_of(const OpParams &P, long long qx, long long qy, long long qz)
 {
     Cell c;
-    c.ix = min(max((int)(qx >> 32), 0), P.px - 2);
-    c.iy = min(max((int)(qy >> 32), 0), P.py - 2);
+    c.ix = (int)(qx >> 32);
+    c.iy = (int)(qy >> 32);
     c.iz = min(max((int)(qz >> 32), 0), P.pz - 2);
     c.fx = frac32(qx);
     c.fy = frac32(qy);
@@ -215,6 +219,9 @@ struct SmemSrc {
     __device__ __forceinline__ float operator()(int i) const { return p[i]; }
 };
 
+// Beer-Lambert factor of samples jl, jl+1, ...: exact exp2 at the start of each run,
+// then one multiply per sample (runs are one chunk long, ~30 samples, so the product
+// drifts by a few 1e-7 at most).
 template <class Src, class Addr>
 __device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, int jl, int jh, const Src &src,
                                              const Addr &addr)
@@ -223,6 +230,8 @@ __device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, in
     long long qy = R.q0y + (long long)jl * R.sy;
     long long qz = R.q0z + (long long)jl * R.sz;
     const int sx = addr.sx, sxy = addr.sxy;
+    float att = exp2f(R.att * ((float)jl + 0.5f));
+    const float ratio = exp2f(R.att);
     float acc = 0.f;
     for (int j = jl; j < jh; ++j) {
         const Cell c = cell_of(P, qx, qy, qz);
@@ -238,7 +247,8 @@ __device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, in
         const float y0 = fmaf(c.fy, x10 - x00, x00);
         const float y1 = fmaf(c.fy, x11 - x01, x01);
         const float val = fmaf(c.fz, y1 - y0, y0);
-        acc = fmaf(exp2f(R.att * ((float)j + 0.5f)), val, acc);
+        acc = fmaf(att, val, acc);
+        att *= ratio;
         qx += R.sx;
         qy += R.sy;
         qz += R.sz;
@@ -246,30 +256,84 @@ __device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, in
     return acc;
 }
 
-template <class Addr>
-__device__ __forceinline__ void walk_scatter(const OpParams &P, const Ray &R, int jl, int jh, float wray, float *dst,
-                                             const Addr &addr)
+// The 8 trilinear shares of weight w at a cell.
+struct Shares {
+    float s000, s100, s010, s110, s001, s101, s011, s111;
+};
+__device__ __forceinline__ Shares shares(float w, const Cell &c)
+{
+    const float wz1 = w * c.fz, wz0 = w - wz1;
+    const float w01 = wz0 * c.fy, w00 = wz0 - w01;
+    const float w11 = wz1 * c.fy, w10 = wz1 - w11;
+    Shares S;
+    S.s100 = w00 * c.fx; S.s000 = w00 - S.s100;
+    S.s110 = w01 * c.fx; S.s010 = w01 - S.s110;
+    S.s101 = w10 * c.fx; S.s001 = w10 - S.s101;
+    S.s111 = w11 * c.fx; S.s011 = w11 - S.s111;
+    return S;
+}
+
+// Global fallback: FP32 reductions straight into the padded accumulator.
+__device__ __forceinline__ void walk_scatter_global(const OpParams &P, const Ray &R, int jl, int jh, float wray,
+                                                    float *dst)
+{
+    long long qx = R.q0x + (long long)jl * R.sx;
+    long long qy = R.q0y + (long long)jl * R.sy;
+    long long qz = R.q0z + (long long)jl * R.sz;
+    const int sx = P.px, sxy = P.px * P.py;
+    float att = exp2f(R.att * ((float)jl + 0.5f));
+    const float ratio = exp2f(R.att);
+    for (int j = jl; j < jh; ++j) {
+        const Cell c = cell_of(P, qx, qy, qz);
+        float *p = dst + (c.iz * sxy + c.iy * sx + c.ix);
+        const Shares S = shares(wray * att, c);
+        atomicAdd(p, S.s000);
+        atomicAdd(p + 1, S.s100);
+        atomicAdd(p + sx, S.s010);
+        atomicAdd(p + sx + 1, S.s110);
+        atomicAdd(p + sxy, S.s001);
+        atomicAdd(p + sxy + 1, S.s101);
+        atomicAdd(p + sxy + sx, S.s011);
+        atomicAdd(p + sxy + sx + 1, S.s111);
+        att *= ratio;
+        qx += R.sx;
+        qy += R.sy;
+        qz += R.sz;
+    }
+}
+
+// Shared-memory box: fixed-point integer accumulation.  Shared-memory integer atomics
+// are native, FP32 ones are not.  `scale` maps the largest ray weight of the block to
+// well under 2^22, so every share rounds exactly through the 1.5 * 2^23 trick, and the
+// bound on shares per voxel and chunk keeps every box sum below 2^31.
+__device__ __forceinline__ int to_fixed(float x, float scale)
+{
+    return __float_as_int(fmaf(x, scale, 12582912.0f)) - 0x4B400000;
+}
+
+__device__ __forceinline__ void walk_scatter_box(const OpParams &P, const Ray &R, int jl, int jh, float wray,
+                                                 float scale, int *box, const BoxAddr &addr)
 {
     long long qx = R.q0x + (long long)jl * R.sx;
     long long qy = R.q0y + (long long)jl * R.sy;
     long long qz = R.q0z + (long long)jl * R.sz;
     const int sx = addr.sx, sxy = addr.sxy;
+    float att = exp2f(R.att * ((float)jl + 0.5f));
+    const float ratio = exp2f(R.att);
+    const float ws = wray * scale;
     for (int j = jl; j < jh; ++j) {
         const Cell c = cell_of(P, qx, qy, qz);
-        float *p = dst + addr(c);
-        const float w = wray * exp2f(R.att * ((float)j + 0.5f));
-        const float wz1 = w * c.fz, wz0 = w - wz1;
-        const float w01 = wz0 * c.fy, w00 = wz0 - w01;
-        const float w11 = wz1 * c.fy, w10 = wz1 - w11;
-        const float a100 = w00 * c.fx, a110 = w01 * c.fx, a101 = w10 * c.fx, a111 = w11 * c.fx;
-        atomicAdd(p, w00 - a100);
-        atomicAdd(p + 1, a100);
-        atomicAdd(p + sx, w01 - a110);
-        atomicAdd(p + sx + 1, a110);
-        atomicAdd(p + sxy, w10 - a101);
-        atomicAdd(p + sxy + 1, a101);
-        atomicAdd(p + sxy + sx, w11 - a111);
-        atomicAdd(p + sxy + sx + 1, a111);
+        int *p = box + addr(c);
+        const Shares S = shares(ws * att, c);
+        atomicAdd(p, to_fixed(S.s000, 1.f));
+        atomicAdd(p + 1, to_fixed(S.s100, 1.f));
+        atomicAdd(p + sx, to_fixed(S.s010, 1.f));
+        atomicAdd(p + sx + 1, to_fixed(S.s110, 1.f));
+        atomicAdd(p + sxy, to_fixed(S.s001, 1.f));
+        atomicAdd(p + sxy + 1, to_fixed(S.s101, 1.f));
+        atomicAdd(p + sxy + sx, to_fixed(S.s011, 1.f));
+        atomicAdd(p + sxy + sx + 1, to_fixed(S.s111, 1.f));
+        att *= ratio;
         qx += R.sx;
         qy += R.sy;
         qz += R.sz;
@@ -280,13 +344,13 @@ __device__ __forceinline__ void walk_scatter(const OpParams &P, const Ray &R, in
 // the tiled traversal, adjoint (FWD = false) or forward (FWD = true)
 // ---------------------------------------------------------------------------------
 template <bool FWD, typename VT, typename PT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     tiled_kernel(const OpParams P, const VT *__restrict__ vol, PT *__restrict__ proj, float *__restrict__ acc,
                  uint32_t flags)
 {
     extern __shared__ float box[];
     __shared__ int s_box[3][6];   // per chunk (rotating): min x,y,z and max x,y,z of the footprint
-    __shared__ int s_rng[3][2];   // per aperture sample (rotating): first and last chunk
+    __shared__ int s_rng[3][3];   // per aperture sample (rotating): first and last chunk, max |ray weight| bits
 
     const int tid = threadIdx.y * kTileU + threadIdx.x;
     const int u = blockIdx.x * kTileU + threadIdx.x;
@@ -299,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     float g = 0.f;
     if (FWD && valid) g = to_f(proj[pix_index]);
     if (tid < 18) s_box[tid / 6][tid % 6] = (tid % 6 < 3) ? INT_MAX : INT_MIN;
-    if (tid < 6) s_rng[tid / 2][tid % 2] = (tid % 2 == 0) ? INT_MAX : INT_MIN;
+    if (tid < 9) s_rng[tid / 3][tid % 3] = (tid % 3 == 0) ? INT_MAX : (tid % 3 == 1) ? INT_MIN : 0;
     __syncthreads();
 
     const int pxy = P.px * P.py;
@@ -316,19 +380,30 @@ __global__ void __launch_bounds__(kThreads, 2)
             cl = (R.dy > kMinDy) ? chunk_of(P, R, R.jhi - 1) : cf;
             if (cl < cf) cl = cf;
         }
+        const float wray = (FWD && active) ? g * R.w : 0.f;
         cf = __reduce_min_sync(kFull, cf);
         cl = __reduce_max_sync(kFull, cl);
+        // |weights| >= 0 order like their bit patterns
+        const int wbits = FWD ? __reduce_max_sync(kFull, __float_as_int(fabsf(wray))) : 0;
         if (threadIdx.x == 0 && cf <= cl) {
             atomicMin(&s_rng[ra][0], cf);
             atomicMax(&s_rng[ra][1], cl);
+            if (FWD) atomicMax(&s_rng[ra][2], wbits);
         }
         __syncthreads();
         const int cmin = s_rng[ra][0], cmax = s_rng[ra][1];
+        float scale = 0.f;
+        if (FWD) {
+            // fixed-point scale: a voxel takes at most cell_bound shares from each of the
+            // block's rays, each at most max|w|; keep the block's sum below 2^31
+            const float wmax = __int_as_float(s_rng[ra][2]);
+            scale = fminf(2147483648.0f / (1.01f * (float)kThreads * P.cell_bound * wmax), 1e30f);
+        }
         if (tid == 0) {
             s_rng[(a + 2) % 3][0] = INT_MAX;
             s_rng[(a + 2) % 3][1] = INT_MIN;
+            s_rng[(a + 2) % 3][2] = 0;
         }
-        const float wray = FWD ? g * (active ? R.w : 0.f) : 0.f;
         float ray_acc = 0.f;
 
         for (int c = cmin; c <= cmax; ++c) {
@@ -390,17 +465,20 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (!FWD)
                         ray_acc += walk_gather(P, R, jl, jh, SmemSrc{box}, addr);
                     else
-                        walk_scatter(P, R, jl, jh, wray, box, addr);
+                        walk_scatter_box(P, R, jl, jh, wray, scale, reinterpret_cast<int *>(box), addr);
                 }
                 if (FWD) {
                     __syncthreads();
+                    const float inv = 1.0f / scale;
+                    const int *ib = reinterpret_cast<const int *>(box);
                     for (int i = tid; i < n4; i += kThreads) {
                         const int x4 = i % ex4, t = i / ex4;
                         const int yy = t % ey, zz = t / ey;
-                        const float *b = box + zz * sxy + yy * sx + 4 * x4;
-                        const float4 q = make_float4(b[0], b[1], b[2], b[3]);
-                        if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f)
-                            red_v4(acc + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4, q);
+                        const int *b = ib + zz * sxy + yy * sx + 4 * x4;
+                        const int b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
+                        if ((b0 | b1 | b2 | b3) != 0)
+                            red_v4(acc + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4,
+                                   make_float4((float)b0 * inv, (float)b1 * inv, (float)b2 * inv, (float)b3 * inv));
                     }
                 }
             } else if (jl < jh) {
@@ -408,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (!FWD)
                     ray_acc += walk_gather(P, R, jl, jh, GlobalSrc<VT>{vol}, addr);
                 else
-                    walk_scatter(P, R, jl, jh, wray, acc, addr);
+                    walk_scatter_global(P, R, jl, jh, wray, acc);
             }
         }
         if (!FWD && active) pix = fmaf(R.w, ray_acc, pix);

@@ -72,7 +72,7 @@ vamrt_status validate(const vamrt_geometry *g)
         for (int k = 0; k < g->n_angles; ++k)
             if (!isfinite(g->angles_rad[k])) return fail(VAMRT_EINVAL, "angle %d is not finite", k);
     const int nmin = g->nx < g->ny ? g->nx : g->ny;
-    if (!(g->r_inner_mm / g->voxel_mm < 0.5 * (nmin + 1) - 1e-6))
+    if (!(g->r_inner_mm / g->voxel_mm <= 0.5 * (nmin + 1) - 0.01))
         return fail(VAMRT_EINVAL, "grid (%d x %d voxels of %g mm) does not enclose the resin radius %g mm",
                     g->nx, g->ny, g->voxel_mm, g->r_inner_mm);
     const int64_t pad = (int64_t)(((g->nx + 2 + 3) / 4) * 4) * (g->ny + 2) * (g->nz + 2);
@@ -231,6 +231,9 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     P.neg_mu_vox_log2e = (float)(-g.mu_per_mm * g.voxel_mm * M_LOG2E);
     // chunk 0 starts one voxel in front of the resin cylinder
     P.y0 = (float)(-g.r_inner_mm / g.voxel_mm - 1.0);
+    // a segment crosses the (-1,1)^3 neighbourhood of a voxel over at most 2 sqrt(3)
+    // voxels; consecutive samples are more than step_vox / 2 apart (K = ceil(ell/ds))
+    P.cell_bound = (float)fmax(2.0, floor(4.0 * sqrt(3.0) / g.step_vox) + 1.0);
 
     guard.p = nullptr;
     *out = p;
