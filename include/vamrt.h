@@ -185,6 +185,14 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
  */
 vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4, int32_t *j2);
 
+/*
+ * Measured shared-memory read bandwidth of the current device in bytes/s (conflict-free
+ * 32-bit loads on every SM).  The operators stage their per-sample corner words in shared
+ * memory, so this is the denominator of their roofline.  Synchronises `stream`; allocates
+ * a small temporary device buffer.  Errors: EINVAL (NULL), ENOMEM, ECUDA.
+ */
+vamrt_status vamrt_measure_smem_bandwidth(double *bytes_per_second, void *stream);
+
 /* Number of kernels this library has launched in the process (all devices). */
 uint64_t vamrt_launch_count(void);
 

@@ -17,8 +17,8 @@ constexpr int kRedBlocks = 1024;
 // chunk by chunk along the projection axis (kChunkVox voxels of the theta = 0 frame's y
 // per chunk).  Each chunk's voxel footprint is staged in a shared-memory box of at most
 // kBoxFloats floats; a chunk whose box would not fit runs straight on global memory.
-constexpr int kTileU = 32;
-constexpr int kTileV = 8;
+constexpr int kTileU = 8;
+constexpr int kTileV = 32;
 constexpr int kThreads = kTileU * kTileV;
 constexpr int kChunkVox = 16;
 constexpr int kBoxFloats = 18 * 1024;

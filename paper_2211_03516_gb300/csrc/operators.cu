@@ -1,9 +1,10 @@
 // The two hot operators: projection (adjoint A^T, a gather) and dose (forward A, a
 // scatter), sharing one tiled traversal.
 //
-// Work mapping.  A block owns 32 x 8 pixels (u fastest, one warp per pixel row) of one
-// angle; a thread owns one pixel and walks its aperture rays one after the other.  For a
-// given aperture sample the block's 256 rays form a coherent bundle, so the block
+// Work mapping.  A block owns 8 x 32 pixels (8 columns u, one warp per column running
+// down 32 rows v) of one angle; a thread owns one pixel and walks its aperture rays one
+// after the other.  For a given aperture sample the block's 256 rays form a coherent
+// bundle, so the block
 // advances them together in chunks: chunk c holds the samples whose position on the
 // theta = 0 frame's y axis (the projection direction) lies in [y0 + 16 c, y0 + 16 (c+1))
 // voxels.  For each chunk the block
@@ -203,9 +204,13 @@ __device__ __forceinline__ Cell cell_of(const OpParams &P, long long qx, long lo
 
 // Addressing of a sample's corner (0,0,0): shared-memory box or global padded volume.
 struct BoxAddr {
-    int sx, sxy, off;
-    __device__ __forceinline__ int operator()(const Cell &c) const { return c.iz * sxy + c.iy * sx + c.ix - off; }
+    int sx, sxy;
+    __device__ __forceinline__ int operator()(const Cell &c) const { return c.iz * sxy + c.iy * sx + c.ix; }
 };
+
+// i / d for 0 <= i < 2^22 and 1 <= d < 2^10 through an FP32 reciprocal: (i + 1/2) / d
+// lies at least 1/(2d) from an integer, well beyond the product's rounding error.
+__device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
 
 // Voxel sources for the gather: the global padded volume (read-only path) or the
 // shared-memory box.
@@ -352,9 +357,12 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     __shared__ int s_box[3][6];   // per chunk (rotating): min x,y,z and max x,y,z of the footprint
     __shared__ int s_rng[3][3];   // per aperture sample (rotating): first and last chunk, max |ray weight| bits
 
-    const int tid = threadIdx.y * kTileU + threadIdx.x;
-    const int u = blockIdx.x * kTileU + threadIdx.x;
-    const int v = blockIdx.y * kTileV + threadIdx.y;
+    // lanes run down a pixel column (v), warps across columns (u): at every step the 32
+    // samples of a warp are stacked along z, one voxel plane apart, so with an odd plane
+    // stride their shared-memory words fall in distinct banks
+    const int tid = threadIdx.y * kTileV + threadIdx.x;
+    const int u = blockIdx.x * kTileU + threadIdx.y;
+    const int v = blockIdx.y * kTileV + threadIdx.x;
     const int k = blockIdx.z;
     const bool valid = u < P.nu && v < P.nv;
     const double2 cs = P.cs[k];
@@ -444,14 +452,15 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
             if (hx == INT_MIN) continue;                      // no samples in this chunk
             const int ex = ((hx + 4) & ~3) - bx0;             // x extent, a multiple of 4
             const int ey = hy + 1 - by0, ez = hz + 1 - bz0;
-            const int sx = ex + 1, sxy = sx * ey;             // odd row stride: no bank conflicts
+            const int sx = ex + 1, sxy = sx * (ey | 1);       // odd row and plane strides
             const int ex4 = ex >> 2;
             const int n4 = ex4 * ey * ez;
+            const float inv_ex4 = 1.0f / (float)ex4, inv_ey = 1.0f / (float)ey;
             if ((long long)sxy * ez <= kBoxFloats) {
                 if (!FWD) {
                     for (int i = tid; i < n4; i += kThreads) {
-                        const int x4 = i % ex4, t = i / ex4;
-                        const int yy = t % ey, zz = t / ey;
+                        const int t = fdiv(i, inv_ex4), x4 = i - t * ex4;
+                        const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
                         const float4 q = ld4(vol + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
                         float *b = box + zz * sxy + yy * sx + 4 * x4;
                         b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
@@ -460,20 +469,22 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
                     for (int i = tid; i < sxy * ez; i += kThreads) box[i] = 0.f;
                 }
                 __syncthreads();
-                const BoxAddr addr{sx, sxy, bz0 * sxy + by0 * sx + bx0};
+                // box-relative addressing folded into the base pointer
+                const BoxAddr addr{sx, sxy};
+                const int off = bz0 * sxy + by0 * sx + bx0;
                 if (jl < jh) {
                     if (!FWD)
-                        ray_acc += walk_gather(P, R, jl, jh, SmemSrc{box}, addr);
+                        ray_acc += walk_gather(P, R, jl, jh, SmemSrc{box - off}, addr);
                     else
-                        walk_scatter_box(P, R, jl, jh, wray, scale, reinterpret_cast<int *>(box), addr);
+                        walk_scatter_box(P, R, jl, jh, wray, scale, reinterpret_cast<int *>(box) - off, addr);
                 }
                 if (FWD) {
                     __syncthreads();
                     const float inv = 1.0f / scale;
                     const int *ib = reinterpret_cast<const int *>(box);
                     for (int i = tid; i < n4; i += kThreads) {
-                        const int x4 = i % ex4, t = i / ex4;
-                        const int yy = t % ey, zz = t / ey;
+                        const int t = fdiv(i, inv_ex4), x4 = i - t * ex4;
+                        const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
                         const int *b = ib + zz * sxy + yy * sx + 4 * x4;
                         const int b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
                         if ((b0 | b1 | b2 | b3) != 0)
@@ -482,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
                     }
                 }
             } else if (jl < jh) {
-                const BoxAddr addr{P.px, pxy, 0};
+                const BoxAddr addr{P.px, pxy};
                 if (!FWD)
                     ray_acc += walk_gather(P, R, jl, jh, GlobalSrc<VT>{vol}, addr);
                 else
@@ -521,7 +532,7 @@ cudaError_t launch_tiled(const OpParams &P, const VT *vol, PT *proj, float *acc,
     cudaError_t e = cudaFuncSetAttribute(tiled_kernel<FWD, VT, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmem);
     if (e != cudaSuccess) return e;
-    tiled_kernel<FWD, VT, PT><<<op_grid(P), dim3(kTileU, kTileV), kSmem, s>>>(P, vol, proj, acc, flags);
+    tiled_kernel<FWD, VT, PT><<<op_grid(P), dim3(kTileV, kTileU), kSmem, s>>>(P, vol, proj, acc, flags);
     count_launches(1);
     return cudaGetLastError();
 }

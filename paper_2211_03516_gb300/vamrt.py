@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
         L.vamrt_status_string.restype = ctypes.c_char_p
         L.vamrt_last_error.argtypes = []
         L.vamrt_last_error.restype = ctypes.c_char_p
+        L.vamrt_measure_smem_bandwidth.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+        L.vamrt_measure_smem_bandwidth.restype = i32
         L.vamrt_launch_count.argtypes = []
         L.vamrt_launch_count.restype = ctypes.c_uint64
         for name in ("vamrt_make_projector", "vamrt_get_info", "vamrt_sample_count", "vamrt_adjoint",
@@ -279,6 +281,13 @@ class Projector:
         return dict(proj=proj, dose=dose, model=model, errors=hist[:rep.iterations].copy(),
                     iterations=rep.iterations, final_error=rep.final_error, converged=(st == VAMRT_OK),
                     adjoint_ms=rep.adjoint_ms, forward_ms=rep.forward_ms, update_ms=rep.update_ms)
+
+
+def vamrt_measure_smem_bandwidth(stream=None) -> float:
+    """Measured shared-memory read bandwidth of the current GPU, bytes/s."""
+    out = ctypes.c_double()
+    _check(lib().vamrt_measure_smem_bandwidth(ctypes.byref(out), _stream(stream)), "vamrt_measure_smem_bandwidth")
+    return float(out.value)
 
 
 def vamrt_launch_count() -> int:
