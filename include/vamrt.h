@@ -142,6 +142,28 @@ vamrt_status vamrt_forward_dose(vamrt_projector *p, const void *proj, vamrt_dtyp
                                 void *dose, vamrt_dtype dose_dtype, uint32_t flags, void *stream);
 
 /*
+ * Dose operator with no device allocation: the same computation and arguments as
+ * vamrt_forward_dose, but the FP32 accumulator is a fixed, statically allocated device
+ * array of 4,194,304 floats (16 MiB) instead of the projector's scratch volume.  The
+ * paper has no counterpart; this entry point exists for callers that cannot allocate
+ * device memory (memory owned by another allocator or budgeted up front, or code that
+ * must not allocate where it calls).  The call itself makes no cudaMalloc, cudaFree or
+ * other allocating call; the projector (made earlier) supplies the ray table.
+ *   - Limit: the padded grid, (nx+2 rounded up to a multiple of 4) x (ny+2) x (nz+2),
+ *     must be at most 4,194,304 voxels (e.g. 158^3); larger grids return EINVAL.
+ *   - The array exists once per device for the life of the process (every device that
+ *     loads the library holds the 16 MiB) and is shared by all calls and projectors: each
+ *     call first clears the part it uses, and calls that overlap on the GPU (other streams,
+ *     other threads) race on it.  Serialise them.
+ *   - The first call on a device looks up the array's device address (one runtime call,
+ *     no allocation); make that first call before any CUDA stream capture.
+ *   - The current device must be the projector's device.
+ * Errors: EINVAL (NULL, dtype, flags, grid too large, wrong device), ECUDA.
+ */
+vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dtype,
+                                       void *dose, vamrt_dtype dose_dtype, uint32_t flags, void *stream);
+
+/*
  * Projection optimisation (Sec. 2.7).  The paper runs the object-space model
  * optimisation of Rackson et al. with both operators replaced by the ray-traced ones
  * and stops once the absolute relative dose error is below 0.5 %.  Iteration, per the

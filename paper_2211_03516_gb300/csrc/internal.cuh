@@ -80,6 +80,8 @@ namespace vamrt {
 
 // Count of kernel launches issued by the library (vamrt_launch_count).
 void count_launches(unsigned n);
+// Set the calling thread's vamrt_last_error() text.
+void set_error(const char *msg);
 
 // raytable.cu
 cudaError_t launch_raytable(const TraceParams &T, float4 *A, float4 *B, int2 *J,
@@ -92,6 +94,12 @@ cudaError_t launch_adjoint(const vamrt_projector *p, vamrt_dtype vol_dt, void *p
                            uint32_t flags, cudaStream_t s);
 cudaError_t launch_forward(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, cudaStream_t s);
 cudaError_t launch_unpad(const vamrt_projector *p, void *dose, vamrt_dtype dt, uint32_t flags, cudaStream_t s);
+// The same two steps on a caller-chosen FP32 accumulator of p->pad_elems floats (the
+// caller zeroes it first).
+cudaError_t launch_forward_acc(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, float *acc,
+                               cudaStream_t s);
+cudaError_t launch_unpad_acc(const vamrt_projector *p, const float *acc, void *dose, vamrt_dtype dt, uint32_t flags,
+                             cudaStream_t s);
 
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);

@@ -592,4 +592,28 @@ cudaError_t launch_unpad(const vamrt_projector *p, void *dose, vamrt_dtype dt, u
     return cudaGetLastError();
 }
 
+cudaError_t launch_forward_acc(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, float *acc,
+                               cudaStream_t s)
+{
+    const OpParams &P = p->op;
+    const float *none = nullptr;
+    if (proj_dt == VAMRT_F32) return launch_tiled<true>(P, none, (float *)proj, acc, 0u, s);
+    return launch_tiled<true>(P, none, (__nv_bfloat16 *)proj, acc, 0u, s);
+}
+
+cudaError_t launch_unpad_acc(const vamrt_projector *p, const float *acc, void *dose, vamrt_dtype dt, uint32_t flags,
+                             cudaStream_t s)
+{
+    const OpParams &P = p->op;
+    const unsigned grid = grid_for(p, (int64_t)P.nx * P.ny * P.nz, 256);
+    const int accumulate = (flags & VAMRT_ACCUMULATE) ? 1 : 0;
+    if (dt == VAMRT_F32)
+        unpad_kernel<float><<<grid, 256, 0, s>>>(acc, (float *)dose, P.nx, P.ny, P.nz, P.px, P.py, accumulate);
+    else
+        unpad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(acc, (__nv_bfloat16 *)dose, P.nx, P.ny, P.nz, P.px, P.py,
+                                                         accumulate);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace vamrt

@@ -120,6 +120,7 @@ struct Guard {
 
 namespace vamrt {
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace vamrt
 
 extern "C" {
