@@ -199,6 +199,20 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
                             void *stream);
 
 /*
+ * Thresholded dose loss (the differentiable objective around the dose operator; the
+ * paper's optimiser targets the same in-part / out-of-part contrast, Sec. 2.7):
+ *   L = (1/|P|) sum_P relu(d_h - D)^2 + (1/|Q|) sum_Q relu(D - d_l)^2,
+ *   P = {target > 1/2}, Q = the other voxels (|.| counted at least 1),
+ * and, if grad is not NULL, dL/dD = -2 relu(d_h - D)/|P| on P, +2 relu(D - d_l)/|Q| on Q.
+ * dose: device [nz][ny][nx] in dose_dtype; target: device f32, same layout; loss: DEVICE
+ * pointer to one double (FP64 sums in a fixed order: deterministic); grad: device, dose
+ * layout, grad_dtype.  Uses the handle's reduction buffer.  Errors: EINVAL, ECUDA.
+ */
+vamrt_status vamrt_threshold_loss(vamrt_projector *p, const void *dose, vamrt_dtype dose_dtype, const float *target,
+                                  double d_l, double d_h, double *loss, void *grad, vamrt_dtype grad_dtype,
+                                  void *stream);
+
+/*
  * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index
  * r = (a nv + v) nu + u):  a4[r] = (e_x, e_y, e_z, delta) in voxel units (entry point
  * relative to the axis, sample spacing);  b4[r] = (d_x, d_y, d_z, T1 T2 delta_mm / M);

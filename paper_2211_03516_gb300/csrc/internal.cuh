@@ -101,6 +101,11 @@ cudaError_t launch_forward_acc(const vamrt_projector *p, const void *proj, vamrt
 cudaError_t launch_unpad_acc(const vamrt_projector *p, const float *acc, void *dose, vamrt_dtype dt, uint32_t flags,
                              cudaStream_t s);
 
+// loss.cu: loss3 = device doubles {L, 1/|P|, 1/|Q|}; grad may be NULL
+cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, vamrt_dtype dose_dt,
+                                  const float *target, float d_l, float d_h, double *loss3, void *grad,
+                                  vamrt_dtype grad_dt, cudaStream_t s);
+
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,

@@ -353,6 +353,21 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
     return converged ? VAMRT_OK : VAMRT_NOT_CONVERGED;
 }
 
+vamrt_status vamrt_threshold_loss(vamrt_projector *p, const void *dose, vamrt_dtype dose_dtype, const float *target,
+                                  double d_l, double d_h, double *loss, void *grad, vamrt_dtype grad_dtype,
+                                  void *stream)
+{
+    if (!p || !dose || !target || !loss) return fail(VAMRT_EINVAL, "NULL argument");
+    if (check_dtype(dose_dtype) || check_dtype(grad_dtype)) return VAMRT_EINVAL;
+    if (!isfinite(d_l) || !isfinite(d_h)) return fail(VAMRT_EINVAL, "thresholds must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *scal = p->red + vamrt::kRedBlocks + 2;       // {L, 1/|P|, 1/|Q|}
+    CK(vamrt::launch_threshold_loss(p, dose, dose_dtype, target, (float)d_l, (float)d_h, scal, grad, grad_dtype, s),
+       "loss kernels");
+    CK(cudaMemcpyAsync(loss, scal, sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    return VAMRT_OK;
+}
+
 vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4, int32_t *j2)
 {
     if (!p) return fail(VAMRT_EINVAL, "NULL projector");

@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
         L.vamrt_status_string.restype = ctypes.c_char_p
         L.vamrt_last_error.argtypes = []
         L.vamrt_last_error.restype = ctypes.c_char_p
+        L.vamrt_threshold_loss.argtypes = [vp, vp, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, i32, vp]
+        L.vamrt_threshold_loss.restype = i32
         L.vamrt_measure_smem_bandwidth.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.vamrt_measure_smem_bandwidth.restype = i32
         L.vamrt_launch_count.argtypes = []
@@ -257,6 +259,18 @@ class Projector:
         _check(lib().vamrt_forward_dose(self.handle, pp, _DTYPES[proj.dtype], dp, _DTYPES[out.dtype], flags,
                                         _stream(stream)), "vamrt_forward_dose")
         return out
+
+    def threshold_loss(self, dose: torch.Tensor, target: torch.Tensor, d_l: float, d_h: float, grad=True,
+                       grad_dtype=torch.float32, stream=None):
+        """(L as a 0-d float64 CUDA tensor, dL/dD or None) (vamrt_threshold_loss)."""
+        loss = torch.empty((), device=dose.device, dtype=torch.float64)
+        dp = _dev_ptr(dose, self.vol_shape, "dose")
+        tp = _dev_ptr(target, self.vol_shape, "target", (torch.float32,))
+        g = torch.empty(self.vol_shape, device=dose.device, dtype=grad_dtype) if grad else None
+        _check(lib().vamrt_threshold_loss(self.handle, dp, _DTYPES[dose.dtype], tp, float(d_l), float(d_h),
+                                          loss.data_ptr(), g.data_ptr() if g is not None else None,
+                                          _DTYPES[grad_dtype], _stream(stream)), "vamrt_threshold_loss")
+        return loss, g
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,

@@ -269,3 +269,19 @@ def test_full_size_sparse_dose_matches_oracle(vamrt, mid_full):
     d = P.forward_dose(gpu(g)).cpu().numpy()
     ref = O.forward(w, g, pupil)
     assert rel_l2(d, ref) <= FP32_TOL
+
+
+def test_optimizer_bf16_storage_within_bound(vamrt):
+    """Projections and dose stored in BF16 (sums in FP32): the optimiser's iterates stay
+    within the 2e-3 bound of the FP64 oracle's FP64 iteration over 10 iterations."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, proj_dtype=torch.bfloat16, dose_dtype=torch.bfloat16)
+    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                          n_iter=w.osmo_iters, tol=0.0)
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=BF16_DOSE_TOL)
+    assert rel_l2(res["proj"].float().cpu().numpy(), g_ref) <= BF16_DOSE_TOL
+    assert rel_l2(res["dose"].float().cpu().numpy(), dn_ref) <= BF16_DOSE_TOL
+    assert rel_l2(res["model"].cpu().numpy(), m_ref) <= BF16_DOSE_TOL
