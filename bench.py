@@ -161,6 +161,44 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def time_to_target(P, target, w, iters):
+    """Run the plain FP32 optimiser for `iters` iterations from m = f, then the BF16-storage
+    one, recording per-iteration device time (CUDA events) and the voxel error rate (VER).
+    Target: VER <= 1.01 x the plain run's final VER."""
+    import torch
+
+    def run(dtype):
+        model = target.clone()
+        proj = torch.empty(w.proj_shape, device=target.device, dtype=dtype)
+        dose = torch.empty(w.vol_shape, device=target.device, dtype=dtype)
+        t, vers = [], []
+        for _ in range(iters):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.optimize(target, model=model, max_iter=1, tol=0.0, proj=proj, dose=dose)
+            e1.record()
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1) / 1e3)
+            vers.append(P.voxel_error_rate(dose, target)[0])
+        return np.cumsum(t), vers
+
+    t32, v32 = run(torch.float32)
+    goal = 1.01 * v32[-1]
+    t16, v16 = run(torch.bfloat16)
+    hit = next((i for i, v in enumerate(v16) if v <= goal), None)
+    return {
+        "target": "VER <= 1.01 x plain FP32 final VER",
+        "plain_fp32": {"iterations": iters, "seconds": float(t32[-1]), "final_ver": v32[-1],
+                       "ver_per_iteration": [round(v, 6) for v in v32]},
+        "bf16_storage": {"iterations_to_target": None if hit is None else hit + 1,
+                         "seconds_to_target": None if hit is None else float(t16[hit]),
+                         "final_ver": v16[-1]},
+        "time_ratio": None if hit is None else float(t16[hit] / t32[-1]),
+        "warm_start": None,
+    }
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -270,6 +308,11 @@ def run_gpu(args, rank, world):
         except Exception:
             traffic = None
 
+    # ---- time to target: plain FP32 optimiser vs the BF16-storage optimiser ----
+    ttt = None
+    if args.ttt_iters > 0:
+        ttt = time_to_target(P, target, w, args.ttt_iters)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt = oracle_sample(w, pupil, target_np, list(range(w.nv // 2, w.nv // 2 + args.cpu_rows)))
@@ -304,6 +347,7 @@ def run_gpu(args, rank, world):
                              "peak_kind": peak_kind}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": host_target.numel() * 4,
                 "d2h_bytes_per_step": host_proj.numel() * 4 + 8},
+        "time_to_target": ttt,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -322,6 +366,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=48)
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt-iters", type=int, default=30,
+                    help="optimiser iterations of the time-to-target comparison (0 = skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -213,6 +213,18 @@ vamrt_status vamrt_threshold_loss(vamrt_projector *p, const void *dose, vamrt_dt
                                   void *stream);
 
 /*
+ * Voxel error rate (VER) of a dose against a binary target: the fraction of resin voxels
+ * (centres within r_inner_mm of the axis) whose printed state differs from the target at
+ * the best of the 1023 thresholds tau_i = (i/1024) max(dose), i = 1..1023 -- how well the
+ * dose prints the part whatever its scale (the optimiser's goal, Sec. 2.7).  A voxel is
+ * above tau_i iff min(floor(dose * (1024 / max)), 1023) >= i, evaluated in FP32.
+ * dose: device [nz][ny][nx] in dose_dtype (>= 0); target: device f32.  Writes the rate
+ * to *ver and the best i to *threshold_index (may be NULL).  Synchronous.
+ */
+vamrt_status vamrt_voxel_error_rate(vamrt_projector *p, const void *dose, vamrt_dtype dose_dtype, const float *target,
+                                    double *ver, int32_t *threshold_index, void *stream);
+
+/*
  * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index
  * r = (a nv + v) nu + u):  a4[r] = (e_x, e_y, e_z, delta) in voxel units (entry point
  * relative to the axis, sample spacing);  b4[r] = (d_x, d_y, d_z, T1 T2 delta_mm / M);

@@ -55,3 +55,22 @@ def threshold_loss(dose, target, d_l, d_h):
     L = (under ** 2).sum() / nP + (over ** 2).sum() / nQ
     grad = -2.0 * under / nP + 2.0 * over / nQ
     return L, grad
+
+
+def voxel_error_rate(dose, target, resin_mask):
+    """VER: fraction of resin voxels whose state at threshold tau_i = (i/1024) max(dose)
+    differs from the target, minimised over i = 1..1023.  The above/below decision is
+    the FP32 bin floor(dose * (1024 / max)) >= i (the dose's own precision); the counts
+    are a direct sweep over thresholds (no histogram), independent of the CUDA path."""
+    x = np.asarray(dose, dtype=np.float32)[resin_mask]
+    f = np.asarray(target)[resin_mask] > 0.5
+    m = np.float32(x.max())
+    scale = np.float32(1024.0) / m if m > 0 else np.float32(0.0)
+    b = np.clip(np.floor(x * scale), 0, 1023).astype(np.int64)
+    best, best_i = None, 1
+    for i in range(1, 1024):
+        above = b >= i
+        mis = int(np.count_nonzero(above != f))
+        if best is None or mis < best:
+            best, best_i = mis, i
+    return best / x.size, best_i

@@ -106,6 +106,10 @@ cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, va
                                   const float *target, float d_l, float d_h, double *loss3, void *grad,
                                   vamrt_dtype grad_dt, cudaStream_t s);
 
+// ver.cu: out3 = device {best mismatch count, best threshold index, resin voxels}
+cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype dt, const float *target,
+                       long long *out3, cudaStream_t s);
+
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,

@@ -368,6 +368,22 @@ vamrt_status vamrt_threshold_loss(vamrt_projector *p, const void *dose, vamrt_dt
     return VAMRT_OK;
 }
 
+vamrt_status vamrt_voxel_error_rate(vamrt_projector *p, const void *dose, vamrt_dtype dose_dtype, const float *target,
+                                    double *ver, int32_t *threshold_index, void *stream)
+{
+    if (!p || !dose || !target || !ver) return fail(VAMRT_EINVAL, "NULL argument");
+    if (check_dtype(dose_dtype)) return VAMRT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long *out3 = reinterpret_cast<long long *>(p->red + vamrt::kRedBlocks + 5);
+    CK(vamrt::launch_ver(p, dose, dose_dtype, target, out3, s), "voxel error rate kernels");
+    long long h[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(h, out3, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    *ver = h[2] > 0 ? (double)h[0] / (double)h[2] : 0.0;
+    if (threshold_index) *threshold_index = (int32_t)h[1];
+    return VAMRT_OK;
+}
+
 vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4, int32_t *j2)
 {
     if (!p) return fail(VAMRT_EINVAL, "NULL projector");

@@ -90,6 +90,9 @@ def lib() -> ctypes.CDLL:
         L.vamrt_last_error.restype = ctypes.c_char_p
         L.vamrt_threshold_loss.argtypes = [vp, vp, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, i32, vp]
         L.vamrt_threshold_loss.restype = i32
+        L.vamrt_voxel_error_rate.argtypes = [vp, vp, i32, vp, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int32), vp]
+        L.vamrt_voxel_error_rate.restype = i32
         L.vamrt_measure_smem_bandwidth.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.vamrt_measure_smem_bandwidth.restype = i32
         L.vamrt_launch_count.argtypes = []
@@ -271,6 +274,16 @@ class Projector:
                                           loss.data_ptr(), g.data_ptr() if g is not None else None,
                                           _DTYPES[grad_dtype], _stream(stream)), "vamrt_threshold_loss")
         return loss, g
+
+    def voxel_error_rate(self, dose: torch.Tensor, target: torch.Tensor, stream=None):
+        """(VER, best threshold index) of a dose against the binary target (vamrt_voxel_error_rate)."""
+        ver = ctypes.c_double()
+        idx = ctypes.c_int32()
+        _check(lib().vamrt_voxel_error_rate(self.handle, _dev_ptr(dose, self.vol_shape, "dose"), _DTYPES[dose.dtype],
+                                            _dev_ptr(target, self.vol_shape, "target", (torch.float32,)),
+                                            ctypes.byref(ver), ctypes.byref(idx), _stream(stream)),
+               "vamrt_voxel_error_rate")
+        return float(ver.value), int(idx.value)
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,

@@ -285,3 +285,22 @@ def test_optimizer_bf16_storage_within_bound(vamrt):
     assert rel_l2(res["proj"].float().cpu().numpy(), g_ref) <= BF16_DOSE_TOL
     assert rel_l2(res["dose"].float().cpu().numpy(), dn_ref) <= BF16_DOSE_TOL
     assert rel_l2(res["model"].cpu().numpy(), m_ref) <= BF16_DOSE_TOL
+
+
+def test_voxel_error_rate_matches_oracle_exactly(vamrt):
+    """VER is integer bookkeeping on the same dose: GPU and oracle agree exactly."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    Z, Y, X = I.voxel_centres(w)
+    resin = X ** 2 + Y ** 2 <= w.r_inner_mm ** 2
+    res = P.optimize(gpu(f), max_iter=3, tol=0.0)
+    for dose in (res["dose"], res["dose"].to(torch.bfloat16)):
+        ver, idx = P.voxel_error_rate(dose, gpu(f))
+        ver_ref, idx_ref = OS.voxel_error_rate(dose.float().cpu().numpy(), f, resin)
+        assert (ver, idx) == (ver_ref, idx_ref)
+        assert 0 < ver < 0.2
+    # a dose equal to the target prints it exactly
+    ver, _ = P.voxel_error_rate(gpu(f), gpu(f))
+    assert ver == 0.0

@@ -378,3 +378,18 @@ def test_threshold_loss_gradient_central_differences():
         assert abs(fd - g[i]) < 1e-7
     L0, g0 = OS.threshold_loss(np.where(f > 0, 1.2, 0.5), f, 0.9, 1.0)
     assert L0 == 0.0 and np.all(g0 == 0.0)
+
+
+def test_voxel_error_rate_small_cases():
+    """VER by hand: doses whose best threshold is known."""
+    f = np.array([1, 1, 0, 0, 1, 0], dtype=np.float32)
+    resin = np.ones(6, dtype=bool)
+    d = np.array([0.9, 1.0, 0.2, 0.1, 0.95, 0.3], dtype=np.float32)
+    ver, i = OS.voxel_error_rate(d, f, resin)
+    assert ver == 0.0 and 0.3 < i / 1024 <= 0.9
+    d2 = np.array([0.9, 0.2, 0.5, 0.1, 1.0, 0.3], dtype=np.float32)   # one in-part voxel too dim
+    ver2, _ = OS.voxel_error_rate(d2, f, resin)
+    assert abs(ver2 - 1 / 6) < 1e-12
+    resin2 = np.array([1, 0, 1, 1, 1, 1], dtype=bool)                  # ...unless it is outside the resin
+    ver3, _ = OS.voxel_error_rate(d2, f, resin2)
+    assert ver3 == 0.0
