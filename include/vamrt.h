@@ -225,6 +225,22 @@ vamrt_status vamrt_voxel_error_rate(vamrt_projector *p, const void *dose, vamrt_
                                     double *ver, int32_t *threshold_index, void *stream);
 
 /*
+ * 3x3x3 (taps = 27) or 1x1x1 (taps = 1) convolution, stride 1, zero padding, on the
+ * tensor cores: the layers of the learned warm start (a 3D U-Net mapping a target's
+ * projections to initial optimiser projections; the paper's optimiser starts from the
+ * target itself, Sec. 2.7).  BF16 operands, FP32 accumulation:
+ *   y[p][co] = act(bias[co] + sum_{t,ci} x[p + off(t)][ci] w[co][t][ci]),  act = ReLU if relu.
+ * x: device [d][h][wd][cin] bf16 (channels last), cin a multiple of 16; w: device
+ * [cout][taps][cin] bf16; bias: device f32 [cout] or NULL; y: device [d][h][wd][cout],
+ * bf16 (out_f32 = 0) or f32; cout a multiple of 16, <= 256.  x and w 16-byte aligned.
+ * err_flag: device int32, set to 1 if a bounded wait inside the kernel timed out (the
+ * output is then invalid).  Errors: EINVAL, ECUDA.
+ */
+vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, void *y, int32_t out_f32, int32_t d,
+                               int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps, int32_t relu,
+                               int32_t *err_flag, void *stream);
+
+/*
  * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index
  * r = (a nv + v) nu + u):  a4[r] = (e_x, e_y, e_z, delta) in voxel units (entry point
  * relative to the axis, sample spacing);  b4[r] = (d_x, d_y, d_z, T1 T2 delta_mm / M);

@@ -110,6 +110,10 @@ cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, va
 cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype dt, const float *target,
                        long long *out3, cudaStream_t s);
 
+// conv3d_tc.cu (tensor-core convolution of the warm-start network)
+cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
+                             int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s);
+
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,

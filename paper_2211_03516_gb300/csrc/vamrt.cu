@@ -384,6 +384,23 @@ vamrt_status vamrt_voxel_error_rate(vamrt_projector *p, const void *dose, vamrt_
     return VAMRT_OK;
 }
 
+vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, void *y, int32_t out_f32, int32_t d,
+                               int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps, int32_t relu,
+                               int32_t *err_flag, void *stream)
+{
+    if (!x || !w || !y || !err_flag) return fail(VAMRT_EINVAL, "NULL argument");
+    if (d < 1 || h < 1 || wd < 1) return fail(VAMRT_EINVAL, "volume extents must be >= 1");
+    if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256)
+        return fail(VAMRT_EINVAL, "channels: cin a multiple of 16, cout a multiple of 16 in 16..256");
+    if (taps != 1 && taps != 27) return fail(VAMRT_EINVAL, "taps must be 1 or 27");
+    if (((uintptr_t)x | (uintptr_t)w) & 15) return fail(VAMRT_EINVAL, "x and w must be 16-byte aligned");
+    if ((int64_t)d * h * wd * (cin > cout ? cin : cout) >= ((int64_t)1 << 40)) return fail(VAMRT_EINVAL, "too large");
+    CK(vamrt::launch_conv3d_tc(x, w, bias, y, out_f32, d, h, wd, cin, cout, taps, relu, (int *)err_flag,
+                               (cudaStream_t)stream),
+       "conv3d kernel");
+    return VAMRT_OK;
+}
+
 vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4, int32_t *j2)
 {
     if (!p) return fail(VAMRT_EINVAL, "NULL projector");

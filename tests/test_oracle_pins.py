@@ -393,3 +393,29 @@ def test_voxel_error_rate_small_cases():
     resin2 = np.array([1, 0, 1, 1, 1, 1], dtype=bool)                  # ...unless it is outside the resin
     ver3, _ = OS.voxel_error_rate(d2, f, resin2)
     assert ver3 == 0.0
+
+
+def test_conv3d_oracle_against_scalar_loops():
+    """The oracle convolution against the definition written out as scalar loops."""
+    from oracle import conv3d as C
+    rng = np.random.default_rng(4)
+    D, H, W, Cin, Cout = 3, 4, 5, 2, 3
+    x = rng.standard_normal((D, H, W, Cin))
+    w = rng.standard_normal((Cout, 27, Cin))
+    b = rng.standard_normal(Cout)
+    y = C.conv3d(x, w, b, relu=False)
+    for (z, yy, xx) in [(0, 0, 0), (1, 2, 3), (2, 3, 4), (0, 3, 2)]:
+        for co in range(Cout):
+            acc = b[co]
+            t = 0
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        zi, yi, xi = z + dz, yy + dy, xx + dx
+                        if 0 <= zi < D and 0 <= yi < H and 0 <= xi < W:
+                            acc += sum(x[zi, yi, xi, ci] * w[co, t, ci] for ci in range(Cin))
+                        t += 1
+            assert abs(y[z, yy, xx, co] - acc) < 1e-12
+    # 1x1x1 is a per-voxel matrix product
+    w1 = rng.standard_normal((Cout, 1, Cin))
+    np.testing.assert_allclose(C.conv3d(x, w1), x @ w1[:, 0, :].T, rtol=1e-14)
