@@ -183,7 +183,16 @@ typedef struct {
     vamrt_dtype proj_dtype;    /* storage of g */
     vamrt_dtype dose_dtype;    /* storage of dn */
     int32_t timing;            /* nonzero: time each phase with CUDA events on `stream` */
+    int32_t mode;              /* VAMRT_OPT_OBJECT (the reading above) or VAMRT_OPT_PROJECTIONS */
 } vamrt_opt_params;
+
+/* Optimiser modes.  VAMRT_OPT_OBJECT iterates on the model m (model in = m0).
+ * VAMRT_OPT_PROJECTIONS iterates on the projections themselves, starting from proj (in =
+ * g0, e.g. a learned warm start): d = A g; dn = d / max(d); E as above;
+ * g <- max(0, g + A^T (f - dn)) -- the same update OSMO makes to g = A^T m when the model
+ * clamp is inactive; the model buffer is used as the residual workspace (out = f - dn). */
+#define VAMRT_OPT_OBJECT 0
+#define VAMRT_OPT_PROJECTIONS 1
 
 typedef struct {
     int32_t iterations;        /* iterations run */
@@ -239,6 +248,51 @@ vamrt_status vamrt_voxel_error_rate(vamrt_projector *p, const void *dose, vamrt_
 vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, void *y, int32_t out_f32, int32_t d,
                                int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps, int32_t relu,
                                int32_t *err_flag, void *stream);
+
+/*
+ * Building blocks of the learned warm start (a 3D U-Net on the projection stack; the paper
+ * has no such network -- its optimiser starts from the target, Sec. 2.7).  Activations are
+ * channels-last BF16 [d][h][w][c] device arrays; gradients of weights and biases are FP32.
+ *
+ * vamrt_conv3d_wgrad_bf16: dw[co][t][ci] += sum_p dy[p][co] x[p + off(t)][ci] for the
+ *   convolution of vamrt_conv3d_bf16 (same x layout; dy [d][h][wd][cout]); tensor cores,
+ *   split over positions with FP32 atomics (caller zeroes dw).  wd must be a multiple of 16.
+ * vamrt_nn_resample: op 0 = 2x2x2 average pool (fine -> coarse), 1 = its backward (coarse
+ *   -> fine, /8), 2 = nearest 2x upsample (coarse -> fine), 3 = its backward (sum of 8);
+ *   d, h, w are the FINE extents (even).
+ * vamrt_nn_concat: ab[p] = (a[p], b[p]) over channels; backward = 1 splits ab into a, b.
+ * vamrt_nn_relu_backward: dy <- dy where y > 0, else 0 (n elements).
+ * vamrt_nn_bias_grad: db[c] += sum_p dy[p][c] (c <= 256).
+ * vamrt_nn_flip_weights: wt[ci][taps-1-t][co] = w[co][t][ci] (the data-gradient
+ *   convolution's weights: dx = conv(dy, wt)).
+ * vamrt_nn_adam: Adam step on FP32 params (moments m, v), refreshing an optional BF16 copy.
+ * vamrt_nn_prepare_input: x[z][v][u][0] = scale proj[z mod n_angles][v][u] (angles padded
+ *   circularly to d_padded), channels 1..15 zero.
+ * vamrt_nn_softplus_mse: out = softplus(z[...][0]) on the first n_angles slices;
+ *   loss = mean 0.5 (out - target)^2 (device double, may be NULL); dz (BF16, same layout as
+ *   z, may be NULL) = its gradient with respect to z.
+ * vamrt_nn_add: y += x (BF16, n elements).
+ * vamrt_projected_step: g <- max(0, g - eta grad) (FP32, n elements).
+ * Errors: EINVAL (NULL or bad sizes), ECUDA.
+ */
+vamrt_status vamrt_conv3d_wgrad_bf16(const void *x, const void *dy, float *dw, int32_t d, int32_t h, int32_t wd,
+                                     int32_t cin, int32_t cout, int32_t taps, int32_t *err_flag, void *stream);
+vamrt_status vamrt_nn_resample(int32_t op, const void *in, void *out, int32_t d, int32_t h, int32_t w, int32_t c,
+                               void *stream);
+vamrt_status vamrt_nn_concat(void *a, int32_t ca, void *b, int32_t cb, void *ab, int64_t npos, int32_t backward,
+                             void *stream);
+vamrt_status vamrt_nn_relu_backward(const void *y, void *dy, int64_t n, void *stream);
+vamrt_status vamrt_nn_bias_grad(const void *dy, float *db, int64_t npos, int32_t c, void *stream);
+vamrt_status vamrt_nn_flip_weights(const void *w, void *wt, int32_t cout, int32_t taps, int32_t cin, void *stream);
+vamrt_status vamrt_nn_adam(float *param, const float *grad, float *m, float *v, void *param_bf16, int64_t n, float lr,
+                           float beta1, float beta2, float eps, int32_t step, void *stream);
+vamrt_status vamrt_nn_prepare_input(const float *proj, void *x, int32_t n_angles, int32_t nv, int32_t nu,
+                                    int32_t d_padded, float scale, void *stream);
+vamrt_status vamrt_nn_softplus_mse(const float *z, int32_t cz, const float *target, float *out, void *dz,
+                                   int32_t n_angles, int32_t nv, int32_t nu, int32_t d_padded, double *loss,
+                                   void *stream);
+vamrt_status vamrt_nn_add(const void *x, void *y, int64_t n, void *stream);
+vamrt_status vamrt_projected_step(float *g, const float *grad, float eta, int64_t n, void *stream);
 
 /*
  * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index

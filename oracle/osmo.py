@@ -74,3 +74,20 @@ def voxel_error_rate(dose, target, resin_mask):
         if best is None or mis < best:
             best, best_i = mis, i
     return best / x.size, best_i
+
+
+def osmo_projections(target, g0, project, dose, n_iter):
+    """Projection-space iteration from g0 (reading; the learned warm start's continuation):
+    d = A g; dn = d / max(d); E = sum|dn - f| / sum f; g <- max(0, g + P(f - dn)).
+    Without the model clamp this is the update OSMO makes to g = P m."""
+    f = np.asarray(target, dtype=np.float64)
+    fsum = f.sum()
+    g = np.asarray(g0, dtype=np.float64).copy()
+    errors = []
+    dn = None
+    for _ in range(n_iter):
+        d = dose(g)
+        dn = d / d.max()
+        errors.append(np.abs(dn - f).sum() / fsum)
+        g = np.maximum(0.0, g + project(f - dn))
+    return g, dn, np.array(errors)

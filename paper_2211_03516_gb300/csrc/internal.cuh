@@ -114,9 +114,27 @@ cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype d
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s);
 
+cudaError_t launch_conv3d_wgrad_tc(const void *X, const void *dY, float *dW, int D, int H, int W, int Cin, int Cout,
+                                   int taps, int *err, cudaStream_t s);
+
+// nn_ops.cu
+cudaError_t nn_resample(int op, const void *in, void *out, int D, int H, int W, int C, cudaStream_t s);
+cudaError_t nn_concat(const void *a, int ca, const void *b, int cb, void *out, int64_t npos, int backward,
+                      cudaStream_t s);
+cudaError_t nn_relu_bwd(const void *y, void *dy, int64_t n, cudaStream_t s);
+cudaError_t nn_bias_grad(const void *dy, float *db, int64_t npos, int C, cudaStream_t s);
+cudaError_t nn_flip_weights(const void *w, void *wt, int cout, int taps, int cin, cudaStream_t s);
+cudaError_t nn_adam(float *p, const float *g, float *m, float *v, void *pb, int64_t n, float lr, float b1, float b2,
+                    float eps, int step, cudaStream_t s);
+cudaError_t nn_prepare_input(const float *proj, void *x, int A, int V, int U, int Dp, float scale, cudaStream_t s);
+cudaError_t nn_softplus_mse(const float *z, int cz, const float *target, float *out, void *dz, int A, int V, int U,
+                            int Dp, double *loss, cudaStream_t s);
+cudaError_t nn_add(const void *x, void *y, int64_t n, cudaStream_t s);
+cudaError_t nn_projected_step(float *g, const float *grad, float eta, int64_t n, cudaStream_t s);
+
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
-                             vamrt_dtype dose_dt, const double *fsum, double *err_out, cudaStream_t s);
+                             vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, cudaStream_t s);
 
 }  // namespace vamrt

@@ -1,0 +1,107 @@
+// C-ABI entry points of the warm-start network's building blocks (tensor-core weight
+// gradient, resampling, concatenation, ReLU/bias gradients, weight flip, Adam, input and
+// head kernels) and of the projected-gradient step.  Argument checks only; all work runs
+// in the kernels of conv3d_tc.cu and nn_ops.cu.
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace {
+vamrt_status einval(const char *msg)
+{
+    vamrt::set_error(msg);
+    return VAMRT_EINVAL;
+}
+vamrt_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return VAMRT_OK;
+    vamrt::set_error(cudaGetErrorString(e));
+    return VAMRT_ECUDA;
+}
+}  // namespace
+
+extern "C" {
+
+vamrt_status vamrt_conv3d_wgrad_bf16(const void *x, const void *dy, float *dw, int32_t d, int32_t h, int32_t wd,
+                                     int32_t cin, int32_t cout, int32_t taps, int32_t *err_flag, void *stream)
+{
+    if (!x || !dy || !dw || !err_flag) return einval("NULL argument");
+    if (d < 1 || h < 1 || wd < 16 || wd % 16) return einval("extents: d, h >= 1 and wd a multiple of 16");
+    if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256) return einval("channel counts");
+    if (taps != 1 && taps != 27) return einval("taps must be 1 or 27");
+    return cuda_status(vamrt::launch_conv3d_wgrad_tc(x, dy, dw, d, h, wd, cin, cout, taps, (int *)err_flag,
+                                                     (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_resample(int32_t op, const void *in, void *out, int32_t d, int32_t h, int32_t w, int32_t c,
+                               void *stream)
+{
+    if (!in || !out) return einval("NULL argument");
+    if (op < 0 || op > 3) return einval("op must be 0..3");
+    if (d < 2 || h < 2 || w < 2 || (d | h | w) & 1 || c < 1) return einval("fine extents must be even and >= 2");
+    return cuda_status(vamrt::nn_resample(op, in, out, d, h, w, c, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_concat(void *a, int32_t ca, void *b, int32_t cb, void *ab, int64_t npos, int32_t backward,
+                             void *stream)
+{
+    if (!a || !b || !ab) return einval("NULL argument");
+    if (ca < 1 || cb < 1 || npos < 0) return einval("sizes");
+    return cuda_status(vamrt::nn_concat(a, ca, b, cb, ab, npos, backward, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_relu_backward(const void *y, void *dy, int64_t n, void *stream)
+{
+    if (!y || !dy || n < 0) return einval("bad argument");
+    return cuda_status(vamrt::nn_relu_bwd(y, dy, n, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_bias_grad(const void *dy, float *db, int64_t npos, int32_t c, void *stream)
+{
+    if (!dy || !db || npos < 0 || c < 1 || c > 256) return einval("bad argument");
+    return cuda_status(vamrt::nn_bias_grad(dy, db, npos, c, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_flip_weights(const void *w, void *wt, int32_t cout, int32_t taps, int32_t cin, void *stream)
+{
+    if (!w || !wt || cout < 1 || cin < 1 || (taps != 1 && taps != 27)) return einval("bad argument");
+    return cuda_status(vamrt::nn_flip_weights(w, wt, cout, taps, cin, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_adam(float *param, const float *grad, float *m, float *v, void *param_bf16, int64_t n, float lr,
+                           float beta1, float beta2, float eps, int32_t step, void *stream)
+{
+    if (!param || !grad || !m || !v || n < 0 || step < 1) return einval("bad argument");
+    return cuda_status(vamrt::nn_adam(param, grad, m, v, param_bf16, n, lr, beta1, beta2, eps, step,
+                                      (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_prepare_input(const float *proj, void *x, int32_t n_angles, int32_t nv, int32_t nu,
+                                    int32_t d_padded, float scale, void *stream)
+{
+    if (!proj || !x || n_angles < 1 || nv < 1 || nu < 1 || d_padded < n_angles) return einval("bad argument");
+    return cuda_status(vamrt::nn_prepare_input(proj, x, n_angles, nv, nu, d_padded, scale, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_softplus_mse(const float *z, int32_t cz, const float *target, float *out, void *dz,
+                                   int32_t n_angles, int32_t nv, int32_t nu, int32_t d_padded, double *loss,
+                                   void *stream)
+{
+    if (!z || cz < 1 || n_angles < 1 || nv < 1 || nu < 1 || d_padded < n_angles) return einval("bad argument");
+    return cuda_status(vamrt::nn_softplus_mse(z, cz, target, out, dz, n_angles, nv, nu, d_padded, loss,
+                                              (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_add(const void *x, void *y, int64_t n, void *stream)
+{
+    if (!x || !y || n < 0) return einval("bad argument");
+    return cuda_status(vamrt::nn_add(x, y, n, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_projected_step(float *g, const float *grad, float eta, int64_t n, void *stream)
+{
+    if (!g || !grad || n < 0) return einval("bad argument");
+    return cuda_status(vamrt::nn_projected_step(g, grad, eta, n, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,324 @@
+// Layout, elementwise and optimiser kernels of the warm-start network (everything
+// around its tensor-core convolutions).  Activations are channels-last BF16
+// [D][H][W][C]; master weights and optimiser moments are FP32.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace vamrt {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ __nv_bfloat16 tobf(float v) { return __float2bfloat16_rn(v); }
+
+inline unsigned grid_n(int64_t n)
+{
+    int64_t g = (n + kT - 1) / kT;
+    if (g > 152 * 32) g = 152 * 32;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+#define GRID_STRIDE(i, n) for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// fine grid [D][H][W][C] <-> coarse grid [D/2][H/2][W/2][C]
+__global__ void avgpool2_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, int D, int H,
+                                int W, int C)
+{
+    const int d = D / 2, h = H / 2, w = W / 2;
+    const int64_t n = (int64_t)d * h * w * C;
+    GRID_STRIDE(i, n)
+    {
+        const int c = (int)(i % C);
+        const int64_t q = i / C;
+        const int x = (int)(q % w), y = (int)((q / w) % h), z = (int)(q / ((int64_t)w * h));
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+            s += bf(in[(((int64_t)zz * H + yy) * W + xx) * C + c]);
+        }
+        out[i] = tobf(0.125f * s);
+    }
+}
+
+// mode 0: average-pool backward (each fine voxel gets coarse / 8)
+// mode 1: nearest upsample (each fine voxel gets its coarse voxel)
+__global__ void spread2_kernel(const __nv_bfloat16 *__restrict__ coarse, __nv_bfloat16 *__restrict__ fine, int D,
+                               int H, int W, int C, float scale)
+{
+    const int64_t n = (int64_t)D * H * W * C;
+    const int h = H / 2, w = W / 2;
+    GRID_STRIDE(i, n)
+    {
+        const int c = (int)(i % C);
+        const int64_t q = i / C;
+        const int x = (int)(q % W), y = (int)((q / W) % H), z = (int)(q / ((int64_t)W * H));
+        fine[i] = tobf(scale * bf(coarse[(((int64_t)(z / 2) * h + y / 2) * w + x / 2) * C + c]));
+    }
+}
+
+// nearest-upsample backward: coarse = sum of its 8 fine voxels
+__global__ void sum2_kernel(const __nv_bfloat16 *__restrict__ fine, __nv_bfloat16 *__restrict__ coarse, int D, int H,
+                            int W, int C)
+{
+    const int d = D / 2, h = H / 2, w = W / 2;
+    const int64_t n = (int64_t)d * h * w * C;
+    GRID_STRIDE(i, n)
+    {
+        const int c = (int)(i % C);
+        const int64_t q = i / C;
+        const int x = (int)(q % w), y = (int)((q / w) % h), z = (int)(q / ((int64_t)w * h));
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) {
+            const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+            s += bf(fine[(((int64_t)zz * H + yy) * W + xx) * C + c]);
+        }
+        coarse[i] = tobf(s);
+    }
+}
+
+__global__ void concat_kernel(const __nv_bfloat16 *__restrict__ a, int ca, const __nv_bfloat16 *__restrict__ b, int cb,
+                              __nv_bfloat16 *__restrict__ out, int64_t npos)
+{
+    const int C = ca + cb;
+    GRID_STRIDE(i, npos * C)
+    {
+        const int c = (int)(i % C);
+        const int64_t p = i / C;
+        out[i] = c < ca ? a[p * ca + c] : b[p * cb + (c - ca)];
+    }
+}
+
+__global__ void split_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ a, int ca,
+                             __nv_bfloat16 *__restrict__ b, int cb, int64_t npos)
+{
+    const int C = ca + cb;
+    GRID_STRIDE(i, npos * C)
+    {
+        const int c = (int)(i % C);
+        const int64_t p = i / C;
+        if (c < ca)
+            a[p * ca + c] = in[i];
+        else
+            b[p * cb + (c - ca)] = in[i];
+    }
+}
+
+// dy <- dy where y > 0, else 0
+__global__ void relu_bwd_kernel(const __nv_bfloat16 *__restrict__ y, __nv_bfloat16 *__restrict__ dy, int64_t n)
+{
+    GRID_STRIDE(i, n)
+    {
+        if (!(bf(y[i]) > 0.f)) dy[i] = tobf(0.f);
+    }
+}
+
+// db[c] += sum_p dy[p][c]
+__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, float *__restrict__ db, int64_t npos, int C)
+{
+    // one block-stride sweep per channel group; C <= 256
+    __shared__ float acc[256];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) acc[c] = 0.f;
+    __syncthreads();
+    GRID_STRIDE(i, npos * C) atomicAdd(&acc[i % C], bf(dy[i]));
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], acc[c]);
+}
+
+// wt[ci][taps-1-t][co] = w[co][t][ci] (weights of the data-gradient convolution)
+__global__ void flip_weights_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bfloat16 *__restrict__ wt, int cout,
+                                    int taps, int cin)
+{
+    const int64_t n = (int64_t)cout * taps * cin;
+    GRID_STRIDE(i, n)
+    {
+        const int ci = (int)(i % cin);
+        const int t = (int)((i / cin) % taps);
+        const int co = (int)(i / ((int64_t)cin * taps));
+        wt[((int64_t)ci * taps + (taps - 1 - t)) * cout + co] = w[i];
+    }
+}
+
+// Adam on FP32 master parameters; refreshes their BF16 copy
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, __nv_bfloat16 *__restrict__ pb, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    GRID_STRIDE(i, n)
+    {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (pb) pb[i] = tobf(pi);
+    }
+}
+
+// x[z][v][u][0..15]: channel 0 = scale * proj[(z - pad) mod A][v][u] (circular in angle), others 0
+__global__ void prepare_input_kernel(const float *__restrict__ proj, __nv_bfloat16 *__restrict__ x, int A, int V,
+                                     int U, int Dp, float scale)
+{
+    const int64_t n = (int64_t)Dp * V * U * 16;
+    GRID_STRIDE(i, n)
+    {
+        const int c = (int)(i % 16);
+        const int64_t q = i / 16;
+        const int u = (int)(q % U), v = (int)((q / U) % V), z = (int)(q / ((int64_t)U * V));
+        float val = 0.f;
+        if (c == 0) val = scale * proj[((int64_t)(z % A) * V + v) * U + u];
+        x[i] = tobf(val);
+    }
+}
+
+// head: out = softplus(zin[...][0]) on the first A slices; loss sums 0.5 (out - target)^2;
+// dz[...][0] = (out - target) * sigmoid(z) / n (0 elsewhere and beyond A)
+__global__ void softplus_mse_kernel(const float *__restrict__ zin, int cz, const float *__restrict__ target,
+                                    float *__restrict__ out, __nv_bfloat16 *__restrict__ dz, int A, int V, int U, int Dp,
+                                    double *__restrict__ loss)
+{
+    const int64_t n = (int64_t)Dp * V * U;
+    const double inv_n = 1.0 / ((double)A * V * U);
+    double acc = 0.0;
+    GRID_STRIDE(q, n)
+    {
+        const int z = (int)(q / ((int64_t)U * V));
+        const float zz = zin[q * cz];
+        const float sp = zz > 20.f ? zz : log1pf(__expf(zz));
+        if (z < A) {
+            if (out) out[q] = sp;
+            if (target) {
+                const float r = sp - target[q];
+                acc += 0.5 * (double)r * (double)r;
+                if (dz) {
+                    const float sig = 1.f / (1.f + __expf(-zz));
+                    dz[q * cz] = tobf((float)((double)r * sig * inv_n));
+                }
+            } else if (dz) {
+                dz[q * cz] = tobf(0.f);
+            }
+        } else if (dz) {
+            dz[q * cz] = tobf(0.f);
+        }
+        if (dz)
+            for (int c = 1; c < cz; ++c) dz[q * cz + c] = tobf(0.f);
+    }
+    if (loss && target) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv_n);
+    }
+}
+
+// y += x (BF16)
+__global__ void add_kernel(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n)
+{
+    GRID_STRIDE(i, n) y[i] = tobf(bf(y[i]) + bf(x[i]));
+}
+
+// projected gradient step g <- max(0, g - eta * grad)
+__global__ void projected_step_kernel(float *__restrict__ g, const float *__restrict__ grad, float eta, int64_t n)
+{
+    GRID_STRIDE(i, n) g[i] = fmaxf(0.f, g[i] - eta * grad[i]);
+}
+
+}  // namespace
+
+cudaError_t nn_resample(int op, const void *in, void *out, int D, int H, int W, int C, cudaStream_t s)
+{
+    const __nv_bfloat16 *a = (const __nv_bfloat16 *)in;
+    __nv_bfloat16 *b = (__nv_bfloat16 *)out;
+    const int64_t fine = (int64_t)D * H * W * C, coarse = fine / 8;
+    switch (op) {
+    case 0: avgpool2_kernel<<<grid_n(coarse), kT, 0, s>>>(a, b, D, H, W, C); break;
+    case 1: spread2_kernel<<<grid_n(fine), kT, 0, s>>>(a, b, D, H, W, C, 0.125f); break;
+    case 2: spread2_kernel<<<grid_n(fine), kT, 0, s>>>(a, b, D, H, W, C, 1.0f); break;
+    case 3: sum2_kernel<<<grid_n(coarse), kT, 0, s>>>(a, b, D, H, W, C); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_concat(const void *a, int ca, const void *b, int cb, void *out, int64_t npos, int backward,
+                      cudaStream_t s)
+{
+    if (!backward)
+        concat_kernel<<<grid_n(npos * (ca + cb)), kT, 0, s>>>((const __nv_bfloat16 *)a, ca, (const __nv_bfloat16 *)b,
+                                                              cb, (__nv_bfloat16 *)out, npos);
+    else
+        split_kernel<<<grid_n(npos * (ca + cb)), kT, 0, s>>>((const __nv_bfloat16 *)out, (__nv_bfloat16 *)a, ca,
+                                                             (__nv_bfloat16 *)b, cb, npos);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_relu_bwd(const void *y, void *dy, int64_t n, cudaStream_t s)
+{
+    relu_bwd_kernel<<<grid_n(n), kT, 0, s>>>((const __nv_bfloat16 *)y, (__nv_bfloat16 *)dy, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_bias_grad(const void *dy, float *db, int64_t npos, int C, cudaStream_t s)
+{
+    bias_grad_kernel<<<grid_n(npos * C), kT, 0, s>>>((const __nv_bfloat16 *)dy, db, npos, C);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_flip_weights(const void *w, void *wt, int cout, int taps, int cin, cudaStream_t s)
+{
+    flip_weights_kernel<<<grid_n((int64_t)cout * taps * cin), kT, 0, s>>>((const __nv_bfloat16 *)w,
+                                                                          (__nv_bfloat16 *)wt, cout, taps, cin);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_adam(float *p, const float *g, float *m, float *v, void *pb, int64_t n, float lr, float b1, float b2,
+                    float eps, int step, cudaStream_t s)
+{
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<grid_n(n), kT, 0, s>>>(p, g, m, v, (__nv_bfloat16 *)pb, n, lr, b1, b2, eps, c1, c2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_prepare_input(const float *proj, void *x, int A, int V, int U, int Dp, float scale, cudaStream_t s)
+{
+    prepare_input_kernel<<<grid_n((int64_t)Dp * V * U * 16), kT, 0, s>>>(proj, (__nv_bfloat16 *)x, A, V, U, Dp, scale);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_softplus_mse(const float *z, int cz, const float *target, float *out, void *dz, int A, int V, int U,
+                            int Dp, double *loss, cudaStream_t s)
+{
+    if (loss) {
+        cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    softplus_mse_kernel<<<grid_n((int64_t)Dp * V * U), kT, 0, s>>>(z, cz, target, out, (__nv_bfloat16 *)dz, A, V, U, Dp,
+                                                                    loss);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_add(const void *x, void *y, int64_t n, cudaStream_t s)
+{
+    add_kernel<<<grid_n(n), kT, 0, s>>>((const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_projected_step(float *g, const float *grad, float eta, int64_t n, cudaStream_t s)
+{
+    projected_step_kernel<<<grid_n(n), kT, 0, s>>>(g, grad, eta, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace vamrt

@@ -293,6 +293,8 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
     if (params->check_every < 1) return fail(VAMRT_EINVAL, "check_every must be >= 1");
     if (!(params->tol >= 0.0)) return fail(VAMRT_EINVAL, "tol must be >= 0");
     if (check_dtype(params->proj_dtype) || check_dtype(params->dose_dtype)) return VAMRT_EINVAL;
+    if (params->mode != VAMRT_OPT_OBJECT && params->mode != VAMRT_OPT_PROJECTIONS)
+        return fail(VAMRT_EINVAL, "unknown optimiser mode %d", params->mode);
     cudaStream_t s = (cudaStream_t)stream;
     double *fsum = p->red + vamrt::kRedBlocks;
     // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration
@@ -308,16 +310,27 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
     int it = 0;
     double err = NAN;
     bool converged = false;
+    const bool proj_space = params->mode == VAMRT_OPT_PROJECTIONS;
     for (; it < params->max_iter;) {
         if (params->timing) CK(cudaEventRecord(ev[0], s), "cudaEventRecord");
-        // g = max(0, A^T m)
-        CK(vamrt::launch_pad(p, model, VAMRT_F32, s), "pad kernel");
-        CK(vamrt::launch_adjoint(p, VAMRT_F32, proj, params->proj_dtype, VAMRT_CLAMP_NONNEG, s), "adjoint kernel");
+        if (!proj_space) {
+            // g = max(0, A^T m)
+            CK(vamrt::launch_pad(p, model, VAMRT_F32, s), "pad kernel");
+            CK(vamrt::launch_adjoint(p, VAMRT_F32, proj, params->proj_dtype, VAMRT_CLAMP_NONNEG, s), "adjoint kernel");
+        }
         if (params->timing) CK(cudaEventRecord(ev[1], s), "cudaEventRecord");
         // d = A g (left in the scratch volume), then normalise, update, error
         CK(vamrt::launch_forward(p, proj, params->proj_dtype, s), "forward kernel");
         if (params->timing) CK(cudaEventRecord(ev[2], s), "cudaEventRecord");
-        CK(vamrt::launch_osmo_step(p, target, model, dose, params->dose_dtype, fsum, p->hist + it, s), "osmo step");
+        CK(vamrt::launch_osmo_step(p, target, model, dose, params->dose_dtype, fsum, p->hist + it, proj_space ? 1 : 0,
+                                   s),
+           "osmo step");
+        if (proj_space) {
+            // g <- max(0, g + A^T (f - dn)); the residual is in the model buffer
+            CK(vamrt::launch_pad(p, model, VAMRT_F32, s), "pad kernel");
+            CK(vamrt::launch_adjoint(p, VAMRT_F32, proj, params->proj_dtype, VAMRT_ACCUMULATE | VAMRT_CLAMP_NONNEG, s),
+               "adjoint kernel");
+        }
         if (params->timing) {
             CK(cudaEventRecord(ev[3], s), "cudaEventRecord");
             CK(cudaEventSynchronize(ev[3]), "cudaEventSynchronize");

@@ -56,7 +56,8 @@ class Info(ctypes.Structure):
 
 class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("check_every", ctypes.c_int32),
-                ("proj_dtype", ctypes.c_int), ("dose_dtype", ctypes.c_int), ("timing", ctypes.c_int32)]
+                ("proj_dtype", ctypes.c_int), ("dose_dtype", ctypes.c_int), ("timing", ctypes.c_int32),
+                ("mode", ctypes.c_int32)]
 
 
 class OptReport(ctypes.Structure):
@@ -287,10 +288,16 @@ class Projector:
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,
-                 timing=False, stream=None) -> dict:
-        """Projection optimisation (vamrt_optimize).  Returns g, dn, model, errors, converged."""
+                 timing=False, mode="object", stream=None) -> dict:
+        """Projection optimisation (vamrt_optimize).  Returns g, dn, model, errors, converged.
+        mode "object": OSMO on the model (model in = m0, default the target);
+        mode "projections": iterate on proj (in = g0, required), model = workspace."""
+        if mode not in ("object", "projections"):
+            raise ValueError("mode must be 'object' or 'projections'")
+        if mode == "projections" and proj is None:
+            raise ValueError("projection mode needs the starting projections in proj")
         if model is None:
-            model = target.clone()
+            model = target.clone() if mode == "object" else torch.empty_like(target)
         if proj is None:
             proj = torch.empty(self.proj_shape, device=target.device, dtype=proj_dtype)
         if dose is None:
@@ -300,7 +307,8 @@ class Projector:
         pp = _dev_ptr(proj, self.proj_shape, "proj")
         dp = _dev_ptr(dose, self.vol_shape, "dose")
         params = OptParams(max_iter=max_iter, tol=tol, check_every=check_every, proj_dtype=_DTYPES[proj.dtype],
-                           dose_dtype=_DTYPES[dose.dtype], timing=1 if timing else 0)
+                           dose_dtype=_DTYPES[dose.dtype], timing=1 if timing else 0,
+                           mode=0 if mode == "object" else 1)
         hist = np.zeros(max_iter, dtype=np.float64)
         rep = OptReport(iterations=0, final_error=math.nan, error_history=hist.ctypes.data_as(_dp))
         st = _check(lib().vamrt_optimize(self.handle, tp, mp, pp, dp, ctypes.byref(params), ctypes.byref(rep),

@@ -304,3 +304,19 @@ def test_voxel_error_rate_matches_oracle_exactly(vamrt):
     # a dose equal to the target prints it exactly
     ver, _ = P.voxel_error_rate(gpu(f), gpu(f))
     assert ver == 0.0
+
+
+def test_projection_space_optimiser_matches_oracle(vamrt):
+    """Projection-space iteration (the warm start's continuation) from g0 = max(0, A^T f),
+    per iteration against the FP64 oracle."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    g0 = np.maximum(0.0, O.adjoint(w, f, pupil))
+    res = P.optimize(gpu(f), proj=gpu(g0), max_iter=5, tol=0.0, mode="projections")
+    g_ref, dn_ref, e_ref = OS.osmo_projections(f, g0, lambda m: O.adjoint(w, m, pupil),
+                                               lambda g: O.forward(w, g, pupil), n_iter=5)
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
+    assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
+    assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL

@@ -45,3 +45,50 @@ def test_conv3d_matches_direct_convolution(U, shape, cin, cout, taps):
     U.check_errors(DEV)
     assert rel_l2(y32.cpu().numpy(), ref) <= 1e-5
     assert rel_l2(yr.float().cpu().numpy(), np.maximum(ref, 0)) <= 4e-3
+
+
+@pytest.mark.parametrize("cin,cout,taps", [(16, 16, 27), (48, 16, 27), (16, 32, 27), (16, 16, 1)])
+def test_conv3d_weight_gradient_matches_direct_sum(U, cin, cout, taps):
+    rng = np.random.default_rng(cin * 7 + cout)
+    D, H, W = 3, 5, 32
+    x = torch.from_numpy(rng.standard_normal((D, H, W, cin)).astype(np.float32)).to(torch.bfloat16)
+    dy = torch.from_numpy(rng.standard_normal((D, H, W, cout)).astype(np.float32)).to(torch.bfloat16)
+    xs, dys = x.double().numpy(), dy.double().numpy()
+    xp = np.zeros((D + 2, H + 2, W + 2, cin))
+    xp[1:-1, 1:-1, 1:-1] = xs
+    ref = np.zeros((cout, taps, cin))
+    for t, (dz, dyy, dx) in enumerate(C.tap_offsets(taps)):
+        sh = xp[1 + dz:1 + dz + D, 1 + dyy:1 + dyy + H, 1 + dx:1 + dx + W].reshape(-1, cin)
+        ref[:, t, :] = dys.reshape(-1, cout).T @ sh
+    dw = torch.zeros((cout, taps, cin), device=DEV)
+    U.conv3d_wgrad(x.to(DEV), dy.to(DEV), dw, taps)
+    torch.cuda.synchronize()
+    U.check_errors(DEV)
+    assert rel_l2(dw.cpu().numpy(), ref) <= 1e-5
+
+
+def test_unet_forward_backward_matches_fp64_reference(U):
+    """Whole network: output, loss and every layer's weight and bias gradient against the
+    FP64 autograd reference at the same (BF16-rounded) weights and input.  BF16 activation
+    and gradient storage bounds the agreement at a few 1e-2."""
+    from oracle import unet_ref
+    net = U.UNet3D(device=DEV, seed=1)
+    rng = np.random.default_rng(2)
+    Dp, Vv, Uu, A = 8, 16, 128, 6
+    proj = torch.from_numpy(rng.random((A, Vv, Uu), dtype=np.float32)).to(DEV)
+    target = torch.from_numpy(rng.random((A, Vv, Uu), dtype=np.float32)).to(DEV)
+    x0 = net.prepare(proj, 1.0, Dp)
+    net.zero_grad()
+    z = net.forward(x0)
+    out, loss, dz = net.head(z, A, target, want_grad=True)
+    net.backward(dz)
+    torch.cuda.synchronize()
+    U.check_errors(DEV)
+    weights = {n: (L.Wb.float().cpu().numpy(), L.b.cpu().numpy()) for n, L in net.layers.items()}
+    L_ref, z_ref, g_ref = unet_ref.loss_and_grads(U.ARCH, weights, x0.float().cpu().numpy(), target.cpu().numpy(), A)
+    assert rel_l2(z.cpu().numpy()[..., 0], z_ref[..., 0]) <= 2e-2
+    assert abs(loss.item() - L_ref) <= 2e-2 * L_ref
+    for n, L in net.layers.items():
+        gw, gb = g_ref[n]
+        assert rel_l2(L.gW.cpu().numpy(), gw) <= 5e-2, n
+        assert rel_l2(L.gb.cpu().numpy(), gb) <= 5e-2, n
