@@ -184,13 +184,15 @@ typedef struct {
     vamrt_dtype dose_dtype;    /* storage of dn */
     int32_t timing;            /* nonzero: time each phase with CUDA events on `stream` */
     int32_t mode;              /* VAMRT_OPT_OBJECT (the reading above) or VAMRT_OPT_PROJECTIONS */
+    double step;               /* projection mode: relaxation alpha in (0, 1] of the update */
 } vamrt_opt_params;
 
 /* Optimiser modes.  VAMRT_OPT_OBJECT iterates on the model m (model in = m0).
  * VAMRT_OPT_PROJECTIONS iterates on the projections themselves, starting from proj (in =
  * g0, e.g. a learned warm start): d = A g; dn = d / max(d); E as above;
- * g <- max(0, g + A^T (f - dn)) -- the same update OSMO makes to g = A^T m when the model
- * clamp is inactive; the model buffer is used as the residual workspace (out = f - dn). */
+ * g <- max(0, g + alpha A^T (f - dn)) -- with alpha = 1 the update OSMO makes to g = A^T m
+ * when the model clamp is inactive; the model buffer is the residual workspace
+ * (out = alpha (f - dn)). */
 #define VAMRT_OPT_OBJECT 0
 #define VAMRT_OPT_PROJECTIONS 1
 
@@ -268,11 +270,13 @@ vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, 
  * vamrt_nn_adam: Adam step on FP32 params (moments m, v), refreshing an optional BF16 copy.
  * vamrt_nn_prepare_input: x[z][v][u][0] = scale proj[z mod n_angles][v][u] (angles padded
  *   circularly to d_padded), channels 1..15 zero.
- * vamrt_nn_softplus_mse: out = softplus(z[...][0]) on the first n_angles slices;
- *   loss = mean 0.5 (out - target)^2 (device double, may be NULL); dz (BF16, same layout as
- *   z, may be NULL) = its gradient with respect to z.
+ * vamrt_nn_head_mse: residual head on the first n_angles slices, v = in_scale base + z[...][0]
+ *   (base: the network's input projections [n_angles][nv][nu] f32); out = out_scale max(v, 0)
+ *   (may be NULL); loss = mean 0.5 (v - target_scale target)^2 (device double, may be NULL);
+ *   dz (BF16, layout of z, may be NULL) = dloss/dz.
  * vamrt_nn_add: y += x (BF16, n elements).
  * vamrt_projected_step: g <- max(0, g - eta grad) (FP32, n elements).
+ * vamrt_nn_absmax: *out = max |x| over n FP32 elements (out: device float).
  * Errors: EINVAL (NULL or bad sizes), ECUDA.
  */
 vamrt_status vamrt_conv3d_wgrad_bf16(const void *x, const void *dy, float *dw, int32_t d, int32_t h, int32_t wd,
@@ -288,11 +292,12 @@ vamrt_status vamrt_nn_adam(float *param, const float *grad, float *m, float *v, 
                            float beta1, float beta2, float eps, int32_t step, void *stream);
 vamrt_status vamrt_nn_prepare_input(const float *proj, void *x, int32_t n_angles, int32_t nv, int32_t nu,
                                     int32_t d_padded, float scale, void *stream);
-vamrt_status vamrt_nn_softplus_mse(const float *z, int32_t cz, const float *target, float *out, void *dz,
-                                   int32_t n_angles, int32_t nv, int32_t nu, int32_t d_padded, double *loss,
-                                   void *stream);
+vamrt_status vamrt_nn_head_mse(const float *z, int32_t cz, const float *base, float in_scale, const float *target,
+                               float target_scale, float *out, float out_scale, void *dz, int32_t n_angles,
+                               int32_t nv, int32_t nu, int32_t d_padded, double *loss, void *stream);
 vamrt_status vamrt_nn_add(const void *x, void *y, int64_t n, void *stream);
 vamrt_status vamrt_projected_step(float *g, const float *grad, float eta, int64_t n, void *stream);
+vamrt_status vamrt_nn_absmax(const float *x, int64_t n, float *out, void *stream);
 
 /*
  * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index

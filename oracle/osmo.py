@@ -76,9 +76,9 @@ def voxel_error_rate(dose, target, resin_mask):
     return best / x.size, best_i
 
 
-def osmo_projections(target, g0, project, dose, n_iter):
+def osmo_projections(target, g0, project, dose, n_iter, alpha=1.0):
     """Projection-space iteration from g0 (reading; the learned warm start's continuation):
-    d = A g; dn = d / max(d); E = sum|dn - f| / sum f; g <- max(0, g + P(f - dn)).
+    d = A g; dn = d / max(d); E = sum|dn - f| / sum f; g <- max(0, g + P(alpha (f - dn))).
     Without the model clamp this is the update OSMO makes to g = P m."""
     f = np.asarray(target, dtype=np.float64)
     fsum = f.sum()
@@ -89,5 +89,5 @@ def osmo_projections(target, g0, project, dose, n_iter):
         d = dose(g)
         dn = d / d.max()
         errors.append(np.abs(dn - f).sum() / fsum)
-        g = np.maximum(0.0, g + project(f - dn))
+        g = np.maximum(0.0, g + project(alpha * (f - dn)))
     return g, dn, np.array(errors)

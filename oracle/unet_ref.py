@@ -1,6 +1,7 @@
 """FP64 CPU reference of the warm-start network (test infrastructure only): the same
 layers as the CUDA path -- 3^3 convolutions (zero padding) + ReLU, 2x average pool,
-nearest 2x upsample, channel concatenation, 1^3 head, softplus, mean 0.5 squared error --
+nearest 2x upsample, channel concatenation, 1^3 head added to the (scaled) input
+projections, mean 0.5 squared error --
 written with plain PyTorch CPU ops in float64, differentiated by autograd."""
 import numpy as np
 import torch
@@ -15,9 +16,9 @@ def _w5(W, taps):
     return W.permute(0, 2, 1).reshape(cout, cin, k, k, k)
 
 
-def loss_and_grads(arch, weights, x, target, n_angles):
+def loss_and_grads(arch, weights, x, target, n_angles, base, in_scale):
     """arch: [(name, cin, cout, taps)]; weights: name -> (W, b) numpy; x [Dp][V][U][16];
-    target [n_angles][V][U].  Returns (loss, z [Dp][V][U][16], grads name -> (gW, gb))."""
+    target, base [n_angles][V][U].  Returns (loss, z [Dp][V][U][16], grads name -> (gW, gb))."""
     params = {}
     for (n, ci, co, t) in arch:
         W, b = weights[n]
@@ -39,7 +40,7 @@ def loss_and_grads(arch, weights, x, target, n_angles):
     d1 = conv("dec1b", conv("dec1a", torch.cat([up(d2), s1], 1)))
     d0 = conv("dec0b", conv("dec0a", torch.cat([up(d1), s0], 1)))
     z = conv("head", d0, relu=False)
-    out = F.softplus(z[0, 0, :n_angles])
+    out = in_scale * torch.as_tensor(np.asarray(base, np.float64)) + z[0, 0, :n_angles]
     t = torch.as_tensor(np.asarray(target, np.float64))
     loss = 0.5 * ((out - t) ** 2).mean()
     loss.backward()

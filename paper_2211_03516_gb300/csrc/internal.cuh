@@ -127,14 +127,17 @@ cudaError_t nn_flip_weights(const void *w, void *wt, int cout, int taps, int cin
 cudaError_t nn_adam(float *p, const float *g, float *m, float *v, void *pb, int64_t n, float lr, float b1, float b2,
                     float eps, int step, cudaStream_t s);
 cudaError_t nn_prepare_input(const float *proj, void *x, int A, int V, int U, int Dp, float scale, cudaStream_t s);
-cudaError_t nn_softplus_mse(const float *z, int cz, const float *target, float *out, void *dz, int A, int V, int U,
-                            int Dp, double *loss, cudaStream_t s);
+cudaError_t nn_head_mse(const float *z, int cz, const float *base, float in_scale, const float *target,
+                        float target_scale, float *out, float out_scale, void *dz, int A, int V, int U, int Dp,
+                        double *loss, cudaStream_t s);
 cudaError_t nn_add(const void *x, void *y, int64_t n, cudaStream_t s);
 cudaError_t nn_projected_step(float *g, const float *grad, float eta, int64_t n, cudaStream_t s);
+cudaError_t nn_absmax(const float *x, int64_t n, float *out, cudaStream_t s);
 
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
-                             vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, cudaStream_t s);
+                             vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, float alpha,
+                             cudaStream_t s);
 
 }  // namespace vamrt

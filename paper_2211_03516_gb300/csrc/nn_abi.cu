@@ -83,13 +83,13 @@ vamrt_status vamrt_nn_prepare_input(const float *proj, void *x, int32_t n_angles
     return cuda_status(vamrt::nn_prepare_input(proj, x, n_angles, nv, nu, d_padded, scale, (cudaStream_t)stream));
 }
 
-vamrt_status vamrt_nn_softplus_mse(const float *z, int32_t cz, const float *target, float *out, void *dz,
-                                   int32_t n_angles, int32_t nv, int32_t nu, int32_t d_padded, double *loss,
-                                   void *stream)
+vamrt_status vamrt_nn_head_mse(const float *z, int32_t cz, const float *base, float in_scale, const float *target,
+                               float target_scale, float *out, float out_scale, void *dz, int32_t n_angles,
+                               int32_t nv, int32_t nu, int32_t d_padded, double *loss, void *stream)
 {
-    if (!z || cz < 1 || n_angles < 1 || nv < 1 || nu < 1 || d_padded < n_angles) return einval("bad argument");
-    return cuda_status(vamrt::nn_softplus_mse(z, cz, target, out, dz, n_angles, nv, nu, d_padded, loss,
-                                              (cudaStream_t)stream));
+    if (!z || !base || cz < 1 || n_angles < 1 || nv < 1 || nu < 1 || d_padded < n_angles) return einval("bad argument");
+    return cuda_status(vamrt::nn_head_mse(z, cz, base, in_scale, target, target_scale, out, out_scale, dz, n_angles,
+                                          nv, nu, d_padded, loss, (cudaStream_t)stream));
 }
 
 vamrt_status vamrt_nn_add(const void *x, void *y, int64_t n, void *stream)
@@ -102,6 +102,12 @@ vamrt_status vamrt_projected_step(float *g, const float *grad, float eta, int64_
 {
     if (!g || !grad || n < 0) return einval("bad argument");
     return cuda_status(vamrt::nn_projected_step(g, grad, eta, n, (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_nn_absmax(const float *x, int64_t n, float *out, void *stream)
+{
+    if (!x || !out || n < 0) return einval("bad argument");
+    return cuda_status(vamrt::nn_absmax(x, n, out, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -175,11 +175,13 @@ __global__ void prepare_input_kernel(const float *__restrict__ proj, __nv_bfloat
     }
 }
 
-// head: out = softplus(zin[...][0]) on the first A slices; loss sums 0.5 (out - target)^2;
-// dz[...][0] = (out - target) * sigmoid(z) / n (0 elsewhere and beyond A)
-__global__ void softplus_mse_kernel(const float *__restrict__ zin, int cz, const float *__restrict__ target,
-                                    float *__restrict__ out, __nv_bfloat16 *__restrict__ dz, int A, int V, int U, int Dp,
-                                    double *__restrict__ loss)
+// head (residual): v = in_scale * base[q] + z[q][0] on the first A slices (base = the
+// network's input projections); out = out_scale * max(v, 0); loss = mean 0.5 (v -
+// target_scale * target)^2; dz[q][0] = (v - target_scale * target) / n, 0 elsewhere.
+__global__ void head_mse_kernel(const float *__restrict__ zin, int cz, const float *__restrict__ base, float in_scale,
+                                const float *__restrict__ target, float target_scale, float *__restrict__ out,
+                                float out_scale, __nv_bfloat16 *__restrict__ dz, int A, int V, int U, int Dp,
+                                double *__restrict__ loss)
 {
     const int64_t n = (int64_t)Dp * V * U;
     const double inv_n = 1.0 / ((double)A * V * U);
@@ -187,25 +189,20 @@ __global__ void softplus_mse_kernel(const float *__restrict__ zin, int cz, const
     GRID_STRIDE(q, n)
     {
         const int z = (int)(q / ((int64_t)U * V));
-        const float zz = zin[q * cz];
-        const float sp = zz > 20.f ? zz : log1pf(__expf(zz));
+        float g = 0.f;
         if (z < A) {
-            if (out) out[q] = sp;
+            const float v = fmaf(in_scale, base[q], zin[q * cz]);
+            if (out) out[q] = out_scale * fmaxf(v, 0.f);
             if (target) {
-                const float r = sp - target[q];
+                const float r = v - target_scale * target[q];
                 acc += 0.5 * (double)r * (double)r;
-                if (dz) {
-                    const float sig = 1.f / (1.f + __expf(-zz));
-                    dz[q * cz] = tobf((float)((double)r * sig * inv_n));
-                }
-            } else if (dz) {
-                dz[q * cz] = tobf(0.f);
+                g = (float)((double)r * inv_n);
             }
-        } else if (dz) {
-            dz[q * cz] = tobf(0.f);
         }
-        if (dz)
+        if (dz) {
+            dz[q * cz] = tobf(g);
             for (int c = 1; c < cz; ++c) dz[q * cz + c] = tobf(0.f);
+        }
     }
     if (loss && target) {
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -217,6 +214,15 @@ __global__ void softplus_mse_kernel(const float *__restrict__ zin, int cz, const
 __global__ void add_kernel(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n)
 {
     GRID_STRIDE(i, n) y[i] = tobf(bf(y[i]) + bf(x[i]));
+}
+
+// out = max |x| (FP32; |x| >= 0 orders like its bit pattern); caller zeroes out
+__global__ void absmax_kernel(const float *__restrict__ x, int64_t n, float *__restrict__ out)
+{
+    float m = 0.f;
+    GRID_STRIDE(i, n) m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
 }
 
 // projected gradient step g <- max(0, g - eta * grad)
@@ -294,15 +300,16 @@ cudaError_t nn_prepare_input(const float *proj, void *x, int A, int V, int U, in
     return cudaGetLastError();
 }
 
-cudaError_t nn_softplus_mse(const float *z, int cz, const float *target, float *out, void *dz, int A, int V, int U,
-                            int Dp, double *loss, cudaStream_t s)
+cudaError_t nn_head_mse(const float *z, int cz, const float *base, float in_scale, const float *target,
+                        float target_scale, float *out, float out_scale, void *dz, int A, int V, int U, int Dp,
+                        double *loss, cudaStream_t s)
 {
     if (loss) {
         cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    softplus_mse_kernel<<<grid_n((int64_t)Dp * V * U), kT, 0, s>>>(z, cz, target, out, (__nv_bfloat16 *)dz, A, V, U, Dp,
-                                                                    loss);
+    head_mse_kernel<<<grid_n((int64_t)Dp * V * U), kT, 0, s>>>(z, cz, base, in_scale, target, target_scale, out,
+                                                                out_scale, (__nv_bfloat16 *)dz, A, V, U, Dp, loss);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -310,6 +317,15 @@ cudaError_t nn_softplus_mse(const float *z, int cz, const float *target, float *
 cudaError_t nn_add(const void *x, void *y, int64_t n, cudaStream_t s)
 {
     add_kernel<<<grid_n(n), kT, 0, s>>>((const __nv_bfloat16 *)x, (__nv_bfloat16 *)y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_absmax(const float *x, int64_t n, float *out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    absmax_kernel<<<grid_n(n), kT, 0, s>>>(x, n, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -71,7 +71,7 @@ template <typename DT>
 __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *__restrict__ dmax,
                                    const float *__restrict__ target, float *__restrict__ model,
                                    DT *__restrict__ dose, int nx, int ny, int nz, int px, int py,
-                                   double *__restrict__ partials, int residual)
+                                   double *__restrict__ partials, int residual, float alpha)
 {
     __shared__ double sh[kRedThreads / 32];
     const int64_t total = (int64_t)nx * ny * nz;
@@ -85,7 +85,7 @@ __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *_
         const float f = target[i];
         st_dose(dose + i, dn);
         // object space: m <- max(0, m + f - dn); projection space: the residual f - dn
-        model[i] = residual ? (f - dn) : fmaxf(0.f, model[i] + (f - dn));
+        model[i] = residual ? alpha * (f - dn) : fmaxf(0.f, model[i] + (f - dn));
         err += fabs((double)dn - (double)f);
     }
     const double s = block_sum(err, sh);
@@ -113,7 +113,8 @@ cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cu
 }
 
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
-                             vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, cudaStream_t s)
+                             vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, float alpha,
+                             cudaStream_t s)
 {
     const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
     const int64_t n = (int64_t)nx * ny * nz;
@@ -126,10 +127,10 @@ cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, floa
     const int G = red_grid(n);
     if (dose_dt == VAMRT_F32)
         osmo_update_kernel<float><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,
-                                                         nx, ny, nz, px, py, p->red, residual);
+                                                         nx, ny, nz, px, py, p->red, residual, alpha);
     else
         osmo_update_kernel<__nv_bfloat16><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model,
-                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, px, py, p->red, residual);
+                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, px, py, p->red, residual, alpha);
     finish_sum_kernel<<<1, kRedThreads, 0, s>>>(p->red, G, fsum, err_out);
     count_launches(3);
     return cudaGetLastError();

@@ -295,6 +295,8 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
     if (check_dtype(params->proj_dtype) || check_dtype(params->dose_dtype)) return VAMRT_EINVAL;
     if (params->mode != VAMRT_OPT_OBJECT && params->mode != VAMRT_OPT_PROJECTIONS)
         return fail(VAMRT_EINVAL, "unknown optimiser mode %d", params->mode);
+    if (params->mode == VAMRT_OPT_PROJECTIONS && !(params->step > 0.0 && params->step <= 1.0))
+        return fail(VAMRT_EINVAL, "projection-space step must be in (0, 1]");
     cudaStream_t s = (cudaStream_t)stream;
     double *fsum = p->red + vamrt::kRedBlocks;
     // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration
@@ -323,7 +325,7 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         CK(vamrt::launch_forward(p, proj, params->proj_dtype, s), "forward kernel");
         if (params->timing) CK(cudaEventRecord(ev[2], s), "cudaEventRecord");
         CK(vamrt::launch_osmo_step(p, target, model, dose, params->dose_dtype, fsum, p->hist + it, proj_space ? 1 : 0,
-                                   s),
+                                   (float)params->step, s),
            "osmo step");
         if (proj_space) {
             // g <- max(0, g + A^T (f - dn)); the residual is in the model buffer

@@ -82,12 +82,13 @@ def _setup_nn(L):
     L.vamrt_nn_flip_weights.argtypes = [vp, vp, i32, i32, i32, vp]
     L.vamrt_nn_adam.argtypes = [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp]
     L.vamrt_nn_prepare_input.argtypes = [vp, vp, i32, i32, i32, i32, f32, vp]
-    L.vamrt_nn_softplus_mse.argtypes = [vp, i32, vp, vp, vp, i32, i32, i32, i32, vp, vp]
+    L.vamrt_nn_head_mse.argtypes = [vp, i32, vp, f32, vp, f32, vp, f32, vp, i32, i32, i32, i32, vp, vp]
     L.vamrt_nn_add.argtypes = [vp, vp, i64, vp]
     L.vamrt_projected_step.argtypes = [vp, vp, f32, i64, vp]
+    L.vamrt_nn_absmax.argtypes = [vp, i64, vp, vp]
     for n in ("vamrt_conv3d_wgrad_bf16", "vamrt_nn_resample", "vamrt_nn_concat", "vamrt_nn_relu_backward",
               "vamrt_nn_bias_grad", "vamrt_nn_flip_weights", "vamrt_nn_adam", "vamrt_nn_prepare_input",
-              "vamrt_nn_softplus_mse", "vamrt_nn_add", "vamrt_projected_step"):
+              "vamrt_nn_head_mse", "vamrt_nn_add", "vamrt_projected_step", "vamrt_nn_absmax"):
         getattr(L, n).restype = ctypes.c_int
     L._nn_ready = True
     return L
@@ -149,6 +150,13 @@ def split(g, ca):
     return a, b
 
 
+def absmax(x) -> torch.Tensor:
+    """max |x| of an FP32 tensor, as a 1-element device tensor."""
+    out = torch.empty(1, device=x.device, dtype=torch.float32)
+    V._check(_nn().vamrt_nn_absmax(x.data_ptr(), x.numel(), out.data_ptr(), _s()), "absmax")
+    return out
+
+
 def add_(y, x):
     V._check(_nn().vamrt_nn_add(x.data_ptr(), y.data_ptr(), y.numel(), _s()), "add")
     return y
@@ -186,7 +194,7 @@ class Layer:
 
 class UNet3D:
     """4-level 3D U-Net (16/32/64/128 channels, two 3^3 convs per level, 2x average-pool
-    down, nearest 2x up, skip concatenation, 1^3 head + softplus) over a projection stack
+    down, nearest 2x up, skip concatenation, 1^3 head added to the input) over a projection stack
     [angles][v][u]; angles are padded circularly to a multiple of 8.  BF16 activations and
     weights, FP32 accumulation (tensor cores), FP32 master weights and Adam."""
 
@@ -236,14 +244,18 @@ class UNet3D:
         self._acts = a
         return a["z"]
 
-    def head(self, z, n_angles, target=None, want_grad=False):
-        """softplus(z[...,0]) on the first n_angles slices; with target: (out, loss, dz)."""
-        Dp, Vv, U, cz = z.shape
-        out = torch.empty((n_angles, Vv, U), device=z.device, dtype=torch.float32)
+    def head(self, z, base, in_scale, target=None, want_grad=False, out_scale=1.0, target_scale=1.0):
+        """Residual head: v = in_scale * base + z[...,0] on the first n_angles slices (base =
+        the input projections).  Returns (out_scale * max(v, 0), loss, dz); loss = mean
+        0.5 (v - target_scale * target)^2 when target is given."""
+        Dp, Vv, Uu, cz = z.shape
+        A = base.shape[0]
+        out = torch.empty((A, Vv, Uu), device=z.device, dtype=torch.float32)
         loss = torch.zeros((), device=z.device, dtype=torch.float64) if target is not None else None
-        dz = torch.empty((Dp, Vv, U, cz), device=z.device, dtype=torch.bfloat16) if want_grad else None
-        V._check(_nn().vamrt_nn_softplus_mse(z.data_ptr(), cz, _ptr(target), out.data_ptr(), _ptr(dz), n_angles, Vv, U,
-                                             Dp, _ptr(loss), _s()), "softplus_mse")
+        dz = torch.empty((Dp, Vv, Uu, cz), device=z.device, dtype=torch.bfloat16) if want_grad else None
+        V._check(_nn().vamrt_nn_head_mse(z.data_ptr(), cz, base.data_ptr(), float(in_scale), _ptr(target),
+                                         float(target_scale), out.data_ptr(), float(out_scale), _ptr(dz), A, Vv, Uu,
+                                         Dp, _ptr(loss), _s()), "head_mse")
         return out, loss, dz
 
     # ---- backward ----

@@ -57,7 +57,7 @@ class Info(ctypes.Structure):
 class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("check_every", ctypes.c_int32),
                 ("proj_dtype", ctypes.c_int), ("dose_dtype", ctypes.c_int), ("timing", ctypes.c_int32),
-                ("mode", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("step", ctypes.c_double)]
 
 
 class OptReport(ctypes.Structure):
@@ -288,7 +288,7 @@ class Projector:
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,
-                 timing=False, mode="object", stream=None) -> dict:
+                 timing=False, mode="object", step=1.0, stream=None) -> dict:
         """Projection optimisation (vamrt_optimize).  Returns g, dn, model, errors, converged.
         mode "object": OSMO on the model (model in = m0, default the target);
         mode "projections": iterate on proj (in = g0, required), model = workspace."""
@@ -308,7 +308,7 @@ class Projector:
         dp = _dev_ptr(dose, self.vol_shape, "dose")
         params = OptParams(max_iter=max_iter, tol=tol, check_every=check_every, proj_dtype=_DTYPES[proj.dtype],
                            dose_dtype=_DTYPES[dose.dtype], timing=1 if timing else 0,
-                           mode=0 if mode == "object" else 1)
+                           mode=0 if mode == "object" else 1, step=float(step))
         hist = np.zeros(max_iter, dtype=np.float64)
         rep = OptReport(iterations=0, final_error=math.nan, error_history=hist.ctypes.data_as(_dp))
         st = _check(lib().vamrt_optimize(self.handle, tp, mp, pp, dp, ctypes.byref(params), ctypes.byref(rep),

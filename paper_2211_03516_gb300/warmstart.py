@@ -1,0 +1,132 @@
+"""Learned warm start for the projection optimiser.
+
+The network (unet.UNet3D, tensor-core convolutions) maps a target's projections
+A^T f -- the optimiser's own first projections -- to the projections the plain
+optimiser reaches after many iterations.  Training pairs come from the plain ray-traced
+optimiser itself (object-space iterations from m = f).  At inference the predicted
+projections start the projection-space iteration of vamrt_optimize, and the plain
+optimiser's voxel error rate (VER) judges the result.  Both inputs and targets are
+scaled by 1 / max(A^T f) so the network sees values in [0, 1].
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import inputs as I
+from . import unet as U
+from . import vamrt as V
+
+
+def padded_angles(n_angles: int) -> int:
+    return ((n_angles + 7) // 8) * 8
+
+
+def _scale_of(y: torch.Tensor) -> float:
+    m = float(U.absmax(y).item())
+    return 1.0 / m if m > 0 else 1.0
+
+
+def make_pairs(P: V.Projector, w, seeds, osmo_iters: int, device="cuda:0", kind="csg"):
+    """[(f, A^T f, g*, scale)] on the device; g* = projections after osmo_iters plain iterations."""
+    pairs = []
+    for seed in seeds:
+        f = torch.from_numpy(I.make_target(w, kind=kind, seed=int(seed))).to(device)
+        if float(f.sum()) == 0.0:
+            continue
+        y = P.adjoint(f)
+        res = P.optimize(f, max_iter=osmo_iters, tol=0.0)
+        pairs.append((f, y, res["proj"], _scale_of(y)))
+    return pairs
+
+
+def train(net: U.UNet3D, pairs, epochs: int, lr: float = 1e-3, log=None):
+    A = pairs[0][1].shape[0]
+    Dp = padded_angles(A)
+    losses = []
+    for ep in range(epochs):
+        tot = 0.0
+        for i in np.random.default_rng(ep).permutation(len(pairs)):
+            f, y, g, s = pairs[i]
+            x0 = net.prepare(y, s, Dp)
+            net.zero_grad()
+            z = net.forward(x0)
+            _, loss, dz = net.head(z, y, s, target=g, want_grad=True, target_scale=s)
+            net.backward(dz)
+            net.adam_step(lr)
+            tot += float(loss.item())
+        losses.append(tot / len(pairs))
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.3e}")
+    U.check_errors(net.device)
+    return losses
+
+
+def predict(net: U.UNet3D, y: torch.Tensor) -> torch.Tensor:
+    """Warm-start projections from A^T f (same units as the optimiser's projections)."""
+    A = y.shape[0]
+    s = _scale_of(y)
+    z = net.forward(net.prepare(y, s, padded_angles(A)))
+    out, _, _ = net.head(z, y, s, out_scale=1.0 / s)
+    return out
+
+
+def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.float32, step=0.5):
+    """VER after each iteration and cumulative device seconds: object space from m = f when
+    g0 is None, else projection space from g0."""
+    vol = torch.empty_like(f)
+    dose = torch.empty(f.shape, device=f.device, dtype=dtype)
+    if g0 is None:
+        model, proj, mode = f.clone(), torch.empty(P.proj_shape, device=f.device, dtype=dtype), "object"
+    else:
+        model, proj, mode = vol, g0.clone().to(dtype), "projections"
+    t, vers = 0.0, []
+    times = []
+    for _ in range(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.optimize(f, model=model, proj=proj, dose=dose, max_iter=1, tol=0.0, mode=mode, step=step)
+        e1.record()
+        e1.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        times.append(t)
+        vers.append(P.voxel_error_rate(dose, f)[0])
+    return np.array(vers), np.array(times)
+
+
+def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iters: int, device="cuda:0", kind="csg",
+            step=0.5, dtype=torch.float32):
+    """Per held-out target: the plain run's final VER, and for the warm start and for the
+    same continuation started from g0 = max(0, A^T f) (no network): the iterations and
+    device time to reach 1.01 x the plain final VER."""
+    rows = []
+    for seed in seeds:
+        f = torch.from_numpy(I.make_target(w, kind=kind, seed=int(seed))).to(device)
+        if float(f.sum()) == 0.0:
+            continue
+        v_plain, t_plain = ver_curve(P, f, plain_iters)
+        goal = 1.01 * v_plain[-1]
+        y = P.adjoint(f)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g_ws = predict(net, y)
+        e1.record()
+        e1.synchronize()
+        t_inf = e0.elapsed_time(e1) / 1e3
+        v_ws, t_ws = ver_curve(P, f, cont_iters, g0=g_ws, step=step, dtype=dtype)
+        g_cold = P.adjoint(f, clamp_nonneg=True)
+        v_cold, t_cold = ver_curve(P, f, cont_iters, g0=g_cold, step=step, dtype=dtype)
+
+        def hit(v, t, extra=0.0):
+            k = next((i for i, x in enumerate(v) if x <= goal), None)
+            return (None, None) if k is None else (k + 1, float(t[k] + extra))
+
+        k_ws, s_ws = hit(v_ws, t_ws, t_inf)
+        k_cold, s_cold = hit(v_cold, t_cold)
+        rows.append(dict(seed=int(seed), plain_final_ver=float(v_plain[-1]), plain_seconds=float(t_plain[-1]),
+                         warm_ver=v_ws.tolist(), cold_ver=v_cold.tolist(), plain_ver=v_plain.tolist(),
+                         warm_iters_to_target=k_ws, warm_seconds_to_target=s_ws, inference_seconds=t_inf,
+                         cold_iters_to_target=k_cold, cold_seconds_to_target=s_cold))
+    return rows

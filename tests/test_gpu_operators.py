@@ -314,9 +314,9 @@ def test_projection_space_optimiser_matches_oracle(vamrt):
     P = vamrt.Projector.from_workload(w, pupil)
     f = I.make_target(w)
     g0 = np.maximum(0.0, O.adjoint(w, f, pupil))
-    res = P.optimize(gpu(f), proj=gpu(g0), max_iter=5, tol=0.0, mode="projections")
+    res = P.optimize(gpu(f), proj=gpu(g0), max_iter=5, tol=0.0, mode="projections", step=0.5)
     g_ref, dn_ref, e_ref = OS.osmo_projections(f, g0, lambda m: O.adjoint(w, m, pupil),
-                                               lambda g: O.forward(w, g, pupil), n_iter=5)
+                                               lambda g: O.forward(w, g, pupil), n_iter=5, alpha=0.5)
     np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
     assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
     assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL

@@ -80,12 +80,13 @@ def test_unet_forward_backward_matches_fp64_reference(U):
     x0 = net.prepare(proj, 1.0, Dp)
     net.zero_grad()
     z = net.forward(x0)
-    out, loss, dz = net.head(z, A, target, want_grad=True)
+    out, loss, dz = net.head(z, proj, 0.5, target=target, want_grad=True)
     net.backward(dz)
     torch.cuda.synchronize()
     U.check_errors(DEV)
     weights = {n: (L.Wb.float().cpu().numpy(), L.b.cpu().numpy()) for n, L in net.layers.items()}
-    L_ref, z_ref, g_ref = unet_ref.loss_and_grads(U.ARCH, weights, x0.float().cpu().numpy(), target.cpu().numpy(), A)
+    L_ref, z_ref, g_ref = unet_ref.loss_and_grads(U.ARCH, weights, x0.float().cpu().numpy(), target.cpu().numpy(), A,
+                                                  proj.cpu().numpy(), 0.5)
     assert rel_l2(z.cpu().numpy()[..., 0], z_ref[..., 0]) <= 2e-2
     assert abs(loss.item() - L_ref) <= 2e-2 * L_ref
     for n, L in net.layers.items():
