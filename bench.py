@@ -102,6 +102,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Max of a per-rank scalar over all ranks (timings: the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_threads() -> int:
     return 1   # the oracle is single-threaded
 
@@ -302,11 +311,7 @@ def run_gpu(args, rank, world):
         ev1.record(stream)
         barrier()
     launches = vamrt.vamrt_launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
-    t_local = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max = reduce_max(ev0.elapsed_time(ev1), dist, dev)
     value = world * units_per_step * args.steps / (ms_max / 1e3)
 
     # ---- end to end through the public API with host buffers ----
@@ -322,11 +327,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         _ = r["final_error"]
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_local = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
-    e2e_value = world * units_per_step * e2e_steps / float(e2e_local.item())
+    e2e_value = world * units_per_step * e2e_steps / reduce_max(time.perf_counter() - t0, dist, dev)
 
     # ---- roofline of the dominant kernel (CUDA events around it, inside the library) ----
     # Both operators stage their per-sample data -- 8 trilinear corner words, 32 B -- in

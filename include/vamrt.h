@@ -50,6 +50,10 @@ typedef enum {
 /* Operator flags */
 #define VAMRT_ACCUMULATE   1u  /* add into the output instead of overwriting it */
 #define VAMRT_CLAMP_NONNEG 2u  /* adjoint only: write max(0, result) (OSMO's clamp, Sec. 2.7) */
+#define VAMRT_UNATTENUATED 4u  /* adjoint only: the paper-literal projection of Sec. 2.4, the sum of
+                                  the (trilinear-weighted) voxels each ray crosses: weight
+                                  delta / M per sample, no Fresnel or Beer-Lambert factor (no
+                                  longer the transpose of the dose operator) */
 
 /*
  * Printer, vial and grid description (Sec. 2.1, 2.5, 2.6).  All lengths in mm.
@@ -124,7 +128,7 @@ vamrt_status vamrt_sample_count(const vamrt_projector *p, uint64_t *samples_per_
  *   proj[k][v][u] = sum_a sum_j c_j sum_{8 corners} w_c vol[c],
  *   c_j = (T1 T2 / M) exp(-mu s_j) delta,  w_c = trilinear weight (Sec. 2.2).
  * vol: device [nz][ny][nx] of vol_dtype; proj: device [n_angles][nv][nu] of proj_dtype.
- * flags: VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG.  Uses the handle's scratch volume.
+ * flags: VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG, VAMRT_UNATTENUATED.  Uses the handle's scratch volume.
  * Errors: EINVAL (NULL pointers, unknown dtype/flags), ECUDA.
  */
 vamrt_status vamrt_adjoint(vamrt_projector *p, const void *vol, vamrt_dtype vol_dtype,
@@ -298,6 +302,18 @@ vamrt_status vamrt_nn_head_mse(const float *z, int32_t cz, const float *base, fl
 vamrt_status vamrt_nn_add(const void *x, void *y, int64_t n, void *stream);
 vamrt_status vamrt_projected_step(float *g, const float *grad, float eta, int64_t n, void *stream);
 vamrt_status vamrt_nn_absmax(const float *x, int64_t n, float *out, void *stream);
+
+/*
+ * 8-bit export of projections before the final dose simulation (Sec. 2.7: values more
+ * than three standard deviations above the mean are clipped and the range is rescaled
+ * to the projector's 8-bit grey levels).  c = mean + 3 sigma over all n_angles x nv x nu
+ * values (population sigma, FP64); codes[i] = round-half-even(255 min(max(g,0), c) / c).
+ * proj: device, projector layout, proj_dtype; codes: device uint8, same count; dequant:
+ * device f32 or NULL, = codes * c / 255 (what the printer delivers, for the final dose);
+ * clip: HOST double or NULL (then the call is asynchronous), receives c.
+ */
+vamrt_status vamrt_export_u8(vamrt_projector *p, const void *proj, vamrt_dtype proj_dtype, uint8_t *codes,
+                             float *dequant, double *clip, void *stream);
 
 /*
  * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index

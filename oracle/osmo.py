@@ -91,3 +91,12 @@ def osmo_projections(target, g0, project, dose, n_iter, alpha=1.0):
         errors.append(np.abs(dn - f).sum() / fsum)
         g = np.maximum(0.0, g + project(alpha * (f - dn)))
     return g, dn, np.array(errors)
+
+
+def export_u8(proj):
+    """8-bit export (Sec. 2.7, reading: upper clip at mean + 3 sigma, projections >= 0):
+    codes = round-half-even(255 min(max(g, 0), c) / c), c = mean + 3 sigma (population)."""
+    g = np.asarray(proj, dtype=np.float64)
+    c = g.mean() + 3.0 * g.std()
+    codes = np.rint(255.0 * np.clip(g, 0.0, c) / c).astype(np.uint8)
+    return codes, c

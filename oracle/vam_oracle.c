@@ -46,6 +46,7 @@ typedef struct {
     int32_t n_angles;
     const double *angles;   /* radians */
     double step_vox;        /* nominal sample spacing in voxels */
+    int32_t unattenuated;   /* projection only: weight delta / M, no Fresnel or Beer-Lambert (Sec. 2.4 as printed) */
 } orc_geom;
 
 typedef struct {
@@ -185,6 +186,10 @@ static void sample(const orc_geom *g, const orc_ray *ray, int32_t j, double ct, 
     *factor = (ray->t1 * ray->t2 / g->m) * exp(-g->mu * s) * delta;
 }
 
+/* The projection exactly as Sec. 2.4 prints it: the sum, over each ray, of the voxels it
+ * crosses (trilinear weights, step delta), averaged over the pixel's rays. */
+static double unattenuated_factor(const orc_geom *g, const orc_ray *ray) { return (ray->ell / ray->k) / g->m; }
+
 /* One projection pixel: y[k][v][u] = sum_a sum_j factor_j sum_corners w_c V[c]. */
 double orc_adjoint_pixel(const orc_geom *g, const double *vol, int32_t k, int32_t v, int32_t u)
 {
@@ -196,6 +201,7 @@ double orc_adjoint_pixel(const orc_geom *g, const double *vol, int32_t k, int32_
         for (int32_t j = 0; j < ray.k; ++j) {
             double q[3], fac;
             sample(g, &ray, j, ct, st, q, &fac);
+            if (g->unattenuated) fac = unattenuated_factor(g, &ray);
             corners8 c;
             trilinear(g, q, &c);
             for (int i = 0; i < c.n; ++i) acc += fac * c.w[i] * vol[c.idx[i]];

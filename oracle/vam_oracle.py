@@ -43,6 +43,7 @@ class OrcGeom(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("n_angles", ctypes.c_int32), ("angles", _dp),
         ("step_vox", ctypes.c_double),
+        ("unattenuated", ctypes.c_int32),
     ]
 
 
@@ -96,7 +97,7 @@ def lib():
 class _Geom:
     """Keeps the numpy arrays the C struct points to alive."""
 
-    def __init__(self, w, pupil_xy, angles):
+    def __init__(self, w, pupil_xy, angles, unattenuated=False):
         self.pupil_xy = np.ascontiguousarray(pupil_xy, dtype=np.float64).reshape(-1, 2)
         self.angles = np.ascontiguousarray(angles, dtype=np.float64).ravel()
         g = OrcGeom()
@@ -111,6 +112,7 @@ class _Geom:
         g.n_angles = self.angles.size
         g.angles = self.angles.ctypes.data_as(_dp)
         g.step_vox = w.step_vox
+        g.unattenuated = 1 if unattenuated else 0
         self.g = g
 
     @property
@@ -123,10 +125,10 @@ def _angles_default(n):
     return 2.0 * np.pi * np.arange(n, dtype=np.float64) / n
 
 
-def geom(w, pupil_xy, angles=None) -> _Geom:
+def geom(w, pupil_xy, angles=None, unattenuated=False) -> _Geom:
     if angles is None:
         angles = _angles_default(w.n_angles)
-    return _Geom(w, pupil_xy, angles)
+    return _Geom(w, pupil_xy, angles, unattenuated)
 
 
 def trace(w, pupil_xy, u, v, a) -> dict:
@@ -139,9 +141,10 @@ def trace(w, pupil_xy, u, v, a) -> dict:
     return out
 
 
-def adjoint(w, vol, pupil_xy, angles=None) -> np.ndarray:
-    """Sec. 2.4 projection of a volume [nz][ny][nx] -> projections [n_angles][nv][nu] (FP64)."""
-    G = geom(w, pupil_xy, angles)
+def adjoint(w, vol, pupil_xy, angles=None, unattenuated=False) -> np.ndarray:
+    """Sec. 2.4 projection of a volume [nz][ny][nx] -> projections [n_angles][nv][nu] (FP64).
+    unattenuated: the projection exactly as printed (no Fresnel / Beer-Lambert factors)."""
+    G = geom(w, pupil_xy, angles, unattenuated)
     v = np.ascontiguousarray(vol, dtype=np.float64)
     assert v.shape == (w.nz, w.ny, w.nx)
     out = np.zeros((G.angles.size, w.nv, w.nu), dtype=np.float64)

@@ -40,6 +40,7 @@ struct OpParams {
     float neg_mu_vox_log2e;  // -mu h log2(e): attenuation = exp2(this * s_vox)
     float y0;             // start of chunk 0 on the theta = 0 frame's y axis, voxels
     float cell_bound;     // most samples of one ray whose footprint holds a given voxel
+    float h_over_m;       // voxel pitch (mm) / rays per pixel: delta_mm / M = delta_vox * h_over_m
 };
 
 // Per-ray constants of the FP64 tracer.
@@ -133,6 +134,10 @@ cudaError_t nn_head_mse(const float *z, int cz, const float *base, float in_scal
 cudaError_t nn_add(const void *x, void *y, int64_t n, cudaStream_t s);
 cudaError_t nn_projected_step(float *g, const float *grad, float eta, int64_t n, cudaStream_t s);
 cudaError_t nn_absmax(const float *x, int64_t n, float *out, cudaStream_t s);
+
+// export.cu (8-bit export of projections, Sec. 2.7)
+cudaError_t launch_export_u8(const vamrt_projector *p, const void *proj, vamrt_dtype dt, unsigned char *codes,
+                             float *dequant, double *clip, cudaStream_t s);
 
 // osmo.cu
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);

@@ -117,7 +117,7 @@ struct Ray {
     int jlo, jhi;
 };
 
-__device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 cs, Ray &R)
+__device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 cs, Ray &R, bool unattenuated)
 {
     const int2 J = P.J[r];
     if (J.x >= J.y) return false;
@@ -137,8 +137,9 @@ __device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 
     R.sx = __double2ll_rn(stx * kFix);
     R.sy = __double2ll_rn(sty * kFix);
     R.sz = __double2ll_rn(stz * kFix);
-    R.att = P.neg_mu_vox_log2e * A.w;
-    R.w = B.w;
+    // the paper-literal projection (Sec. 2.4): no Beer-Lambert or Fresnel factor, weight delta / M
+    R.att = unattenuated ? 0.f : P.neg_mu_vox_log2e * A.w;
+    R.w = unattenuated ? A.w * P.h_over_m : B.w;
     R.ey = A.y;
     R.dy = A.w * B.y;
     R.jlo = J.x;
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
         const int ra = a % 3;
         Ray R;
         bool active = valid && (!FWD || g != 0.f);
-        if (active) active = ray_begin(P, ((int64_t)a * P.nv + v) * P.nu + u, cs, R);
+        if (active) active = ray_begin(P, ((int64_t)a * P.nv + v) * P.nu + u, cs, R, !FWD && (flags & VAMRT_UNATTENUATED));
         int cf = INT_MAX, cl = INT_MIN;
         if (active) {
             cf = chunk_of(P, R, R.jlo);

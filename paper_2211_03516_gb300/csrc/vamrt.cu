@@ -230,6 +230,7 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     P.cy = 0.5 * (g.ny - 1) + 1.0;
     P.cz = 0.5 * (g.nz - 1) + 1.0;
     P.neg_mu_vox_log2e = (float)(-g.mu_per_mm * g.voxel_mm * M_LOG2E);
+    P.h_over_m = (float)(g.voxel_mm / M);
     // chunk 0 starts one voxel in front of the resin cylinder
     P.y0 = (float)(-g.r_inner_mm / g.voxel_mm - 1.0);
     // a segment crosses the (-1,1)^3 neighbourhood of a voxel over at most 2 sqrt(3)
@@ -265,7 +266,8 @@ vamrt_status vamrt_adjoint(vamrt_projector *p, const void *vol, vamrt_dtype vol_
 {
     if (!p || !vol || !proj) return fail(VAMRT_EINVAL, "NULL argument");
     if (check_dtype(vol_dtype) || check_dtype(proj_dtype)) return VAMRT_EINVAL;
-    if (flags & ~(VAMRT_ACCUMULATE | VAMRT_CLAMP_NONNEG)) return fail(VAMRT_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(VAMRT_ACCUMULATE | VAMRT_CLAMP_NONNEG | VAMRT_UNATTENUATED))
+        return fail(VAMRT_EINVAL, "unknown flags 0x%x", flags);
     cudaStream_t s = (cudaStream_t)stream;
     CK(vamrt::launch_pad(p, vol, vol_dtype, s), "pad kernel");
     CK(vamrt::launch_adjoint(p, vol_dtype, proj, proj_dtype, flags, s), "adjoint kernel");
@@ -413,6 +415,21 @@ vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, 
     CK(vamrt::launch_conv3d_tc(x, w, bias, y, out_f32, d, h, wd, cin, cout, taps, relu, (int *)err_flag,
                                (cudaStream_t)stream),
        "conv3d kernel");
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_export_u8(vamrt_projector *p, const void *proj, vamrt_dtype proj_dtype, uint8_t *codes,
+                             float *dequant, double *clip, void *stream)
+{
+    if (!p || !proj || !codes) return fail(VAMRT_EINVAL, "NULL argument");
+    if (check_dtype(proj_dtype)) return VAMRT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dclip = p->red + vamrt::kRedBlocks + 1;
+    CK(vamrt::launch_export_u8(p, proj, proj_dtype, codes, dequant, dclip, s), "export kernels");
+    if (clip) {
+        CK(cudaMemcpyAsync(clip, dclip, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+    }
     return VAMRT_OK;
 }
 

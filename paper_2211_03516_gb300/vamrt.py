@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libvamrt.so")
 
 VAMRT_OK, VAMRT_EINVAL, VAMRT_EUNSUPPORTED, VAMRT_ECUDA, VAMRT_ENOMEM, VAMRT_NOT_CONVERGED, VAMRT_NUMERIC = range(7)
 VAMRT_F32, VAMRT_BF16 = 0, 1
-VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG = 1, 2
+VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG, VAMRT_UNATTENUATED = 1, 2, 4
 
 _DTYPES = {torch.float32: VAMRT_F32, torch.bfloat16: VAMRT_BF16}
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
         L.vamrt_voxel_error_rate.argtypes = [vp, vp, i32, vp, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int32), vp]
         L.vamrt_voxel_error_rate.restype = i32
+        L.vamrt_export_u8.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+        L.vamrt_export_u8.restype = i32
         L.vamrt_measure_smem_bandwidth.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.vamrt_measure_smem_bandwidth.restype = i32
         L.vamrt_launch_count.argtypes = []
@@ -241,13 +243,15 @@ class Projector:
         return a4, b4, j2
 
     def adjoint(self, vol: torch.Tensor, out: Optional[torch.Tensor] = None, proj_dtype=torch.float32,
-                accumulate=False, clamp_nonneg=False, stream=None) -> torch.Tensor:
-        """A^T: volume [nz][ny][nx] -> projections [n_angles][nv][nu] (vamrt_adjoint)."""
+                accumulate=False, clamp_nonneg=False, unattenuated=False, stream=None) -> torch.Tensor:
+        """A^T: volume [nz][ny][nx] -> projections [n_angles][nv][nu] (vamrt_adjoint).
+        unattenuated: the paper-literal projection (no Fresnel / Beer-Lambert factors)."""
         if out is None:
             out = torch.empty(self.proj_shape, device=vol.device, dtype=proj_dtype)
         vp = _dev_ptr(vol, self.vol_shape, "vol")
         pp = _dev_ptr(out, self.proj_shape, "proj")
-        flags = (VAMRT_ACCUMULATE if accumulate else 0) | (VAMRT_CLAMP_NONNEG if clamp_nonneg else 0)
+        flags = ((VAMRT_ACCUMULATE if accumulate else 0) | (VAMRT_CLAMP_NONNEG if clamp_nonneg else 0)
+                 | (VAMRT_UNATTENUATED if unattenuated else 0))
         _check(lib().vamrt_adjoint(self.handle, vp, _DTYPES[vol.dtype], pp, _DTYPES[out.dtype], flags,
                                    _stream(stream)), "vamrt_adjoint")
         return out
@@ -285,6 +289,16 @@ class Projector:
                                             ctypes.byref(ver), ctypes.byref(idx), _stream(stream)),
                "vamrt_voxel_error_rate")
         return float(ver.value), int(idx.value)
+
+    def export_u8(self, proj: torch.Tensor, stream=None):
+        """(uint8 codes, dequantised f32 projections, clip value c) (vamrt_export_u8)."""
+        pp = _dev_ptr(proj, self.proj_shape, "proj")
+        codes = torch.empty(self.proj_shape, device=proj.device, dtype=torch.uint8)
+        deq = torch.empty(self.proj_shape, device=proj.device, dtype=torch.float32)
+        clip = ctypes.c_double()
+        _check(lib().vamrt_export_u8(self.handle, pp, _DTYPES[proj.dtype], codes.data_ptr(), deq.data_ptr(),
+                                     ctypes.byref(clip), _stream(stream)), "vamrt_export_u8")
+        return codes, deq, float(clip.value)
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,

@@ -320,3 +320,36 @@ def test_projection_space_optimiser_matches_oracle(vamrt):
     np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
     assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
     assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL
+
+
+def test_unattenuated_projection_matches_oracle(vamrt):
+    w = REFRACT_SMALL
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    V = I.random_volume(w, seed=17)
+    y = P.adjoint(gpu(V), unattenuated=True)
+    assert rel_l2(y.cpu().numpy(), O.adjoint(w, V, pupil, unattenuated=True)) <= FP32_TOL
+
+
+def test_export_u8_matches_oracle_and_feeds_the_final_dose(vamrt):
+    """Sec. 2.7: the optimised projections are exported as 8-bit codes (clip at mean +
+    3 sigma) before the final dose simulation.  Codes agree with the oracle's except where
+    the oracle's value sits within 1e-9 of a rounding tie."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = gpu(I.make_target(w))
+    res = P.optimize(f, max_iter=5, tol=0.0)
+    codes, deq, c = P.export_u8(res["proj"])
+    g = res["proj"].cpu().numpy()
+    ref, c_ref = OS.export_u8(g)
+    assert abs(c - c_ref) <= 1e-12 * c_ref
+    x = 255.0 * np.clip(g.astype(np.float64), 0, c_ref) / c_ref
+    near_tie = np.abs(x - np.floor(x) - 0.5) < 1e-9
+    mismatch = codes.cpu().numpy() != ref
+    assert not np.any(mismatch & ~near_tie)
+    np.testing.assert_allclose(deq.cpu().numpy(), codes.cpu().numpy() * (c / 255.0), rtol=1e-6)
+    d8 = P.forward_dose(deq)
+    ver8, _ = P.voxel_error_rate(d8, f)
+    ver, _ = P.voxel_error_rate(res["dose"], f)
+    assert ver8 < 2.0 * ver + 0.01

@@ -419,3 +419,27 @@ def test_conv3d_oracle_against_scalar_loops():
     # 1x1x1 is a per-voxel matrix product
     w1 = rng.standard_normal((Cout, 1, Cin))
     np.testing.assert_allclose(C.conv3d(x, w1), x @ w1[:, 0, :].T, rtol=1e-14)
+
+
+def test_unattenuated_projection_removes_fresnel_and_absorption():
+    """Sec. 2.4's projection as printed: with one ray per pixel it equals the attenuated
+    projection at mu = 0 divided by the ray's Fresnel product T1 T2."""
+    w = refracting_w(pupil_pattern="chief", rays_per_pixel=1, f_number=INF, mu_per_mm=0.4, n_angles=3)
+    V = np.random.default_rng(6).random(w.vol_shape)
+    y_lit = O.adjoint(w, V, CHIEF, unattenuated=True)
+    y_mu0 = O.adjoint(w.scaled(mu_per_mm=0.0), V, CHIEF)
+    for (v, u) in [(3, 10), (1, 4), (5, 16), (0, 0)]:
+        r = O.trace(w, CHIEF, u, v, 0)
+        expect = y_mu0[:, v, u] / (r["t1"] * r["t2"]) if r["status"] == 2 else 0.0 * y_mu0[:, v, u]
+        np.testing.assert_allclose(y_lit[:, v, u], expect, rtol=1e-12, atol=1e-14)
+
+
+def test_export_u8_codes():
+    """Clip at mean + 3 sigma, 255 levels, round half to even."""
+    g = np.array([0.0, 1.0, 2.0, 3.0, 100.0] + [1.0] * 20)
+    codes, c = OS.export_u8(g)
+    assert abs(c - (g.mean() + 3 * g.std())) < 1e-12
+    assert codes[4] == 255 and codes[0] == 0
+    np.testing.assert_array_equal(codes[1:4], np.rint(255 * g[1:4] / c).astype(np.uint8))
+    codes2, _ = OS.export_u8(np.array([0.5, 1.5, 1.0, 1.0]))   # c = 1 + 3 * sqrt(1/8)
+    assert codes2.dtype == np.uint8 and codes2.max() <= 255
