@@ -233,6 +233,43 @@ def warm_start_time_to_target(args):
     t2 = time.perf_counter()
     rows = WS.compare(P, net, w, range(100000, 100000 + args.ws_eval), plain_iters=w.osmo_iters,
                       cont_iters=12, step=0.5, dtype=torch.bfloat16)
+    # tensor-core throughput of the network's convolutions (forward and full training step)
+    y = pairs[0][1]
+    A = y.shape[0]
+    Dp = WS.padded_angles(A)
+    x0 = net.prepare(y, 1.0, Dp)
+    fl = net.forward_flops(Dp, y.shape[1], y.shape[2])
+    for _ in range(2):
+        net.forward(x0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        net.forward(x0)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 5
+    e0.record()
+    for _ in range(3):
+        net.zero_grad()
+        z = net.forward(x0)
+        _, _, dz = net.head(z, y, 1.0, target=pairs[0][2], want_grad=True)
+        net.backward(dz)
+    e1.record()
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / 3
+    peak_tf = 1924.8
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak_tf = float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        pass
+    network = {"input": [Dp, y.shape[1], y.shape[2], 16], "forward_ms": fwd_ms, "train_step_ms": step_ms,
+               "forward_flops": fl,
+               "roofline": {"bound": "tensor", "achieved": fl / (fwd_ms / 1e3) / 1e12, "peak": peak_tf,
+                            "unit": "TFLOP/s", "frac": fl / (fwd_ms / 1e3) / 1e12 / peak_tf,
+                            "peak_kind": "measured (bf16 burst)"},
+               "train_step_tflops": 3 * fl / (step_ms / 1e3) / 1e12}
+
     held = []
     for r in rows:
         ratio = None if r["warm_seconds_to_target"] is None else r["warm_seconds_to_target"] / r["plain_seconds"]
@@ -246,6 +283,7 @@ def warm_start_time_to_target(args):
             "train_pairs": len(pairs), "pair_iterations": w.osmo_iters, "epochs": args.ws_epochs,
             "data_generation_seconds": t1 - t0, "training_seconds": t2 - t1, "final_train_loss": losses[-1],
             "continuation": "projection space, BF16-stored projections and dose, relaxation 0.5",
+            "network": network,
             "held_out": held, "reached": f"{len(ratios)}/{len(held)}",
             "median_time_ratio_of_reached": float(np.median(ratios)) if ratios else None}
 

@@ -239,6 +239,7 @@ __device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, in
     float att = exp2f(R.att * ((float)jl + 0.5f));
     const float ratio = exp2f(R.att);
     float acc = 0.f;
+#pragma unroll 2
     for (int j = jl; j < jh; ++j) {
         const Cell c = cell_of(P, qx, qy, qz);
         const int b = addr(c);
@@ -327,6 +328,7 @@ __device__ __forceinline__ void walk_scatter_box(const OpParams &P, const Ray &R
     float att = exp2f(R.att * ((float)jl + 0.5f));
     const float ratio = exp2f(R.att);
     const float ws = wray * scale;
+#pragma unroll 2
     for (int j = jl; j < jh; ++j) {
         const Cell c = cell_of(P, qx, qy, qz);
         int *p = box + addr(c);
@@ -459,12 +461,32 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
             const float inv_ex4 = 1.0f / (float)ex4, inv_ey = 1.0f / (float)ey;
             if ((long long)sxy * ez <= kBoxFloats) {
                 if (!FWD) {
-                    for (int i = tid; i < n4; i += kThreads) {
-                        const int t = fdiv(i, inv_ex4), x4 = i - t * ex4;
-                        const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
-                        const float4 q = ld4(vol + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
-                        float *b = box + zz * sxy + yy * sx + 4 * x4;
-                        b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
+                    if (ex4 <= kThreads) {
+                        // thread -> (row r0, 16-byte group x4) once; rows advance by `per`
+                        const int per = kThreads / ex4;
+                        const int r0 = fdiv(tid, inv_ex4), x4 = tid - r0 * ex4;
+                        if (r0 < per) {
+                            int zz = fdiv(r0, inv_ey), yy = r0 - zz * ey;
+                            const int dq = fdiv(per, inv_ey), dr = per - dq * ey;
+                            const VT *src = vol + (int64_t)bz0 * pxy + (int64_t)by0 * P.px + bx0 + 4 * x4;
+                            for (int r = r0; r < ey * ez; r += per) {
+                                const float4 q = ld4(src + (int64_t)zz * pxy + (int64_t)yy * P.px);
+                                float *b = box + zz * sxy + yy * sx + 4 * x4;
+                                b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
+                                zz += dq;
+                                yy += dr;
+                                if (yy >= ey) { yy -= ey; ++zz; }
+                            }
+                        }
+                    } else {
+                        for (int i = tid; i < n4; i += kThreads) {
+                            const int t = fdiv(i, inv_ex4), x4 = i - t * ex4;
+                            const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
+                            const float4 q =
+                                ld4(vol + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
+                            float *b = box + zz * sxy + yy * sx + 4 * x4;
+                            b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
+                        }
                     }
                 } else {
                     for (int i = tid; i < sxy * ez; i += kThreads) box[i] = 0.f;

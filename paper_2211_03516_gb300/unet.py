@@ -314,6 +314,14 @@ class UNet3D:
             V._check(L.vamrt_nn_adam(ly.b.data_ptr(), ly.gb.data_ptr(), ly.mb.data_ptr(), ly.vb.data_ptr(), None,
                                      ly.b.numel(), lr, beta1, beta2, eps, self.step_count, _s()), "adam")
 
+    LEVEL = {"enc0a": 0, "enc0b": 0, "enc1a": 1, "enc1b": 1, "enc2a": 2, "enc2b": 2, "bota": 3, "botb": 3,
+             "dec2a": 2, "dec2b": 2, "dec1a": 1, "dec1b": 1, "dec0a": 0, "dec0b": 0, "head": 0}
+
+    def forward_flops(self, d_padded, nv, nu):
+        """Multiply-add FLOPs (2 per MAC) of the convolutions of one forward pass."""
+        p0 = d_padded * nv * nu
+        return sum(2.0 * (p0 / 8 ** self.LEVEL[n]) * L.cin * L.cout * L.taps for n, L in self.layers.items())
+
     def state_dict(self):
         return {n: (L.W.cpu(), L.b.cpu()) for n, L in self.layers.items()}
 
