@@ -208,6 +208,70 @@ def time_to_target(P, target, w, iters):
     }
 
 
+def network_throughput(net, y, g, scale, fwd_reps=5, step_reps=3):
+    """Tensor-core throughput of the warm-start network's convolutions: one forward pass
+    and one training step (forward, head, backward) on projections y [A][nv][nu]."""
+    import torch
+
+    from paper_2211_03516_gb300 import warmstart as WS
+
+    Dp = WS.padded_angles(y.shape[0])
+    x0 = net.prepare(y, scale, Dp)
+    fl = net.forward_flops(Dp, y.shape[1], y.shape[2])
+    for _ in range(2):
+        net.forward(x0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(fwd_reps):
+        net.forward(x0)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / fwd_reps
+    e0.record()
+    for _ in range(step_reps):
+        net.zero_grad()
+        z = net.forward(x0)
+        _, _, dz = net.head(z, y, scale, target=g, want_grad=True, target_scale=scale)
+        net.backward(dz)
+    e1.record()
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / step_reps
+    peak_tf = 1924.8
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak_tf = float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        pass
+    tf = fl / (fwd_ms / 1e3) / 1e12
+    return {"input": [Dp, y.shape[1], y.shape[2], 16], "forward_ms": fwd_ms, "train_step_ms": step_ms,
+            "forward_flops": fl,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": tf / peak_tf, "peak_kind": "measured (bf16 burst)"},
+            "train_step_tflops": 3 * fl / (step_ms / 1e3) / 1e12}
+
+
+def run_network_only(args):
+    """The warm-start network alone on the 128^3 workload's projection shape (random
+    weights, A^T f of one synthetic target as input): timing and profiling of the
+    convolution kernels without the data generation and training."""
+    import torch
+
+    from paper_2211_03516_gb300 import inputs as I
+    from paper_2211_03516_gb300 import unet as U
+    from paper_2211_03516_gb300 import vamrt
+
+    w = I.WORKLOADS["warmstart_128cube_180ang_4rays"]
+    P = vamrt.Projector.from_workload(w, I.workload_pupil(w))
+    f = torch.from_numpy(I.make_target(w, seed=0)).to("cuda:0")
+    y = P.adjoint(f)
+    s = 1.0 / float(y.max())
+    net = U.UNet3D("cuda", seed=0)
+    out = network_throughput(net, y, y, s, fwd_reps=args.steps, step_reps=max(1, args.steps // 2))
+    U.check_errors(net.device)
+    out.update({"workload": w.name, "n_angles": w.n_angles})
+    print(json.dumps(out), flush=True)
+
+
 def warm_start_time_to_target(args):
     """Learned warm start on the 128^3 workload (180 angles, 128^2 pixels, 4 rays): train on
     pairs the plain FP32 optimiser produces, then on held-out targets time (inference + the
@@ -233,42 +297,7 @@ def warm_start_time_to_target(args):
     t2 = time.perf_counter()
     rows = WS.compare(P, net, w, range(100000, 100000 + args.ws_eval), plain_iters=w.osmo_iters,
                       cont_iters=12, step=0.5, dtype=torch.bfloat16)
-    # tensor-core throughput of the network's convolutions (forward and full training step)
-    y = pairs[0][1]
-    A = y.shape[0]
-    Dp = WS.padded_angles(A)
-    x0 = net.prepare(y, 1.0, Dp)
-    fl = net.forward_flops(Dp, y.shape[1], y.shape[2])
-    for _ in range(2):
-        net.forward(x0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(5):
-        net.forward(x0)
-    e1.record()
-    e1.synchronize()
-    fwd_ms = e0.elapsed_time(e1) / 5
-    e0.record()
-    for _ in range(3):
-        net.zero_grad()
-        z = net.forward(x0)
-        _, _, dz = net.head(z, y, 1.0, target=pairs[0][2], want_grad=True)
-        net.backward(dz)
-    e1.record()
-    e1.synchronize()
-    step_ms = e0.elapsed_time(e1) / 3
-    peak_tf = 1924.8
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peak_tf = float(json.load(fh)["bf16_tflops"])
-    except Exception:
-        pass
-    network = {"input": [Dp, y.shape[1], y.shape[2], 16], "forward_ms": fwd_ms, "train_step_ms": step_ms,
-               "forward_flops": fl,
-               "roofline": {"bound": "tensor", "achieved": fl / (fwd_ms / 1e3) / 1e12, "peak": peak_tf,
-                            "unit": "TFLOP/s", "frac": fl / (fwd_ms / 1e3) / 1e12 / peak_tf,
-                            "peak_kind": "measured (bf16 burst)"},
-               "train_step_tflops": 3 * fl / (step_ms / 1e3) / 1e12}
+    network = network_throughput(net, pairs[0][1], pairs[0][2], 1.0)
 
     held = []
     for r in rows:
@@ -454,11 +483,15 @@ def main():
     ap.add_argument("--ws-train", type=int, default=64, help="warm-start training targets (0 = skip)")
     ap.add_argument("--ws-epochs", type=int, default=8)
     ap.add_argument("--ws-eval", type=int, default=4, help="held-out targets for the warm-start comparison")
+    ap.add_argument("--network-only", action="store_true",
+                    help="time the warm-start network's convolutions alone and print their JSON")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.network_only:
+        run_network_only(args)
     else:
         run_gpu(args, rank, world)
 

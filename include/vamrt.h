@@ -256,6 +256,16 @@ vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, 
                                int32_t *err_flag, void *stream);
 
 /*
+ * vamrt_conv3d_tiling: which kernel vamrt_conv3d_bf16 runs for this shape on the current
+ * device, written to out[4] (host array): out[0] = 1 for the halo-tile kernel (W % 8 == 0;
+ * regions of out[1] planes x out[2] rows, out[3] output channels per work item), 0 for the
+ * gather kernel (out[1..3] = 0).  Host-only query, launches nothing.  Errors: EINVAL (NULL or
+ * sizes vamrt_conv3d_bf16 rejects), ECUDA (no device).
+ */
+vamrt_status vamrt_conv3d_tiling(int32_t d, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                 int32_t *out);
+
+/*
  * Building blocks of the learned warm start (a 3D U-Net on the projection stack; the paper
  * has no such network -- its optimiser starts from the target, Sec. 2.7).  Activations are
  * channels-last BF16 [d][h][w][c] device arrays; gradients of weights and biases are FP32.

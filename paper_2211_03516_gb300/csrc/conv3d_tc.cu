@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace vamrt {
 namespace {
@@ -29,95 +30,10 @@ constexpr int kM = 128;
 constexpr int kStageA = kM * 16 * 2;   // 4 KB
 constexpr int kMaxCout = 256;
 constexpr int kStageB = kMaxCout * 16 * 2;   // 8 KB
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+using namespace tc;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait for the completion of the mbarrier phase with this parity
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try(bar, parity))
-        if (globaltimer() - t0 > kWaitNs) return false;
-    return true;
-}
-
-// Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B (between the two
-// 8-element K groups), SBO = 256 B (between 8-row groups), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(256 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N.
-__device__ __forceinline__ uint32_t instr_desc(int n)
-{
-    uint32_t d = 0;
-    d |= 1u << 4;                       // D format F32
-    d |= 1u << 7;                       // A format BF16
-    d |= 1u << 10;                      // B format BF16
-    d |= (uint32_t)(n >> 3) << 17;      // N / 8
-    d |= (uint32_t)(kM >> 4) << 24;     // M / 16
-    return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) { return tc::smem_desc(addr, 128, 256); }
+__device__ __forceinline__ uint32_t instr_desc(int n) { return tc::instr_desc(kM, n); }
 
 // byte offset of element row r, 16-byte half h (channels 8h..8h+7) in a staged tile
 __device__ __forceinline__ int core_off(int r, int h) { return (r >> 3) * 256 + h * 128 + (r & 7) * 16; }
@@ -411,11 +327,13 @@ cudaError_t launch_conv3d_wgrad_tc(const void *X, const void *dY, float *dW, int
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s)
 {
+    // the halo-tile kernel takes every shape with W % 8 == 0; this gather kernel the rest
+    cudaError_t e = launch_conv3d_halo(X, Wt, bias, Y, out_f32, D, H, W, Cin, Cout, taps, relu, err, s);
+    if (e != cudaErrorNotSupported) return e;
     const int64_t P = (int64_t)D * H * W;
     const unsigned grid = (unsigned)((P + kM - 1) / kM);
     const size_t smem = 2 * kStageA + 2 * kStageB;
     const __nv_bfloat16 *x = (const __nv_bfloat16 *)X, *w = (const __nv_bfloat16 *)Wt;
-    cudaError_t e = cudaSuccess;
 #define VAMRT_CONV(T, OT)                                                                                         \
     do {                                                                                                          \
         e = cudaFuncSetAttribute(conv3d_tc_kernel<T, OT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \

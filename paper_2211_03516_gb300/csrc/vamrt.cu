@@ -410,11 +410,30 @@ vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, 
     if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256)
         return fail(VAMRT_EINVAL, "channels: cin a multiple of 16, cout a multiple of 16 in 16..256");
     if (taps != 1 && taps != 27) return fail(VAMRT_EINVAL, "taps must be 1 or 27");
-    if (((uintptr_t)x | (uintptr_t)w) & 15) return fail(VAMRT_EINVAL, "x and w must be 16-byte aligned");
+    if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) & 15) return fail(VAMRT_EINVAL, "x, w and y must be 16-byte aligned");
     if ((int64_t)d * h * wd * (cin > cout ? cin : cout) >= ((int64_t)1 << 40)) return fail(VAMRT_EINVAL, "too large");
     CK(vamrt::launch_conv3d_tc(x, w, bias, y, out_f32, d, h, wd, cin, cout, taps, relu, (int *)err_flag,
                                (cudaStream_t)stream),
        "conv3d kernel");
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_conv3d_tiling(int32_t d, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                 int32_t *out)
+{
+    if (!out) return fail(VAMRT_EINVAL, "NULL argument");
+    if (d < 1 || h < 1 || wd < 1 || cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256 ||
+        (taps != 1 && taps != 27))
+        return fail(VAMRT_EINVAL, "shape not accepted by vamrt_conv3d_bf16");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev), "device");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+    vamrt::ConvHaloPlan pl;
+    if (vamrt::plan_conv3d_halo(d, h, wd, cin, cout, taps, sms, &pl)) {
+        out[0] = 1; out[1] = pl.TZ; out[2] = pl.TY; out[3] = pl.Nt;
+    } else {
+        out[0] = out[1] = out[2] = out[3] = 0;
+    }
     return VAMRT_OK;
 }
 

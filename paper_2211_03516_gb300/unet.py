@@ -15,6 +15,8 @@ def _lib():
         vp, i32 = ctypes.c_void_p, ctypes.c_int32
         L.vamrt_conv3d_bf16.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp]
         L.vamrt_conv3d_bf16.restype = ctypes.c_int
+        L.vamrt_conv3d_tiling.argtypes = [i32, i32, i32, i32, i32, i32, vp]
+        L.vamrt_conv3d_tiling.restype = ctypes.c_int
         L._conv_ready = True
     return L
 
@@ -49,6 +51,15 @@ def conv3d(x: torch.Tensor, w: torch.Tensor, bias: torch.Tensor | None = None, r
                                   1 if relu else 0, err.data_ptr(), torch.cuda.current_stream().cuda_stream)
     V._check(st, "vamrt_conv3d_bf16")
     return out
+
+
+def conv3d_tiling(D, H, W, cin, cout, taps):
+    """(kernel, TZ, TY, Nt) that conv3d uses for this shape on the current device: kernel 1
+    = halo-tile (regions of TZ planes x TY rows, Nt output channels per work item), 0 =
+    the gather kernel."""
+    out = (ctypes.c_int32 * 4)()
+    V._check(_lib().vamrt_conv3d_tiling(D, H, W, cin, cout, taps, out), "vamrt_conv3d_tiling")
+    return tuple(int(v) for v in out)
 
 
 def check_errors(device="cuda:0"):

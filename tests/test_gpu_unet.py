@@ -23,13 +23,23 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+# W % 8 != 0 runs the gather kernel, W % 8 == 0 the halo-tile kernel (both checked below)
 @pytest.mark.parametrize("shape,cin,cout,taps", [
-    ((5, 7, 37), 16, 16, 27),     # ragged: 1295 positions = 10 full tiles + a tail
+    ((5, 7, 37), 16, 16, 27),     # gather: 1295 positions = 10 full tiles + a tail
     ((4, 6, 9), 32, 48, 27),
     ((3, 5, 11), 16, 128, 27),
     ((2, 3, 70), 64, 32, 27),
     ((6, 6, 6), 16, 16, 1),
-    ((4, 4, 8), 128, 16, 1),
+    ((4, 4, 8), 128, 16, 1),      # halo from here on
+    ((5, 7, 40), 16, 16, 27),     # tiles run through the rows of a plane; ragged regions
+    ((4, 6, 24), 48, 48, 27),     # three 16-channel chunks per region
+    ((3, 5, 128), 16, 32, 27),    # one tile per 128-voxel row
+    ((3, 5, 256), 16, 32, 27),    # two tiles per row
+    ((2, 3, 16), 16, 256, 27),    # output channels in slices
+    ((5, 6, 32), 16, 16, 1),
+    ((48, 128, 128), 16, 16, 27),  # several regions per block: both stages, both accumulators cycle
+    ((24, 64, 64), 48, 128, 27),
+    ((20, 32, 32), 64, 192, 27),
 ])
 def test_conv3d_matches_direct_convolution(U, shape, cin, cout, taps):
     rng = np.random.default_rng(cin + cout + taps)
@@ -39,6 +49,10 @@ def test_conv3d_matches_direct_convolution(U, shape, cin, cout, taps):
         torch.bfloat16)
     b = torch.from_numpy(rng.standard_normal(cout).astype(np.float32))
     ref = C.conv3d(x.float().numpy(), w.float().numpy(), b.numpy(), relu=False)
+    kind, tz, ty, nt = U.conv3d_tiling(D, H, W, cin, cout, taps)
+    assert kind == (1 if W % 8 == 0 else 0)
+    if kind == 1:
+        assert 1 <= tz <= D and 1 <= ty <= H and cout % nt == 0
     y32 = U.conv3d(x.to(DEV), w.to(DEV), b.to(DEV), relu=False, out_dtype=torch.float32)
     yr = U.conv3d(x.to(DEV), w.to(DEV), b.to(DEV), relu=True, out_dtype=torch.bfloat16)
     torch.cuda.synchronize()
