@@ -1,5 +1,5 @@
 // Halo-tiled 3x3x3 (or 1x1x1) convolution on the 5th-generation tensor cores: a
-// persistent, warp-specialised implicit GEMM whose input tiles arrive by TMA.
+// persistent, warp-specialised implicit GEMM.
 //
 //   Y[p][co] = act( bias[co] + sum_{t, ci} X[p + off(t)][ci] * Wt[co][t][ci] )
 //
@@ -12,10 +12,8 @@
 // 8-channel halves; each half is a run of 16-byte "slots" (8 bf16 channels of one voxel).
 // A row takes WP = W + 8 slots: W voxels, then 8 zero slots, which are at once the x = W
 // neighbour of this row and the x = -1 neighbour of the next (8 zero guard slots precede
-// the first row).  The TMA writes this padding itself: X is described to it as a 5-D
-// tensor (8 channels, 8 x, W / 8 x-groups, H, D) and the box asks for W / 8 + 1 x-groups,
-// the last of which lies outside the tensor and is zero-filled, as are halo rows and
-// planes outside the volume.
+// the first row).  Pads and guard are zeroed once per launch; halo rows and planes outside
+// the volume are zero-filled by the copies.
 //
 // GEMM mapping.  M = 128 consecutive slots of the region (TMEM lanes), N = Nt output
 // channels (TMEM columns), K = 16 channels of one tap per MMA.  Because the slot index is
@@ -24,20 +22,20 @@
 // data movement.  A core matrix is 8 consecutive slots (128 contiguous bytes); SBO = 128 B,
 // LBO = the distance between the two halves.  Tiles that start in padding or run past the
 // region compute rows that the epilogue discards.  B (weights of one chunk, all taps) is
-// staged by cp.async in the canonical K-major layout.
+// staged in the canonical K-major layout.
 //
-// Roles (192 threads): warps 0-3 drain TMEM (warp w owns lanes 32w..32w+31) and write Y;
-// warp 4 issues the TMA and weight copies into two shared-memory stages; one thread of
-// warp 5 issues the MMAs.  Two TMEM accumulators let the epilogue of one
-// region overlap the MMAs of the next.  Every wait is bounded: on timeout the block sets
-// the error flag, the other roles run out of their own waits, TMEM is freed and the
-// block returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
+// Staging is by cp.async rather than TMA: with channels-last activations a tensor-map box
+// could only move 16 bytes (one half of one voxel) per element, and measured at about one
+// element per five cycles per SM that starved the tensor core; four loader warps moving
+// coalesced 512-byte runs keep up.
+//
+// Roles (384 threads): warps 0-3 drain TMEM (warp w owns lanes 32w..32w+31) and write Y;
+// warps 4-7 copy input tiles and weights into two shared-memory stages; lane 0 of each
+// of warps 8-11 issues the MMAs of every fourth tile.  Two TMEM accumulators let the epilogue of one region overlap
+// the MMAs of the next.  Every wait is bounded: on timeout the block sets the error flag,
+// the other roles run out of their own waits, TMEM is freed and the block returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
-
-#include <mutex>
 
 #include "internal.cuh"
 #include "tcgen05.cuh"
@@ -47,19 +45,21 @@ namespace {
 
 using namespace tc;
 
-constexpr int kHaloThreads = 192;
+constexpr int kLoadWarp0 = 4, kLoadWarps = 4, kMmaWarp0 = 8, kMmaWarps = 4;
+constexpr int kHaloThreads = 384;   // 4 epilogue warps, 4 loader warps, 4 MMA warps
 constexpr int kGuard = 8;          // zero slots ahead of each staged half
 constexpr int kMaxTiles = 32;
 constexpr int kSmemLimit = 225 * 1024;
 
 struct HaloArgs {
-    const __nv_bfloat16 *Wt;
+    const __nv_bfloat16 *X, *Wt;
     const float *bias;
     void *Y;
     int *err;
     int D, H, W, Cin, Cout, relu;
-    int TZ, TY, WP, PT, T, Nt;      // region planes / rows, slot pitches, M tiles, columns per item
-    int half_bytes, x_bytes, stage_bytes, ncols;
+    int TZ, TY, WP, PT, T, Nt;      // region planes / rows, slot pitches, M tiles, channels per item
+    int NX, rowtile, mg, adv;       // dx taps per MMA; tile = one 128-voxel row; tile margin, advance
+    int half_bytes, stage_bytes, ncols;
     int ry, nslice, nitems;         // regions along y, channel slices, work items
 };
 
@@ -71,18 +71,21 @@ __device__ void halo_fail(volatile int *abort_flag, int *err)
     atomicExch(err, 1);
 }
 
-// warp 4: TMA loads of the input halves and cp.async copies of the weights, two stages
+// warps 4-7: cp.async copies of the input tile (both 8-channel halves; pairs of lanes
+// cover the 32 bytes of a voxel's chunk, a warp 16 consecutive voxels of one row; rows
+// outside the volume are zero-filled) and of the weights, into two stages
 template <int TAPS>
-__device__ void role_load(const CUtensorMap *xmap, const HaloArgs &a, uint32_t sbase, uint32_t full0,
-                          uint32_t empty0, volatile int *abort_flag)
+__device__ void role_load(const HaloArgs &a, uint32_t sbase, uint32_t full0, uint32_t empty0,
+                          volatile int *abort_flag)
 {
     constexpr int kHalo = TAPS == 27 ? 1 : 0;
-    const int lane = threadIdx.x & 31;
+    const int lt = threadIdx.x - kLoadWarp0 * 32, lane = lt & 31, lw = lt >> 5;
     const int nc = a.Cin >> 4;
+    const int RY = a.TY + 2 * kHalo, R = (a.TZ + 2 * kHalo) * RY;
     int i = 0;
     for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
         const int slice = item % a.nslice, r = item / a.nslice;
-        const int z0 = (r / a.ry) * a.TZ, y0 = (r % a.ry) * a.TY, co0 = slice * a.Nt;
+        const int z0 = (r / a.ry) * a.TZ - kHalo, y0 = (r % a.ry) * a.TY - kHalo, co0 = slice * a.Nt;
         for (int c = 0; c < nc; ++c, ++i) {
             const int s = i & 1;
             const uint32_t full = full0 + 8 * s, empty = empty0 + 8 * s;
@@ -95,16 +98,22 @@ __device__ void role_load(const CUtensorMap *xmap, const HaloArgs &a, uint32_t s
             }
             if (__any_sync(0xffffffffu, *abort_flag)) return;
             const uint32_t xs = sbase + s * a.stage_bytes;
-            if (lane == 0) {
-                mbar_expect_tx(full, 2u * a.x_bytes);
-                tma_load_5d(xs + kGuard * 16, xmap, c * 16, 0, 0, y0 - kHalo, z0 - kHalo, full);
-                tma_load_5d(xs + a.half_bytes + kGuard * 16, xmap, c * 16 + 8, 0, 0, y0 - kHalo, z0 - kHalo, full);
+            for (int row = lw; row < R; row += kLoadWarps) {
+                const int zb = row / RY, yb = row - zb * RY, z = z0 + zb, y = y0 + yb;
+                const bool in = z >= 0 && z < a.D && y >= 0 && y < a.H;
+                const __nv_bfloat16 *src = in ? a.X + (((int64_t)z * a.H + y) * a.W * a.Cin + c * 16) : a.X;
+                const uint32_t dst = xs + (uint32_t)(kGuard + row * a.WP) * 16;
+                for (int e = lane; e < 2 * a.W; e += 32) {
+                    const int x = e >> 1, h = e & 1;
+                    cp_async16_zfill(dst + h * a.half_bytes + x * 16, in ? src + (x * a.Cin + h * 8) : src, in ? 16 : 0);
+                }
             }
             const uint32_t wb = xs + 2 * a.half_bytes;
             const int ng = TAPS * a.Nt * 2;
-            for (int g = lane; g < ng; g += 32) {
+            for (int g = lt; g < ng; g += kLoadWarps * 32) {
                 const int t = g / (2 * a.Nt), rem = g - t * 2 * a.Nt, co = rem >> 1, h = rem & 1;
-                cp_async16(wb + t * a.Nt * 32 + core_off(co, h),
+                const int grp = t / a.NX, dxi = t - grp * a.NX;      // B rows n = dxi Nt + co
+                cp_async16(wb + grp * a.NX * a.Nt * 32 + core_off(dxi * a.Nt + co, h),
                            a.Wt + (((int64_t)(co0 + co) * TAPS + t) * a.Cin + c * 16 + h * 8));
             }
             cp_async_wait_all();
@@ -114,13 +123,18 @@ __device__ void role_load(const CUtensorMap *xmap, const HaloArgs &a, uint32_t s
     }
 }
 
-// one thread of warp 5: T x TAPS MMAs per staged chunk
+// lane 0 of MMA warp k: per staged chunk, one MMA per (tap group, tile) for tiles k, k + 4,
+// ...  A tap group is the three dx taps of one (dz, dy): A is the slot run shifted by
+// dz PT + dy WP, B stacks the three taps' weights in N (N = 3 Nt), and the epilogue adds
+// the dx shift.  One thread keeps one MMA in flight at a time (about 90 ns each whatever N
+// is), so four issuers and wide N are what bring the narrow layers of this network
+// towards the tensor pipe's rate.
 template <int TAPS>
-__device__ void role_mma(const HaloArgs &a, uint32_t sbase, uint32_t tmem, const uint64_t *s_adesc, uint32_t full0,
-                         uint32_t empty0, uint32_t accf0, uint32_t acce0, volatile int *abort_flag)
+__device__ void role_mma(const HaloArgs &a, int k0, uint32_t sbase, uint32_t tmem, const uint64_t *s_adesc,
+                         uint32_t full0, uint32_t empty0, uint32_t accf0, uint32_t acce0, volatile int *abort_flag)
 {
-    const int nc = a.Cin >> 4;
-    const uint32_t idesc = instr_desc(128, a.Nt);
+    const int nc = a.Cin >> 4, NN = a.NX * a.Nt, ngroups = TAPS / a.NX;
+    const uint32_t idesc = instr_desc(128, NN);
     int i = 0, k = 0;
     for (int item = blockIdx.x; item < a.nitems; item += gridDim.x, ++k) {
         const int b = k & 1;
@@ -129,7 +143,7 @@ __device__ void role_mma(const HaloArgs &a, uint32_t sbase, uint32_t tmem, const
             return;
         }
         tc_fence_after();
-        const uint32_t dcol = tmem + (uint32_t)(b * a.T * a.Nt);
+        const uint32_t dcol = tmem + (uint32_t)(b * a.T * NN);
         for (int c = 0; c < nc; ++c, ++i) {
             const int s = i & 1;
             if (!mbar_wait(full0 + 8 * s, (i >> 1) & 1) || *abort_flag) {
@@ -138,15 +152,15 @@ __device__ void role_mma(const HaloArgs &a, uint32_t sbase, uint32_t tmem, const
             }
             tc_fence_after();
             const uint32_t wb = sbase + s * a.stage_bytes + 2 * a.half_bytes;
-            for (int t = 0; t < TAPS; ++t) {
+            for (int g = 0; g < ngroups; ++g) {
                 int off = 0;
-                if (TAPS == 27) off = (t / 9 - 1) * a.PT + ((t / 3) % 3 - 1) * a.WP + (t % 3 - 1);
-                // stage and tap shift added to the descriptors' 16-byte address field
+                if (TAPS == 27) off = (g / 3 - 1) * a.PT + (g % 3 - 1) * a.WP;
+                // stage and (dz, dy) shift added to the descriptors' 16-byte address field
                 const int64_t dt = (int64_t)(s * a.stage_bytes / 16 + off);
-                const uint64_t bdesc = smem_desc(wb + t * a.Nt * 32, 128, 256);
-                const uint32_t acc = (c | t) ? 1u : 0u;
-                uint32_t d = dcol;
-                for (int j = 0; j < a.T; ++j, d += (uint32_t)a.Nt)
+                const uint64_t bdesc = smem_desc(wb + g * NN * 32, 128, 256);
+                const uint32_t acc = (c | g) ? 1u : 0u;
+                uint32_t d = dcol + (uint32_t)(k0 * NN);
+                for (int j = k0; j < a.T; j += kMmaWarps, d += (uint32_t)(kMmaWarps * NN))
                     mma_bf16(d, (uint64_t)((int64_t)s_adesc[j] + dt), bdesc, idesc, acc);
             }
             mma_commit(empty0 + 8 * s);
@@ -156,13 +170,20 @@ __device__ void role_mma(const HaloArgs &a, uint32_t sbase, uint32_t tmem, const
 }
 
 template <typename OT>
-__device__ __forceinline__ void store16(OT *dst, const float *v, const float *bias, int relu)
+__device__ __forceinline__ void store16(OT *dst, const uint32_t *v, const float *bias, int relu)
 {
     float r[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        r[i] = v[i] + (bias ? bias[i] : 0.f);
-        if (relu) r[i] = fmaxf(r[i], 0.f);
+    for (int i = 0; i < 16; i += 4) {
+        const float4 b4 = bias ? __ldg((const float4 *)(bias + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r[i] = __uint_as_float(v[i]) + b4.x;
+        r[i + 1] = __uint_as_float(v[i + 1]) + b4.y;
+        r[i + 2] = __uint_as_float(v[i + 2]) + b4.z;
+        r[i + 3] = __uint_as_float(v[i + 3]) + b4.w;
+    }
+    if (relu) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) r[i] = fmaxf(r[i], 0.f);
     }
     if constexpr (sizeof(OT) == 2) {
         uint32_t p[8];
@@ -181,33 +202,94 @@ __device__ __forceinline__ void store16(OT *dst, const float *v, const float *bi
     }
 }
 
-// warps 0-3: TMEM -> bias, activation -> Y
+// all 128 epilogue threads (warps 0-3) agree on a flag (named barrier 1)
+__device__ __forceinline__ bool epi_all(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// warps 0-3: TMEM -> Y.  Row m of a tile holds, for each dx, the (dz, dy)-summed partial
+// product of slot m; output slot m takes D[m - 1][dx = -1] + D[m][0] + D[m + 1][+1]
+// (warp shuffles, and shared memory across the warps' 32-row boundaries).  Rows beyond a
+// tile are pads (zero) for one-row tiles and are never outputs for margin tiles.
 template <typename OT>
-__device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, const int *s_oz, uint32_t accf0,
-                              uint32_t acce0, volatile int *abort_flag)
+__device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, const int *s_oz, float *s_xch,
+                              uint32_t accf0, uint32_t acce0, volatile int *abort_flag)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int k = 0;
+    const int NN = a.NX * a.Nt;
+    int k = 0, step = 0;
     for (int item = blockIdx.x; item < a.nitems; item += gridDim.x, ++k) {
         const int b = k & 1;
-        const bool ok = mbar_wait(accf0 + 8 * b, (k >> 1) & 1);
-        if (!__all_sync(0xffffffffu, ok) || __any_sync(0xffffffffu, *abort_flag)) {
-            if (lane == 0) halo_fail(abort_flag, a.err);
+        const bool ok = mbar_wait(accf0 + 8 * b, (k >> 1) & 1) && !*abort_flag;
+        if (!epi_all(ok)) {
+            if (tid == 0) halo_fail(abort_flag, a.err);
             return;
         }
         tc_fence_after();
         const int slice = item % a.nslice, r = item / a.nslice;
         const int z0 = (r / a.ry) * a.TZ, y0 = (r % a.ry) * a.TY, co0 = slice * a.Nt;
-        const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * a.T * a.Nt);
+        const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * a.T * NN);
         for (int j = 0; j < a.T; ++j) {
             const int q = s_q[j] + tid;
-            const int oz = q / a.PT, rem = q - oz * a.PT, oy = rem / a.WP, x = rem - oy * a.WP;
+            const int oz = q >= 0 ? q / a.PT : -1, rem = q - oz * a.PT, oy = rem / a.WP, x = rem - oy * a.WP;
             const int z = z0 + oz, y = y0 + oy;
-            const bool valid = oz == s_oz[j] && oy < a.TY && x < a.W && z < a.D && y < a.H;
+            const bool valid = tid >= a.mg && tid < 128 - a.mg && oz == s_oz[j] && oy < a.TY && x < a.W &&
+                               z < a.D && y < a.H;
             OT *dst = (OT *)a.Y + ((((int64_t)z * a.H + y) * a.W + x) * a.Cout + co0);
-            for (int n0 = 0; n0 < a.Nt; n0 += 16) {
-                float v[16];
-                tmem_ld16(lanes + (uint32_t)(j * a.Nt + n0), v);
+            for (int n0 = 0; n0 < a.Nt; n0 += 16, ++step) {
+                const uint32_t col = lanes + (uint32_t)(j * NN + n0);
+                uint32_t v[16];
+                if (a.NX == 3) {
+                    uint32_t dm[16], dp[16];
+                    tmem_ld16_issue(col, dm);
+                    tmem_ld16_issue(col + (uint32_t)a.Nt, v);
+                    tmem_ld16_issue(col + (uint32_t)(2 * a.Nt), dp);
+                    tmem_ld_wait();
+                    // rows 32w - 1 and 32w + 32 live in the neighbouring warps: lane 31 of each
+                    // warp publishes its dx = -1 part, lane 0 its dx = +1 part; every lane then
+                    // reads both edges (broadcast) and selects without branching, so the
+                    // shuffle loop has no divergent shared-memory loads to wait on
+                    uint4 *xm = (uint4 *)(s_xch + (step & 1) * 128), *xp = xm + 16;   // [warp][4] x 16 B
+                    if (lane == 31)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            xm[warp * 4 + i] = make_uint4(dm[4 * i], dm[4 * i + 1], dm[4 * i + 2], dm[4 * i + 3]);
+                    if (lane == 0)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            xp[warp * 4 + i] = make_uint4(dp[4 * i], dp[4 * i + 1], dp[4 * i + 2], dp[4 * i + 3]);
+                    epi_sync();
+                    uint32_t el[16], er[16];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint4 l4 = warp > 0 ? xm[(warp - 1) * 4 + i] : make_uint4(0, 0, 0, 0);
+                        const uint4 r4 = warp < 3 ? xp[(warp + 1) * 4 + i] : make_uint4(0, 0, 0, 0);
+                        el[4 * i] = l4.x; el[4 * i + 1] = l4.y; el[4 * i + 2] = l4.z; el[4 * i + 3] = l4.w;
+                        er[4 * i] = r4.x; er[4 * i + 1] = r4.y; er[4 * i + 2] = r4.z; er[4 * i + 3] = r4.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const uint32_t up = __shfl_up_sync(0xffffffffu, dm[i], 1);
+                        const uint32_t dn = __shfl_down_sync(0xffffffffu, dp[i], 1);
+                        const float left = __uint_as_float(lane == 0 ? el[i] : up);
+                        const float right = __uint_as_float(lane == 31 ? er[i] : dn);
+                        v[i] = __float_as_uint(left + __uint_as_float(v[i]) + right);
+                    }
+                } else {
+                    tmem_ld16_issue(col, v);
+                    tmem_ld_wait();
+                }
                 if (valid) store16<OT>(dst + n0, v, a.bias ? a.bias + co0 + n0 : nullptr, a.relu);
             }
         }
@@ -219,36 +301,41 @@ __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, 
 
 template <int TAPS, typename OT>
 __global__ void __launch_bounds__(kHaloThreads, 1)
-    conv3d_halo_kernel(const __grid_constant__ CUtensorMap xmap, const HaloArgs a)
+    conv3d_halo_kernel(const HaloArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[8];   // full[2], empty[2], acc_full[2], acc_empty[2]
     __shared__ uint32_t s_tmem;
     __shared__ int s_q[kMaxTiles], s_oz[kMaxTiles];
     __shared__ uint64_t s_adesc[kMaxTiles];
+    __shared__ __align__(16) float s_xch[256];   // epilogue warp-boundary exchange, two buffers
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = smem_u32(smem);
 
-    // guard slots: the x = -1 neighbours of each staged half's first row, zero for the launch
-    for (int i = tid; i < 2 * 2 * kGuard; i += kHaloThreads) {
-        const int s = i / (2 * kGuard), h = (i / kGuard) & 1, g = i % kGuard;
-        *(uint4 *)(smem + s * a.stage_bytes + h * a.half_bytes + g * 16) = make_uint4(0, 0, 0, 0);
+    // zero slots that no load writes: the guard ahead of each staged half (x = -1 of its
+    // first row) and the 8 pad slots closing every row (x = W of the row, x = -1 of the next)
+    {
+        const int R = (a.TZ + (TAPS == 27 ? 2 : 0)) * (a.TY + (TAPS == 27 ? 2 : 0));
+        const int per_half = kGuard + R * 8;
+        for (int i = tid; i < 4 * per_half; i += kHaloThreads) {
+            const int sh = i / per_half, k = i - sh * per_half;
+            const int slot = k < kGuard ? k : kGuard + ((k - kGuard) >> 3) * a.WP + a.W + ((k - kGuard) & 7);
+            *(uint4 *)(smem + (sh >> 1) * a.stage_bytes + (sh & 1) * a.half_bytes + slot * 16) = make_uint4(0, 0, 0, 0);
+        }
     }
     // first slot of each M tile, relative to output voxel (0, 0, 0) of the region, and the
     // output plane the tile belongs to (rows that run on into the next plane are dropped)
     for (int j = tid; j < a.T; j += kHaloThreads) {
         int q, oz;
-        if (a.W % 128 == 0) {     // tiles never straddle a row
-            const int per_row = a.W / 128, per_plane = a.TY * per_row;
+        if (a.rowtile) {          // W = 128: tile j is row (oz, oy)
+            oz = j / a.TY;
+            q = oz * a.PT + (j - oz * a.TY) * a.WP;
+        } else {                  // runs through each plane's rows, advancing 128 - 2 mg slots
+            const int per_plane = (a.TY * a.WP + a.adv - 1) / a.adv;
             oz = j / per_plane;
-            const int r = j - oz * per_plane, oy = r / per_row;
-            q = oz * a.PT + oy * a.WP + 128 * (r - oy * per_row);
-        } else {                  // consecutive runs of 128 slots through each plane's rows
-            const int per_plane = (a.TY * a.WP + 127) / 128;
-            oz = j / per_plane;
-            q = oz * a.PT + 128 * (j - oz * per_plane);
+            q = oz * a.PT + a.adv * (j - oz * per_plane) - a.mg;
         }
         s_q[j] = q;
         s_oz[j] = oz;
@@ -258,15 +345,15 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     }
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&bars[s]), 32);         // full: 32 loader lanes (+ TMA bytes)
-            mbar_init(smem_u32(&bars[2 + s]), 1);      // empty: one MMA commit
-            mbar_init(smem_u32(&bars[4 + s]), 1);      // accumulator full: one MMA commit
+            mbar_init(smem_u32(&bars[s]), kLoadWarps * 32);   // full: every loader thread
+            mbar_init(smem_u32(&bars[2 + s]), kMmaWarps);     // empty: one commit per issuer
+            mbar_init(smem_u32(&bars[4 + s]), kMmaWarps);     // accumulator full: likewise
             mbar_init(smem_u32(&bars[6 + s]), 4);      // accumulator empty: 4 epilogue warps
         }
         mbar_init_fence();
         s_abort = 0;
     }
-    if (warp == 5) tmem_alloc(smem_u32(&s_tmem), (uint32_t)a.ncols);
+    if (warp == kMmaWarp0) tmem_alloc(smem_u32(&s_tmem), (uint32_t)a.ncols);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -276,15 +363,15 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     const uint32_t accf0 = smem_u32(&bars[4]), acce0 = smem_u32(&bars[6]);
 
     if (warp < 4)
-        role_epilogue<OT>(a, tmem, s_q, s_oz, accf0, acce0, &s_abort);
-    else if (warp == 4)
-        role_load<TAPS>(&xmap, a, sbase, full0, empty0, &s_abort);
+        role_epilogue<OT>(a, tmem, s_q, s_oz, s_xch, accf0, acce0, &s_abort);
+    else if (warp < kMmaWarp0)
+        role_load<TAPS>(a, sbase, full0, empty0, &s_abort);
     else if ((tid & 31) == 0)
-        role_mma<TAPS>(a, sbase, tmem, s_adesc, full0, empty0, accf0, acce0, &s_abort);
+        role_mma<TAPS>(a, warp - kMmaWarp0, sbase, tmem, s_adesc, full0, empty0, accf0, acce0, &s_abort);
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == kMmaWarp0) {
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem, (uint32_t)a.ncols);
@@ -292,21 +379,6 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
 }
 
 // ---- host side ----
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
 
 int sm_count()
 {
@@ -324,30 +396,29 @@ int sm_count()
 // Returns false when the halo kernel cannot take the shape.
 bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms, ConvHaloPlan *pl)
 {
-    if (W % 8 != 0 || W / 8 + 1 > 256 || Cin % 16 || Cout % 16 || Cout > 256 || sms < 1) return false;
+    if (W % 8 != 0 || Cin % 16 || Cout % 16 || Cout > 256 || sms < 1) return false;
     if (taps != 1 && taps != 27) return false;
-    if (!encode_fn()) return false;           // driver without TMA descriptor encoding
-    const int halo = taps == 27 ? 1 : 0, WP = W + 8, nc = Cin / 16;
+    const int halo = taps == 27 ? 1 : 0, NX = taps == 27 ? 3 : 1, WP = W + 8, nc = Cin / 16;
+    const int rowtile = W == 128, mg = (taps == 27 && !rowtile) ? 1 : 0, adv = 128 - 2 * mg;
     double best = 0.0;
     bool found = false;
     for (int Nt = Cout; Nt >= 16; Nt -= 16) {
-        if (Cout % Nt) continue;
+        if (Cout % Nt || NX * Nt > 256) continue;
         for (int TZ = 1; TZ <= (D < 16 ? D : 16); ++TZ)
             for (int TY = 1; TY <= (H < 64 ? H : 64); ++TY) {
-                if (TY + 2 * halo > 256 || TZ + 2 * halo > 256) continue;
                 const int PT = (TY + 2 * halo) * WP;
                 const int64_t NSX = (int64_t)(TZ + 2 * halo) * PT;
                 int T, qmax;
-                if (W % 128 == 0) {
-                    T = TZ * TY * (W / 128);
-                    qmax = (TZ - 1) * PT + (TY - 1) * WP + W - 128;
+                if (rowtile) {
+                    T = TZ * TY;
+                    qmax = (TZ - 1) * PT + (TY - 1) * WP;
                 } else {
-                    const int per = (TY * WP + 127) / 128;
+                    const int per = (TY * WP + adv - 1) / adv;
                     T = TZ * per;
-                    qmax = (TZ - 1) * PT + (per - 1) * 128;
+                    qmax = (TZ - 1) * PT + (per - 1) * adv - mg;
                 }
-                if (T > kMaxTiles || 2 * T * Nt > 512) continue;     // two accumulators
-                const int64_t maxslot = kGuard + halo * (PT + WP) + qmax + 127 + (halo ? PT + WP + 1 : 0);
+                if (T > kMaxTiles || 2 * T * NX * Nt > 512) continue;     // two accumulators
+                const int64_t maxslot = kGuard + halo * (PT + WP) + qmax + 127 + (halo ? PT + WP : 0);
                 int64_t hs = kGuard + NSX > maxslot + 1 ? kGuard + NSX : maxslot + 1;
                 hs = (hs + 7) / 8 * 8;
                 const int64_t half_bytes = hs * 16;
@@ -355,19 +426,26 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
                 int64_t stage = 2 * half_bytes + (int64_t)taps * Nt * 32;
                 stage = (stage + 1023) / 1024 * 1024;
                 if (2 * stage > kSmemLimit) continue;
-                const double mma = (double)nc * taps * T * Nt / 16.0 * 8.5;
-                const double load = (double)nc * stage / 64.0;
-                const double cost = (mma > load ? mma : load) + 300.0;
+                // cycles per work item: each issuer keeps one MMA (~185 cycles) in flight and
+                // the pipe sustains about 11.5 cycles per 128 x 16 x 16; staging moves about
+                // 24 B/cycle/SM; the epilogue about 200 cycles per 16 channels of a tile
+                const double issue = (double)((T + kMmaWarps - 1) / kMmaWarps) * 185.0;
+                const double pipe = (double)T * NX * Nt / 16.0 * 11.5;
+                const double mma = (double)nc * (taps / NX) * (issue > pipe ? issue : pipe);
+                const double load = (double)nc * stage / 24.0;
+                const double epi = (double)T * Nt / 16.0 * 200.0;
+                double cost = mma > load ? mma : load;
+                cost = (cost > epi ? cost : epi) + 500.0;
                 const int64_t nreg = (int64_t)((D + TZ - 1) / TZ) * ((H + TY - 1) / TY) * (Cout / Nt);
                 const double total = (double)((nreg + sms - 1) / sms) * cost;
                 if (!found || total < best) {
                     found = true;
                     best = total;
                     int ncols = 32;
-                    while (ncols < 2 * T * Nt) ncols <<= 1;
+                    while (ncols < 2 * T * NX * Nt) ncols <<= 1;
                     pl->TZ = TZ; pl->TY = TY; pl->Nt = Nt; pl->T = T; pl->WP = WP; pl->PT = PT;
+                    pl->NX = NX; pl->rowtile = rowtile; pl->mg = mg; pl->adv = adv;
                     pl->half_bytes = (int)half_bytes;
-                    pl->x_bytes = (int)(16 * (int64_t)WP * (TY + 2 * halo) * (TZ + 2 * halo));
                     pl->stage_bytes = (int)stage;
                     pl->ncols = ncols;
                     pl->ry = (H + TY - 1) / TY;
@@ -385,27 +463,16 @@ cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias,
     const int sms = sm_count();
     ConvHaloPlan pl;
     if (!plan_conv3d_halo(D, H, W, Cin, Cout, taps, sms, &pl)) return cudaErrorNotSupported;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    const int halo = taps == 27 ? 1 : 0;
-    CUtensorMap map;
-    const cuuint64_t dims[5] = {(cuuint64_t)Cin, 8, (cuuint64_t)(W / 8), (cuuint64_t)H, (cuuint64_t)D};
-    const cuuint64_t strides[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)Cin * 16, (cuuint64_t)W * Cin * 2,
-                                   (cuuint64_t)H * W * Cin * 2};
-    const cuuint32_t box[5] = {8, 8, (cuuint32_t)(W / 8 + 1), (cuuint32_t)(pl.TY + 2 * halo),
-                               (cuuint32_t)(pl.TZ + 2 * halo)};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(X), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
     HaloArgs a;
+    a.X = (const __nv_bfloat16 *)X;
     a.Wt = (const __nv_bfloat16 *)Wt;
     a.bias = bias;
     a.Y = Y;
     a.err = err;
     a.D = D; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.relu = relu;
     a.TZ = pl.TZ; a.TY = pl.TY; a.WP = pl.WP; a.PT = pl.PT; a.T = pl.T; a.Nt = pl.Nt;
-    a.half_bytes = pl.half_bytes; a.x_bytes = pl.x_bytes; a.stage_bytes = pl.stage_bytes;
+    a.NX = pl.NX; a.rowtile = pl.rowtile; a.mg = pl.mg; a.adv = pl.adv;
+    a.half_bytes = pl.half_bytes; a.stage_bytes = pl.stage_bytes;
     a.ncols = pl.ncols;
     a.ry = pl.ry; a.nslice = pl.nslice; a.nitems = pl.nitems;
     // at least 116 KB of shared memory keeps one block per SM, so TMEM is never oversubscribed
@@ -417,7 +484,7 @@ cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias,
     do {                                                                                                       \
         e = cudaFuncSetAttribute(conv3d_halo_kernel<T, OT>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                  (int)smem);                                                                   \
-        if (e == cudaSuccess) conv3d_halo_kernel<T, OT><<<grid, kHaloThreads, smem, s>>>(map, a);              \
+        if (e == cudaSuccess) conv3d_halo_kernel<T, OT><<<grid, kHaloThreads, smem, s>>>(a);              \
     } while (0)
     if (taps == 27) {
         if (out_f32) VAMRT_HALO(27, float); else VAMRT_HALO(27, __nv_bfloat16);

@@ -115,10 +115,10 @@ cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype d
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s);
 
-// conv3d_halo.cu (persistent TMA halo-tile variant; W % 8 == 0).  launch returns
+// conv3d_halo.cu (persistent halo-tile variant; W % 8 == 0).  launch returns
 // cudaErrorNotSupported for shapes it does not take.
 struct ConvHaloPlan {
-    int TZ, TY, Nt, T, WP, PT, half_bytes, x_bytes, stage_bytes, ncols, ry, nslice, nitems;
+    int TZ, TY, Nt, T, WP, PT, NX, rowtile, mg, adv, half_bytes, stage_bytes, ncols, ry, nslice, nitems;
 };
 bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms, ConvHaloPlan *pl);
 cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,

@@ -1,6 +1,6 @@
 // Inline-PTX building blocks shared by the tensor-core kernels: mbarriers with bounded
-// waits, shared-memory matrix descriptors, tcgen05 MMA / commit / TMEM loads, TMA and
-// cp.async copies.  sm_100-family only.
+// waits, shared-memory matrix descriptors, tcgen05 MMA / commit / TMEM loads, cp.async
+// copies.  sm_100-family only.
 #pragma once
 #include <stdint.h>
 
@@ -54,11 +54,6 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 static __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-static __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 // Shared-memory matrix descriptor, no swizzle, K-major: lbo = byte distance between the
@@ -118,6 +113,18 @@ static __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t nco
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// Start loading 16 consecutive FP32 accumulator columns of this thread's TMEM lane
+// (warp-collective); the registers are valid after tmem_ld_wait().
+static __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+static __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane (warp-collective)
 static __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 {
@@ -137,22 +144,16 @@ static __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// the same, writing zeros for the bytes beyond src_bytes (0 or 16)
+static __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
 static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // make this thread's generic-proxy shared-memory writes visible to the async proxy
 // (tensor core operand reads)
 static __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 5-D TMA tile load into shared memory, completing bytes on the mbarrier
-static __device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *map, int c0, int c1, int c2, int c3,
-                                                   int c4, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-        "%6}], [%7];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
-        : "memory");
-}
 
 }  // namespace tc
 }  // namespace vamrt
