@@ -15,25 +15,30 @@
 // the first row).  Pads and guard are zeroed once per launch; halo rows and planes outside
 // the volume are zero-filled by the copies.
 //
-// GEMM mapping.  M = 128 consecutive slots of the region (TMEM lanes), N = Nt output
-// channels (TMEM columns), K = 16 channels of one tap per MMA.  Because the slot index is
-// linear in (z, y, x), the A operand of tap (dz, dy, dx) for a tile is the same slot run
-// shifted by dz PT + dy WP + dx slots: one shared-memory descriptor per (tile, tap), no
-// data movement.  A core matrix is 8 consecutive slots (128 contiguous bytes); SBO = 128 B,
-// LBO = the distance between the two halves.  Tiles that start in padding or run past the
-// region compute rows that the epilogue discards.  B (weights of one chunk, all taps) is
-// staged in the canonical K-major layout.
+// GEMM mapping.  M = 128 consecutive slots of the region (TMEM lanes), K = 16 channels per
+// MMA.  Because the slot index is linear in (z, y, x), the A operand of taps (dz, dy, *)
+// for a tile is the same slot run shifted by dz PT + dy WP slots: one shared-memory
+// descriptor per (tile, dz, dy), no data movement.  The three dx taps share that A and are
+// stacked in N (N = 3 Nt: columns dx, then output channel), so row m of the accumulator
+// holds, per dx, the (dz, dy)-summed product at slot m; the epilogue forms
+// Y[m] = D[m - 1][dx = -1] + D[m][0] + D[m + 1][+1].  A core matrix is 8 consecutive slots
+// (128 contiguous bytes); SBO = 128 B, LBO = the distance between the two halves.  For
+// W = 128 a tile is one row (its neighbours beyond the tile are pads); otherwise tiles run
+// through each plane's rows 126 slots apart with one margin row at either end.  Rows in
+// padding or beyond the region are computed and discarded.  B (weights of one chunk, all
+// taps) is staged in the canonical K-major layout.
 //
-// Staging is by cp.async rather than TMA: with channels-last activations a tensor-map box
-// could only move 16 bytes (one half of one voxel) per element, and measured at about one
-// element per five cycles per SM that starved the tensor core; four loader warps moving
-// coalesced 512-byte runs keep up.
+// Staging is by cp.async from four loader warps: pairs of lanes move the 32 bytes of a
+// voxel's 16-channel chunk, so each warp instruction is one coalesced 512-byte run.  (A
+// tensor-map box over channels-last activations moves 16-byte elements -- one half of one
+// voxel -- and was no faster here.)
 //
 // Roles (384 threads): warps 0-3 drain TMEM (warp w owns lanes 32w..32w+31) and write Y;
-// warps 4-7 copy input tiles and weights into two shared-memory stages; lane 0 of each
-// of warps 8-11 issues the MMAs of every fourth tile.  Two TMEM accumulators let the epilogue of one region overlap
-// the MMAs of the next.  Every wait is bounded: on timeout the block sets the error flag,
-// the other roles run out of their own waits, TMEM is freed and the block returns.
+// warps 4-7 copy input tiles and weights into two shared-memory stages; lane 0 of each of
+// warps 8-11 issues the MMAs of every fourth tile.  Two TMEM accumulators let the epilogue
+// of one region overlap the MMAs of the next.  Every wait is bounded: on timeout the block
+// sets the error flag, the other roles run out of their own waits, TMEM is freed and the
+// block returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
