@@ -450,6 +450,9 @@ def run_gpu(args, rank, world):
                    "setup_s": round(setup_s, 3)},
         "phase_ms_per_step": {"adjoint": adj_ms / args.steps, "forward": fwd_ms / args.steps,
                               "update": upd_ms / args.steps},
+        "samples_per_s": {"adjoint": world * spp * args.steps / (adj_ms / 1e3),
+                          "forward": world * spp * args.steps / (fwd_ms / 1e3),
+                          "note": "per operator, CUDA events around each launch inside the timed steps"},
         "roofline": {"kernel": dom, "bound": "smem", "achieved": achieved, "peak": smem_bps / 1e9, "unit": "GB/s",
                      "frac": achieved * 1e9 / smem_bps, "traffic": traffic,
                      "peak_kind": "measured in this run (vamrt_measure_smem_bandwidth)",
