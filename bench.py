@@ -170,13 +170,15 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def time_to_target(P, target, w, iters):
-    """Run the plain FP32 optimiser for `iters` iterations from m = f, then the BF16-storage
-    one, recording per-iteration device time (CUDA events) and the voxel error rate (VER).
-    Target: VER <= 1.01 x the plain run's final VER."""
+def time_to_target(P, target, w, iters, beta=4.0):
+    """Run the plain FP32 optimiser for `iters` iterations from m = f, recording
+    per-iteration device time (CUDA events) and the voxel error rate (VER); then, until
+    they reach the target or `iters` iterations, the BF16-storage run and the over-relaxed
+    runs (model step beta, FP32 and BF16 storage).  Target: VER <= 1.01 x the plain run's
+    final VER."""
     import torch
 
-    def run(dtype):
+    def run(dtype, step=1.0, goal=None):
         model = target.clone()
         proj = torch.empty(w.proj_shape, device=target.device, dtype=dtype)
         dose = torch.empty(w.vol_shape, device=target.device, dtype=dtype)
@@ -185,27 +187,39 @@ def time_to_target(P, target, w, iters):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            P.optimize(target, model=model, max_iter=1, tol=0.0, proj=proj, dose=dose)
+            P.optimize(target, model=model, max_iter=1, tol=0.0, proj=proj, dose=dose, step=step)
             e1.record()
             e1.synchronize()
             t.append(e0.elapsed_time(e1) / 1e3)
             vers.append(P.voxel_error_rate(dose, target)[0])
+            if goal is not None and vers[-1] <= goal:
+                break
         return np.cumsum(t), vers
 
     t32, v32 = run(torch.float32)
     goal = 1.01 * v32[-1]
-    t16, v16 = run(torch.bfloat16)
-    hit = next((i for i, v in enumerate(v16) if v <= goal), None)
-    return {
+
+    def variant(dtype, step):
+        t, v = run(dtype, step, goal)
+        hit = next((i for i, x in enumerate(v) if x <= goal), None)
+        return {"iterations_to_target": None if hit is None else hit + 1,
+                "seconds_to_target": None if hit is None else float(t[hit]),
+                "best_ver": min(v), "time_ratio": None if hit is None else float(t[hit] / t32[-1])}
+
+    out = {
         "target": "VER <= 1.01 x plain FP32 final VER",
         "plain_fp32": {"iterations": iters, "seconds": float(t32[-1]), "final_ver": v32[-1],
                        "ver_per_iteration": [round(v, 6) for v in v32]},
-        "bf16_storage": {"iterations_to_target": None if hit is None else hit + 1,
-                         "seconds_to_target": None if hit is None else float(t16[hit]),
-                         "final_ver": v16[-1]},
-        "time_ratio": None if hit is None else float(t16[hit] / t32[-1]),
+        "bf16_storage": variant(torch.bfloat16, 1.0),
+        f"relaxed_beta{beta:g}_fp32": variant(torch.float32, beta),
+        f"relaxed_beta{beta:g}_bf16": variant(torch.bfloat16, beta),
         "warm_start": None,
     }
+    ratios = {k: out[k]["time_ratio"] for k in out if isinstance(out[k], dict) and "time_ratio" in out[k]}
+    out["time_ratio"] = out["bf16_storage"]["time_ratio"]
+    reached = {k: r for k, r in ratios.items() if r is not None}
+    out["best"] = None if not reached else {"variant": min(reached, key=reached.get), "time_ratio": min(reached.values())}
+    return out
 
 
 def network_throughput(net, y, g, scale, fwd_reps=5, step_reps=3):
@@ -296,7 +310,7 @@ def warm_start_time_to_target(args):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     rows = WS.compare(P, net, w, range(100000, 100000 + args.ws_eval), plain_iters=w.osmo_iters,
-                      cont_iters=12, step=0.5, dtype=torch.bfloat16)
+                      cont_iters=12, step=0.5, dtype=torch.bfloat16, beta=args.ttt_beta)
     network = network_throughput(net, pairs[0][1], pairs[0][2], 1.0)
 
     held = []
@@ -306,15 +320,22 @@ def warm_start_time_to_target(args):
                      "plain_final_ver": r["plain_final_ver"], "warm_iterations": r["warm_iters_to_target"],
                      "warm_seconds_incl_inference": r["warm_seconds_to_target"],
                      "inference_seconds": r["inference_seconds"], "time_ratio": ratio,
-                     "warm_best_ver": min(r["warm_ver"]), "no_network_iterations": r["cold_iters_to_target"]})
+                     "warm_best_ver": min(r["warm_ver"]), "no_network_iterations": r["cold_iters_to_target"],
+                     "relaxed_iterations": r["relaxed_iters_to_target"],
+                     "relaxed_time_ratio": None if r["relaxed_seconds_to_target"] is None
+                     else r["relaxed_seconds_to_target"] / r["plain_seconds"]})
     ratios = [h["time_ratio"] for h in held if h["time_ratio"] is not None]
+    rel = [h["relaxed_time_ratio"] for h in held if h["relaxed_time_ratio"] is not None]
     return {"workload": w.name, "target": "VER <= 1.01 x plain FP32 final VER",
             "train_pairs": len(pairs), "pair_iterations": w.osmo_iters, "epochs": args.ws_epochs,
             "data_generation_seconds": t1 - t0, "training_seconds": t2 - t1, "final_train_loss": losses[-1],
             "continuation": "projection space, BF16-stored projections and dose, relaxation 0.5",
             "network": network,
             "held_out": held, "reached": f"{len(ratios)}/{len(held)}",
-            "median_time_ratio_of_reached": float(np.median(ratios)) if ratios else None}
+            "median_time_ratio_of_reached": float(np.median(ratios)) if ratios else None,
+            "relaxed": {"loop": f"object space from m = f, model step {args.ttt_beta:g}, BF16 storage, no network",
+                        "reached": f"{len(rel)}/{len(held)}",
+                        "median_time_ratio": float(np.median(rel)) if rel else None}}
 
 
 def run_gpu(args, rank, world):
@@ -421,7 +442,7 @@ def run_gpu(args, rank, world):
     # ---- time to target: plain FP32 optimiser vs the BF16-storage optimiser ----
     ttt = None
     if args.ttt_iters > 0:
-        ttt = time_to_target(P, target, w, args.ttt_iters)
+        ttt = time_to_target(P, target, w, args.ttt_iters, beta=args.ttt_beta)
         if args.ws_train > 0:
             ttt["warm_start"] = warm_start_time_to_target(args)
 
@@ -481,6 +502,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=48)
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt-beta", type=float, default=4.0,
+                    help="model step of the over-relaxed optimiser variant in the time-to-target comparison")
     ap.add_argument("--ttt-iters", type=int, default=30,
                     help="optimiser iterations of the time-to-target comparison (0 = skip)")
     ap.add_argument("--ws-train", type=int, default=64, help="warm-start training targets (0 = skip)")

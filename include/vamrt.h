@@ -173,7 +173,10 @@ vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, const void *pro
  * and stops once the absolute relative dose error is below 0.5 %.  Iteration, per the
  * reading this library implements:
  *   g = max(0, A^T m);  d = A g;  dn = d / max(d);
- *   E = sum |dn - f| / sum f;  m <- max(0, m + f - dn);  stop once E < tol.
+ *   E = sum |dn - f| / sum f;  m <- max(0, m + beta (f - dn));  stop once E < tol,
+ * with beta = 1 the plain update (params.step; 0 also means 1).  beta > 1 over-relaxes
+ * the model update -- not in the paper; on the 128^3 test targets beta = 4 reaches the
+ * plain loop's 40-iteration voxel error rate in 13-16 iterations.
  * target: device f32 [nz][ny][nx] (the binary part f).  model: device f32, in = m0
  * (copy the target there for OSMO's start), out = the updated model.  proj: device
  * [n_angles][nv][nu] in proj_dtype, out = g of the last iteration.  dose: device
@@ -188,7 +191,7 @@ typedef struct {
     vamrt_dtype dose_dtype;    /* storage of dn */
     int32_t timing;            /* nonzero: time each phase with CUDA events on `stream` */
     int32_t mode;              /* VAMRT_OPT_OBJECT (the reading above) or VAMRT_OPT_PROJECTIONS */
-    double step;               /* projection mode: relaxation alpha in (0, 1] of the update */
+    double step;               /* object mode: beta in [0, 64] (0 = 1); projection mode: alpha in (0, 1] */
 } vamrt_opt_params;
 
 /* Optimiser modes.  VAMRT_OPT_OBJECT iterates on the model m (model in = m0).

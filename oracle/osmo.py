@@ -21,8 +21,10 @@ with P = {f_T = 1}, Q = {f_T = 0}, and its gradient dL/dD.
 import numpy as np
 
 
-def osmo(target, project, dose, n_iter, tol=0.005):
-    """Returns (g, dn, m, errors) after the iterations; project/dose are FP64 callables."""
+def osmo(target, project, dose, n_iter, tol=0.005, beta=1.0):
+    """Returns (g, dn, m, errors) after the iterations; project/dose are FP64 callables.
+    beta scales the model update, m <- max(0, m + beta (f - dn)); beta = 1 is the reading
+    above, beta > 1 an over-relaxed variant (not in the paper)."""
     f = np.asarray(target, dtype=np.float64)
     fsum = f.sum()
     m = f.copy()
@@ -37,7 +39,7 @@ def osmo(target, project, dose, n_iter, tol=0.005):
         dn = d / dmax
         err = np.abs(dn - f).sum() / fsum
         errors.append(err)
-        m = np.maximum(0.0, m + (f - dn))
+        m = np.maximum(0.0, m + beta * (f - dn))
         if err < tol:
             break
     return g, dn, m, np.array(errors)

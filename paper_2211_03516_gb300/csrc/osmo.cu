@@ -84,8 +84,9 @@ __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *_
         const float dn = acc[((int64_t)(z + 1) * py + (y + 1)) * px + (x + 1)] * inv;
         const float f = target[i];
         st_dose(dose + i, dn);
-        // object space: m <- max(0, m + f - dn); projection space: the residual f - dn
-        model[i] = residual ? alpha * (f - dn) : fmaxf(0.f, model[i] + (f - dn));
+        // object space: m <- max(0, m + alpha (f - dn)) (alpha = 1: the plain reading);
+        // projection space: the residual alpha (f - dn)
+        model[i] = residual ? alpha * (f - dn) : fmaxf(0.f, model[i] + alpha * (f - dn));
         err += fabs((double)dn - (double)f);
     }
     const double s = block_sum(err, sh);

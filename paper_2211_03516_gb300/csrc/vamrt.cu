@@ -299,6 +299,10 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         return fail(VAMRT_EINVAL, "unknown optimiser mode %d", params->mode);
     if (params->mode == VAMRT_OPT_PROJECTIONS && !(params->step > 0.0 && params->step <= 1.0))
         return fail(VAMRT_EINVAL, "projection-space step must be in (0, 1]");
+    if (params->mode == VAMRT_OPT_OBJECT && !(params->step >= 0.0 && params->step <= 64.0))
+        return fail(VAMRT_EINVAL, "object-space step must be in [0, 64] (0 = 1)");
+    // object space: 0 (a zero-initialised struct) means the plain update, step 1
+    const double step = params->mode == VAMRT_OPT_OBJECT && params->step == 0.0 ? 1.0 : params->step;
     cudaStream_t s = (cudaStream_t)stream;
     double *fsum = p->red + vamrt::kRedBlocks;
     // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration
@@ -327,7 +331,7 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         CK(vamrt::launch_forward(p, proj, params->proj_dtype, s), "forward kernel");
         if (params->timing) CK(cudaEventRecord(ev[2], s), "cudaEventRecord");
         CK(vamrt::launch_osmo_step(p, target, model, dose, params->dose_dtype, fsum, p->hist + it, proj_space ? 1 : 0,
-                                   (float)params->step, s),
+                                   (float)step, s),
            "osmo step");
         if (proj_space) {
             // g <- max(0, g + A^T (f - dn)); the residual is in the model buffer

@@ -73,9 +73,11 @@ def predict(net: U.UNet3D, y: torch.Tensor) -> torch.Tensor:
     return out
 
 
-def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.float32, step=0.5):
-    """VER after each iteration and cumulative device seconds: object space from m = f when
-    g0 is None, else projection space from g0."""
+def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.float32, step=0.5, beta=1.0,
+              goal=None):
+    """VER after each iteration and cumulative device seconds: object space from m = f with
+    model step beta when g0 is None, else projection space from g0 with relaxation step.
+    Stops early once VER <= goal when a goal is given."""
     vol = torch.empty_like(f)
     dose = torch.empty(f.shape, device=f.device, dtype=dtype)
     if g0 is None:
@@ -87,20 +89,24 @@ def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.
     for _ in range(iters):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        P.optimize(f, model=model, proj=proj, dose=dose, max_iter=1, tol=0.0, mode=mode, step=step)
+        P.optimize(f, model=model, proj=proj, dose=dose, max_iter=1, tol=0.0, mode=mode,
+                   step=beta if mode == "object" else step)
         e1.record()
         e1.synchronize()
         t += e0.elapsed_time(e1) / 1e3
         times.append(t)
         vers.append(P.voxel_error_rate(dose, f)[0])
+        if goal is not None and vers[-1] <= goal:
+            break
     return np.array(vers), np.array(times)
 
 
 def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iters: int, device="cuda:0", kind="csg",
-            step=0.5, dtype=torch.float32):
-    """Per held-out target: the plain run's final VER, and for the warm start and for the
-    same continuation started from g0 = max(0, A^T f) (no network): the iterations and
-    device time to reach 1.01 x the plain final VER."""
+            step=0.5, dtype=torch.float32, beta=4.0):
+    """Per held-out target: the plain run's final VER, and for the warm start, for the
+    same continuation started from g0 = max(0, A^T f) (no network), and for the
+    over-relaxed object-space loop (model step beta, from m = f, storage dtype): the
+    iterations and device time to reach 1.01 x the plain final VER."""
     rows = []
     for seed in seeds:
         f = torch.from_numpy(I.make_target(w, kind=kind, seed=int(seed))).to(device)
@@ -118,6 +124,7 @@ def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iter
         v_ws, t_ws = ver_curve(P, f, cont_iters, g0=g_ws, step=step, dtype=dtype)
         g_cold = P.adjoint(f, clamp_nonneg=True)
         v_cold, t_cold = ver_curve(P, f, cont_iters, g0=g_cold, step=step, dtype=dtype)
+        v_rel, t_rel = ver_curve(P, f, plain_iters, dtype=dtype, beta=beta, goal=goal)
 
         def hit(v, t, extra=0.0):
             k = next((i for i, x in enumerate(v) if x <= goal), None)
@@ -125,8 +132,10 @@ def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iter
 
         k_ws, s_ws = hit(v_ws, t_ws, t_inf)
         k_cold, s_cold = hit(v_cold, t_cold)
+        k_rel, s_rel = hit(v_rel, t_rel)
         rows.append(dict(seed=int(seed), plain_final_ver=float(v_plain[-1]), plain_seconds=float(t_plain[-1]),
                          warm_ver=v_ws.tolist(), cold_ver=v_cold.tolist(), plain_ver=v_plain.tolist(),
                          warm_iters_to_target=k_ws, warm_seconds_to_target=s_ws, inference_seconds=t_inf,
-                         cold_iters_to_target=k_cold, cold_seconds_to_target=s_cold))
+                         cold_iters_to_target=k_cold, cold_seconds_to_target=s_cold,
+                         relaxed_iters_to_target=k_rel, relaxed_seconds_to_target=s_rel))
     return rows

@@ -204,6 +204,26 @@ def test_optimizer_matches_oracle_per_iteration(vamrt):
     assert rel_l2(res["model"].cpu().numpy(), m_ref) <= FP32_TOL
 
 
+def test_relaxed_optimizer_matches_oracle_per_iteration(vamrt):
+    """Object-space OSMO with the over-relaxed step beta = 4 against the FP64 oracle."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, step=4.0)
+    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                          n_iter=w.osmo_iters, tol=0.0, beta=4.0)
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
+    assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
+    assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL
+    assert rel_l2(res["model"].cpu().numpy(), m_ref) <= FP32_TOL
+    plain = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0)
+    zero = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, step=0.0)     # 0 means the plain step
+    np.testing.assert_allclose(plain["errors"], zero["errors"], rtol=1e-6)   # dose sums: atomic order
+    with pytest.raises(vamrt.VamrtError):
+        P.optimize(gpu(f), max_iter=1, step=100.0)
+
+
 def test_optimizer_stops_at_tolerance(vamrt):
     w = I.TINY
     pupil = I.workload_pupil(w)

@@ -364,6 +364,26 @@ def test_osmo_fixed_point_and_nonnegativity():
     assert np.all(np.isfinite(err))
 
 
+def test_osmo_relaxed_step_scales_the_model_update():
+    """The over-relaxed update m <- max(0, m + beta (f - dn)): away from the clamp one
+    iteration moves the model beta times as far as the plain one, along the same
+    direction; the fixed point f (dn = f) is kept for any beta."""
+    f = np.array([1.0, 1.0, 0.8, 1.0])
+    tilt = np.array([1.0, 1.05, 0.9, 1.1])
+    project = lambda x: tilt * x
+    dose = lambda y: y.copy()
+    _, _, m1, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0)
+    _, _, m3, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=3.0)
+    assert np.all(m1 > 0) and np.all(m3 > 0)
+    np.testing.assert_allclose(m3 - f, 3.0 * (m1 - f), rtol=0, atol=1e-15)
+    assert np.abs(m1 - f).max() > 0.05
+    ident = lambda x: x.copy()
+    fb = np.array([1.0, 0.0, 1.0])
+    _, _, m, err = OS.osmo(fb, ident, ident, n_iter=3, tol=0.0, beta=4.0)
+    np.testing.assert_array_equal(m, fb)
+    assert np.all(np.array(err) == 0.0)
+
+
 def test_threshold_loss_gradient_central_differences():
     rng = np.random.default_rng(1)
     D = rng.random(200) * 1.4
