@@ -384,6 +384,62 @@ def test_osmo_relaxed_step_scales_the_model_update():
     assert np.all(np.array(err) == 0.0)
 
 
+def test_osmo_momentum_adds_the_previous_step():
+    """Heavy-ball momentum: from rest the first iteration is the plain one; from a model
+    m1 with predecessor m0, away from the clamp, the iterate differs from the
+    momentum-free one from m1 by exactly mu (m1 - m0)."""
+    f = np.array([1.0, 1.0, 0.8, 1.0])
+    tilt = np.array([1.0, 1.05, 0.9, 1.1])
+    project = lambda x: tilt * x
+    dose = lambda y: y.copy()
+    _, _, m1, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0)
+    _, _, m1_mu, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, mu=0.5)
+    np.testing.assert_array_equal(m1_mu, m1)
+    _, _, m2, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, m0=m1)
+    _, _, m2_mu, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, mu=0.5, m0=m1, m_prev=f)
+    assert np.all(m2 > 0) and np.all(m2_mu > 0)
+    np.testing.assert_allclose(m2_mu - m2, 0.5 * (m1 - f), rtol=0, atol=1e-15)
+    assert np.abs(m1 - f).max() > 0.05
+    _, _, m2_two, _ = OS.osmo(f, project, dose, n_iter=2, tol=0.0, beta=2.0, mu=0.5)
+    np.testing.assert_allclose(m2_two, m2_mu, rtol=0, atol=1e-15)
+
+
+# --- Radon-method baseline (Sec. 2.3) ---------------------------------------------------
+def test_ramlak_frequency_response_is_the_ramp():
+    """The band-limited ramp kernel's discrete-time Fourier transform is |omega| / (2 pi) on
+    [-pi, pi] (Kak & Slaney); truncated to 4096 taps it stays within 3e-5 of it."""
+    from oracle import radon as RD
+    h = RD.ramlak_taps(4096)
+    k = np.arange(1, 4096)
+    for om in (0.0, 0.3, np.pi / 4, np.pi / 2, 2.0, np.pi):
+        H = h[0] + 2.0 * np.sum(h[1:] * np.cos(om * k))
+        assert abs(H - om / (2 * np.pi)) < 3e-5, om
+
+
+def test_ramlak_filtered_backprojection_reconstructs_a_disk():
+    """Textbook filtered backprojection: the analytic parallel-beam sinogram of a unit disk
+    (chords 2 sqrt(R^2 - s^2)), filtered by the oracle and backprojected over 180 angles,
+    gives 1 inside the disk and ~0 outside."""
+    from oracle import radon as RD
+    n, tau, R = 129, 0.5, 20.0
+    s = (np.arange(n) - (n - 1) / 2) * tau
+    sino = np.where(np.abs(s) < R, 2 * np.sqrt(np.maximum(R * R - s * s, 0.0)), 0.0)
+    na = 180
+    th = np.pi * np.arange(na) / na
+    q = RD.ramlak_filter(np.tile(sino, (na, 1)), tau)
+    X, Y = np.meshgrid(s, s)
+    rec = np.zeros_like(X)
+    for a in range(na):
+        rec += np.interp(X * np.cos(th[a]) + Y * np.sin(th[a]), s, q[a], left=0.0, right=0.0)
+    rec *= np.pi / na
+    r = np.hypot(X, Y)
+    assert np.abs(rec[r < 0.8 * R] - 1.0).max() < 0.01
+    ring = (r > 1.2 * R) & (r < 1.5 * R)
+    assert np.abs(rec[ring]).mean() < 0.02
+    clipped = RD.ramlak_filter(np.tile(sino, (2, 1)), tau, clamp=True)
+    assert clipped.min() == 0.0 and np.array_equal(clipped[0], np.maximum(q[0], 0.0))
+
+
 def test_threshold_loss_gradient_central_differences():
     rng = np.random.default_rng(1)
     D = rng.random(200) * 1.4
