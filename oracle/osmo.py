@@ -21,13 +21,15 @@ with P = {f_T = 1}, Q = {f_T = 0}, and its gradient dL/dD.
 import numpy as np
 
 
-def osmo(target, project, dose, n_iter, tol=0.005, beta=1.0):
+def osmo(target, project, dose, n_iter, tol=0.005, beta=1.0, mu=0.0, m0=None, m_prev=None):
     """Returns (g, dn, m, errors) after the iterations; project/dose are FP64 callables.
-    beta scales the model update, m <- max(0, m + beta (f - dn)); beta = 1 is the reading
-    above, beta > 1 an over-relaxed variant (not in the paper)."""
+    beta scales the model update and mu adds heavy-ball momentum,
+    m <- max(0, m + beta (f - dn) + mu (m - m_prev)); beta = 1, mu = 0 is the reading
+    above, the others variants not in the paper.  m0 defaults to f, m_prev to m0 (at rest)."""
     f = np.asarray(target, dtype=np.float64)
     fsum = f.sum()
-    m = f.copy()
+    m = f.copy() if m0 is None else np.array(m0, dtype=np.float64)
+    prev = m.copy() if m_prev is None else np.array(m_prev, dtype=np.float64)
     errors = []
     g = dn = None
     for _ in range(n_iter):
@@ -39,7 +41,7 @@ def osmo(target, project, dose, n_iter, tol=0.005, beta=1.0):
         dn = d / dmax
         err = np.abs(dn - f).sum() / fsum
         errors.append(err)
-        m = np.maximum(0.0, m + beta * (f - dn))
+        m, prev = np.maximum(0.0, m + beta * (f - dn) + mu * (m - prev)), m
         if err < tol:
             break
     return g, dn, m, np.array(errors)

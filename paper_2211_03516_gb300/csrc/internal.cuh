@@ -111,6 +111,10 @@ cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, va
 cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype dt, const float *target,
                        long long *out3, cudaStream_t s);
 
+// ramlak.cu (Radon-method baseline): rows x nu floats, in place allowed
+cudaError_t launch_ramlak(const float *in, float *out, int64_t rows, int nu, double pixel_mm, int clamp,
+                          cudaStream_t s);
+
 // conv3d_tc.cu (tensor-core convolution of the warm-start network)
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s);
@@ -152,6 +156,6 @@ cudaError_t launch_export_u8(const vamrt_projector *p, const void *proj, vamrt_d
 cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cudaStream_t s);
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
                              vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, float alpha,
-                             cudaStream_t s);
+                             float mu, float *prev, cudaStream_t s);
 
 }  // namespace vamrt

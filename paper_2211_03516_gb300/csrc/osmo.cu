@@ -71,7 +71,8 @@ template <typename DT>
 __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *__restrict__ dmax,
                                    const float *__restrict__ target, float *__restrict__ model,
                                    DT *__restrict__ dose, int nx, int ny, int nz, int px, int py,
-                                   double *__restrict__ partials, int residual, float alpha)
+                                   double *__restrict__ partials, int residual, float alpha, float mu,
+                                   float *__restrict__ prev)
 {
     __shared__ double sh[kRedThreads / 32];
     const int64_t total = (int64_t)nx * ny * nz;
@@ -84,9 +85,17 @@ __global__ void osmo_update_kernel(const float *__restrict__ acc, const float *_
         const float dn = acc[((int64_t)(z + 1) * py + (y + 1)) * px + (x + 1)] * inv;
         const float f = target[i];
         st_dose(dose + i, dn);
-        // object space: m <- max(0, m + alpha (f - dn)) (alpha = 1: the plain reading);
-        // projection space: the residual alpha (f - dn)
-        model[i] = residual ? alpha * (f - dn) : fmaxf(0.f, model[i] + alpha * (f - dn));
+        // object space: m <- max(0, m + alpha (f - dn) + mu (m - m_prev)) (alpha = 1, mu = 0:
+        // the plain reading), m_prev <- m; projection space: the residual alpha (f - dn)
+        if (residual) {
+            model[i] = alpha * (f - dn);
+        } else if (prev) {
+            const float m = model[i];
+            model[i] = fmaxf(0.f, m + alpha * (f - dn) + mu * (m - prev[i]));
+            prev[i] = m;
+        } else {
+            model[i] = fmaxf(0.f, model[i] + alpha * (f - dn));
+        }
         err += fabs((double)dn - (double)f);
     }
     const double s = block_sum(err, sh);
@@ -115,7 +124,7 @@ cudaError_t launch_sum(const vamrt_projector *p, const float *x, double *out, cu
 
 cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, float *model, void *dose,
                              vamrt_dtype dose_dt, const double *fsum, double *err_out, int residual, float alpha,
-                             cudaStream_t s)
+                             float mu, float *prev, cudaStream_t s)
 {
     const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
     const int64_t n = (int64_t)nx * ny * nz;
@@ -128,10 +137,11 @@ cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, floa
     const int G = red_grid(n);
     if (dose_dt == VAMRT_F32)
         osmo_update_kernel<float><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,
-                                                         nx, ny, nz, px, py, p->red, residual, alpha);
+                                                         nx, ny, nz, px, py, p->red, residual, alpha, mu, prev);
     else
         osmo_update_kernel<__nv_bfloat16><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model,
-                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, px, py, p->red, residual, alpha);
+                                                                 (__nv_bfloat16 *)dose, nx, ny, nz, px, py, p->red, residual, alpha,
+                                                                 mu, prev);
     finish_sum_kernel<<<1, kRedThreads, 0, s>>>(p->red, G, fsum, err_out);
     count_launches(3);
     return cudaGetLastError();

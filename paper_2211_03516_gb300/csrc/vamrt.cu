@@ -303,6 +303,10 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         return fail(VAMRT_EINVAL, "object-space step must be in [0, 64] (0 = 1)");
     // object space: 0 (a zero-initialised struct) means the plain update, step 1
     const double step = params->mode == VAMRT_OPT_OBJECT && params->step == 0.0 ? 1.0 : params->step;
+    if (!(params->momentum >= 0.0 && params->momentum < 1.0))
+        return fail(VAMRT_EINVAL, "momentum must be in [0, 1)");
+    if (params->momentum != 0.0 && (params->mode != VAMRT_OPT_OBJECT || !params->prev_model))
+        return fail(VAMRT_EINVAL, "momentum needs object mode and a prev_model buffer");
     cudaStream_t s = (cudaStream_t)stream;
     double *fsum = p->red + vamrt::kRedBlocks;
     // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration
@@ -331,7 +335,8 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         CK(vamrt::launch_forward(p, proj, params->proj_dtype, s), "forward kernel");
         if (params->timing) CK(cudaEventRecord(ev[2], s), "cudaEventRecord");
         CK(vamrt::launch_osmo_step(p, target, model, dose, params->dose_dtype, fsum, p->hist + it, proj_space ? 1 : 0,
-                                   (float)step, s),
+                                   (float)step, (float)params->momentum,
+                                   params->momentum != 0.0 ? params->prev_model : nullptr, s),
            "osmo step");
         if (proj_space) {
             // g <- max(0, g + A^T (f - dn)); the residual is in the model buffer
@@ -419,6 +424,21 @@ vamrt_status vamrt_conv3d_bf16(const void *x, const void *w, const float *bias, 
     CK(vamrt::launch_conv3d_tc(x, w, bias, y, out_f32, d, h, wd, cin, cout, taps, relu, (int *)err_flag,
                                (cudaStream_t)stream),
        "conv3d kernel");
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_ramlak_filter(const float *proj, float *out, int64_t rows, int32_t nu, double pixel_mm,
+                                 uint32_t flags, void *stream)
+{
+    if (rows < 0) return fail(VAMRT_EINVAL, "rows must be >= 0");
+    if (rows > 0 && (!proj || !out)) return fail(VAMRT_EINVAL, "NULL argument");
+    if (nu < 1 || nu > 4096) return fail(VAMRT_EINVAL, "nu must be in 1..4096");
+    if (!(pixel_mm > 0.0) || !isfinite(pixel_mm)) return fail(VAMRT_EINVAL, "pixel_mm must be positive and finite");
+    if (flags & ~(uint32_t)VAMRT_CLAMP_NONNEG) return fail(VAMRT_EINVAL, "only VAMRT_CLAMP_NONNEG is accepted");
+    if (((uintptr_t)proj | (uintptr_t)out) & 3) return fail(VAMRT_EINVAL, "proj and out must be 4-byte aligned");
+    CK(vamrt::launch_ramlak(proj, out, rows, nu, pixel_mm, (flags & VAMRT_CLAMP_NONNEG) ? 1 : 0,
+                            (cudaStream_t)stream),
+       "Ram-Lak filter kernel");
     return VAMRT_OK;
 }
 

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
 class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("check_every", ctypes.c_int32),
                 ("proj_dtype", ctypes.c_int), ("dose_dtype", ctypes.c_int), ("timing", ctypes.c_int32),
-                ("mode", ctypes.c_int32), ("step", ctypes.c_double)]
+                ("mode", ctypes.c_int32), ("step", ctypes.c_double), ("momentum", ctypes.c_double),
+                ("prev_model", ctypes.c_void_p)]
 
 
 class OptReport(ctypes.Structure):
@@ -98,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.vamrt_export_u8.restype = i32
         L.vamrt_measure_smem_bandwidth.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.vamrt_measure_smem_bandwidth.restype = i32
+        L.vamrt_ramlak_filter.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, u32, vp]
+        L.vamrt_ramlak_filter.restype = i32
         L.vamrt_launch_count.argtypes = []
         L.vamrt_launch_count.restype = ctypes.c_uint64
         for name in ("vamrt_make_projector", "vamrt_get_info", "vamrt_sample_count", "vamrt_adjoint",
@@ -302,9 +305,13 @@ class Projector:
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,
-                 timing=False, mode="object", step=1.0, stream=None) -> dict:
+                 timing=False, mode="object", step=1.0, momentum=0.0, prev_model=None, stream=None) -> dict:
         """Projection optimisation (vamrt_optimize).  Returns g, dn, model, errors, converged.
-        mode "object": OSMO on the model (model in = m0, default the target);
+        mode "object": OSMO on the model (model in = m0, default the target), model step
+        `step` (1 = the plain update) and heavy-ball `momentum` (0 = none), whose previous
+        model lives in prev_model (in: the model before m0 -- a copy of m0 to start at rest,
+        made here when prev_model is None; out: updated; pass the same buffer back to keep
+        momentum across calls);
         mode "projections": iterate on proj (in = g0, required), model = workspace."""
         if mode not in ("object", "projections"):
             raise ValueError("mode must be 'object' or 'projections'")
@@ -312,6 +319,9 @@ class Projector:
             raise ValueError("projection mode needs the starting projections in proj")
         if model is None:
             model = target.clone() if mode == "object" else torch.empty_like(target)
+        if momentum and prev_model is None:
+            prev_model = model.clone()
+        pm = _dev_ptr(prev_model, self.vol_shape, "prev_model", (torch.float32,)) if momentum else None
         if proj is None:
             proj = torch.empty(self.proj_shape, device=target.device, dtype=proj_dtype)
         if dose is None:
@@ -322,14 +332,34 @@ class Projector:
         dp = _dev_ptr(dose, self.vol_shape, "dose")
         params = OptParams(max_iter=max_iter, tol=tol, check_every=check_every, proj_dtype=_DTYPES[proj.dtype],
                            dose_dtype=_DTYPES[dose.dtype], timing=1 if timing else 0,
-                           mode=0 if mode == "object" else 1, step=float(step))
+                           mode=0 if mode == "object" else 1, step=float(step), momentum=float(momentum),
+                           prev_model=pm)
         hist = np.zeros(max_iter, dtype=np.float64)
         rep = OptReport(iterations=0, final_error=math.nan, error_history=hist.ctypes.data_as(_dp))
         st = _check(lib().vamrt_optimize(self.handle, tp, mp, pp, dp, ctypes.byref(params), ctypes.byref(rep),
                                          _stream(stream)), "vamrt_optimize", ok=(VAMRT_OK, VAMRT_NOT_CONVERGED))
-        return dict(proj=proj, dose=dose, model=model, errors=hist[:rep.iterations].copy(),
+        return dict(proj=proj, dose=dose, model=model, prev_model=prev_model, errors=hist[:rep.iterations].copy(),
                     iterations=rep.iterations, final_error=rep.final_error, converged=(st == VAMRT_OK),
                     adjoint_ms=rep.adjoint_ms, forward_ms=rep.forward_ms, update_ms=rep.update_ms)
+
+
+def ramlak_filter(proj: torch.Tensor, pixel_mm: float, clamp: bool = False, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """Ram-Lak filter along the last axis of an f32 CUDA tensor (vamrt_ramlak_filter, the
+    Radon-method baseline of Sec. 2.3); clamp clips negatives to zero; out may be proj."""
+    if not isinstance(proj, torch.Tensor) or not proj.is_cuda or proj.dtype != torch.float32:
+        raise TypeError("proj must be a float32 CUDA tensor")
+    if not proj.is_contiguous():
+        raise ValueError("proj must be contiguous")
+    if out is None:
+        out = torch.empty_like(proj)
+    if out.shape != proj.shape or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor of proj's shape")
+    nu = proj.shape[-1]
+    rows = proj.numel() // nu if nu else 0
+    _check(lib().vamrt_ramlak_filter(proj.data_ptr(), out.data_ptr(), rows, nu, float(pixel_mm),
+                                     VAMRT_CLAMP_NONNEG if clamp else 0, _stream(stream)), "vamrt_ramlak_filter")
+    return out
 
 
 def vamrt_measure_smem_bandwidth(stream=None) -> float:

@@ -74,23 +74,25 @@ def predict(net: U.UNet3D, y: torch.Tensor) -> torch.Tensor:
 
 
 def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.float32, step=0.5, beta=1.0,
-              goal=None):
+              goal=None, mu=0.0):
     """VER after each iteration and cumulative device seconds: object space from m = f with
-    model step beta when g0 is None, else projection space from g0 with relaxation step.
-    Stops early once VER <= goal when a goal is given."""
+    model step beta and momentum mu when g0 is None, else projection space from g0 with
+    relaxation step.  Stops early once VER <= goal when a goal is given."""
     vol = torch.empty_like(f)
     dose = torch.empty(f.shape, device=f.device, dtype=dtype)
     if g0 is None:
         model, proj, mode = f.clone(), torch.empty(P.proj_shape, device=f.device, dtype=dtype), "object"
     else:
         model, proj, mode = vol, g0.clone().to(dtype), "projections"
+    prev = f.clone() if (g0 is None and mu) else None
     t, vers = 0.0, []
     times = []
     for _ in range(iters):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         P.optimize(f, model=model, proj=proj, dose=dose, max_iter=1, tol=0.0, mode=mode,
-                   step=beta if mode == "object" else step)
+                   step=beta if mode == "object" else step, momentum=mu if mode == "object" else 0.0,
+                   prev_model=prev)
         e1.record()
         e1.synchronize()
         t += e0.elapsed_time(e1) / 1e3
@@ -102,10 +104,11 @@ def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.
 
 
 def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iters: int, device="cuda:0", kind="csg",
-            step=0.5, dtype=torch.float32, beta=4.0):
+            step=0.5, dtype=torch.float32, beta=4.0, mu=0.5):
     """Per held-out target: the plain run's final VER, and for the warm start, for the
     same continuation started from g0 = max(0, A^T f) (no network), and for the
-    over-relaxed object-space loop (model step beta, from m = f, storage dtype): the
+    over-relaxed object-space loop (model step beta, momentum mu, from m = f, storage
+    dtype): the
     iterations and device time to reach 1.01 x the plain final VER."""
     rows = []
     for seed in seeds:
@@ -124,7 +127,7 @@ def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iter
         v_ws, t_ws = ver_curve(P, f, cont_iters, g0=g_ws, step=step, dtype=dtype)
         g_cold = P.adjoint(f, clamp_nonneg=True)
         v_cold, t_cold = ver_curve(P, f, cont_iters, g0=g_cold, step=step, dtype=dtype)
-        v_rel, t_rel = ver_curve(P, f, plain_iters, dtype=dtype, beta=beta, goal=goal)
+        v_rel, t_rel = ver_curve(P, f, plain_iters, dtype=dtype, beta=beta, goal=goal, mu=mu)
 
         def hit(v, t, extra=0.0):
             k = next((i for i, x in enumerate(v) if x <= goal), None)

@@ -224,6 +224,30 @@ def test_relaxed_optimizer_matches_oracle_per_iteration(vamrt):
         P.optimize(gpu(f), max_iter=1, step=100.0)
 
 
+def test_momentum_optimizer_matches_oracle_per_iteration(vamrt):
+    """Object-space OSMO with beta = 4 and heavy-ball momentum 0.5 against the FP64 oracle,
+    in one call and as a loop of single-iteration calls that carries prev_model."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                          n_iter=w.osmo_iters, tol=0.0, beta=4.0, mu=0.5)
+    res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, step=4.0, momentum=0.5)
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
+    assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
+    assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL
+    assert rel_l2(res["model"].cpu().numpy(), m_ref) <= FP32_TOL
+    model, prev, errs = gpu(f), gpu(f), []
+    for _ in range(w.osmo_iters):
+        r = P.optimize(gpu(f), model=model, prev_model=prev, max_iter=1, tol=0.0, step=4.0, momentum=0.5)
+        errs.append(r["errors"][0])
+    np.testing.assert_allclose(errs, e_ref, rtol=FP32_TOL)
+    assert rel_l2(model.cpu().numpy(), m_ref) <= FP32_TOL
+    with pytest.raises(vamrt.VamrtError):
+        P.optimize(gpu(f), max_iter=1, momentum=1.0)
+
+
 def test_optimizer_stops_at_tolerance(vamrt):
     w = I.TINY
     pupil = I.workload_pupil(w)
