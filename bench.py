@@ -170,16 +170,18 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def time_to_target(P, target, w, iters, beta=4.0):
+def time_to_target(P, target, w, iters, beta=4.0, mu=0.5):
     """Run the plain FP32 optimiser for `iters` iterations from m = f, recording
     per-iteration device time (CUDA events) and the voxel error rate (VER); then, until
-    they reach the target or `iters` iterations, the BF16-storage run and the over-relaxed
-    runs (model step beta, FP32 and BF16 storage).  Target: VER <= 1.01 x the plain run's
-    final VER."""
+    they reach the target or `iters` iterations, the BF16-storage run, the over-relaxed run
+    (model step beta, BF16 storage) and the over-relaxed runs with heavy-ball momentum mu
+    (FP32 and BF16 storage); and the Radon-method baseline's VER.  Target: VER <= 1.01 x
+    the plain run's final VER."""
     import torch
 
-    def run(dtype, step=1.0, goal=None):
+    def run(dtype, step=1.0, goal=None, momentum=0.0):
         model = target.clone()
+        prev = target.clone() if momentum else None
         proj = torch.empty(w.proj_shape, device=target.device, dtype=dtype)
         dose = torch.empty(w.vol_shape, device=target.device, dtype=dtype)
         t, vers = [], []
@@ -187,7 +189,8 @@ def time_to_target(P, target, w, iters, beta=4.0):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            P.optimize(target, model=model, max_iter=1, tol=0.0, proj=proj, dose=dose, step=step)
+            P.optimize(target, model=model, max_iter=1, tol=0.0, proj=proj, dose=dose, step=step,
+                       momentum=momentum, prev_model=prev)
             e1.record()
             e1.synchronize()
             t.append(e0.elapsed_time(e1) / 1e3)
@@ -199,8 +202,8 @@ def time_to_target(P, target, w, iters, beta=4.0):
     t32, v32 = run(torch.float32)
     goal = 1.01 * v32[-1]
 
-    def variant(dtype, step):
-        t, v = run(dtype, step, goal)
+    def variant(dtype, step, momentum=0.0):
+        t, v = run(dtype, step, goal, momentum)
         hit = next((i for i, x in enumerate(v) if x <= goal), None)
         return {"iterations_to_target": None if hit is None else hit + 1,
                 "seconds_to_target": None if hit is None else float(t[hit]),
@@ -211,10 +214,20 @@ def time_to_target(P, target, w, iters, beta=4.0):
         "plain_fp32": {"iterations": iters, "seconds": float(t32[-1]), "final_ver": v32[-1],
                        "ver_per_iteration": [round(v, 6) for v in v32]},
         "bf16_storage": variant(torch.bfloat16, 1.0),
-        f"relaxed_beta{beta:g}_fp32": variant(torch.float32, beta),
         f"relaxed_beta{beta:g}_bf16": variant(torch.bfloat16, beta),
+        f"relaxed_beta{beta:g}_mu{mu:g}_fp32": variant(torch.float32, beta, mu),
+        f"relaxed_beta{beta:g}_mu{mu:g}_bf16": variant(torch.bfloat16, beta, mu),
         "warm_start": None,
     }
+    from paper_2211_03516_gb300 import radon as RB
+
+    rb = RB.radon_baseline(P, w, target)
+    out["radon_baseline"] = {
+        "method": "Sec. 2.3: per-slice parallel-beam Radon transform, Ram-Lak filter, negatives clipped "
+                  "(no coordinate remap)",
+        "ver_ideal_radon_printer": rb["ver_ideal_radon_printer"],
+        "ver_ray_traced_printer": rb["ver_ray_traced_printer"],
+        "ver_ray_traced_optimiser": v32[-1]}
     ratios = {k: out[k]["time_ratio"] for k in out if isinstance(out[k], dict) and "time_ratio" in out[k]}
     out["time_ratio"] = out["bf16_storage"]["time_ratio"]
     reached = {k: r for k, r in ratios.items() if r is not None}
@@ -310,7 +323,7 @@ def warm_start_time_to_target(args):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     rows = WS.compare(P, net, w, range(100000, 100000 + args.ws_eval), plain_iters=w.osmo_iters,
-                      cont_iters=12, step=0.5, dtype=torch.bfloat16, beta=args.ttt_beta)
+                      cont_iters=12, step=0.5, dtype=torch.bfloat16, beta=args.ttt_beta, mu=args.ttt_mu)
     network = network_throughput(net, pairs[0][1], pairs[0][2], 1.0)
 
     held = []
@@ -333,7 +346,8 @@ def warm_start_time_to_target(args):
             "network": network,
             "held_out": held, "reached": f"{len(ratios)}/{len(held)}",
             "median_time_ratio_of_reached": float(np.median(ratios)) if ratios else None,
-            "relaxed": {"loop": f"object space from m = f, model step {args.ttt_beta:g}, BF16 storage, no network",
+            "relaxed": {"loop": f"object space from m = f, model step {args.ttt_beta:g}, momentum {args.ttt_mu:g}, "
+                                "BF16 storage, no network",
                         "reached": f"{len(rel)}/{len(held)}",
                         "median_time_ratio": float(np.median(rel)) if rel else None}}
 
@@ -442,7 +456,7 @@ def run_gpu(args, rank, world):
     # ---- time to target: plain FP32 optimiser vs the BF16-storage optimiser ----
     ttt = None
     if args.ttt_iters > 0:
-        ttt = time_to_target(P, target, w, args.ttt_iters, beta=args.ttt_beta)
+        ttt = time_to_target(P, target, w, args.ttt_iters, beta=args.ttt_beta, mu=args.ttt_mu)
         if args.ws_train > 0:
             ttt["warm_start"] = warm_start_time_to_target(args)
 
@@ -504,6 +518,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttt-beta", type=float, default=4.0,
                     help="model step of the over-relaxed optimiser variant in the time-to-target comparison")
+    ap.add_argument("--ttt-mu", type=float, default=0.5,
+                    help="heavy-ball momentum of the over-relaxed optimiser variant")
     ap.add_argument("--ttt-iters", type=int, default=30,
                     help="optimiser iterations of the time-to-target comparison (0 = skip)")
     ap.add_argument("--ws-train", type=int, default=64, help="warm-start training targets (0 = skip)")

@@ -181,6 +181,15 @@ def workload_pupil(w: Workload) -> np.ndarray:
     return pupil_samples(w.pupil_pattern, w.rays_per_pixel, w.seed)
 
 
+def radon_workload(w: Workload) -> Workload:
+    """The printer the Radon method assumes (Sec. 2.3): parallel chief rays (telecentric,
+    zero etendue), no refraction (all indices 1) and no attenuation, on w's grid, pixels
+    and angles -- the geometry in which the ray-traced projection is the per-slice
+    parallel-beam Radon transform."""
+    return replace(w, name=w.name + "_radon", pupil_mm=INF, f_number=INF, pupil_pattern="chief",
+                   rays_per_pixel=1, n_outside=1.0, n_glass=1.0, n_resin=1.0, mu_per_mm=0.0)
+
+
 def default_angles(n_angles: int) -> np.ndarray:
     """theta_k = 2*pi*k/N (a full turn in equal steps, Sec. 2.5)."""
     return 2.0 * np.pi * np.arange(n_angles, dtype=np.float64) / n_angles
