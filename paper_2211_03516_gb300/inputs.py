@@ -181,6 +181,32 @@ def workload_pupil(w: Workload) -> np.ndarray:
     return pupil_samples(w.pupil_pattern, w.rays_per_pixel, w.seed)
 
 
+# Fin part (Sec. 3: 1 mm fins at a 2.25 mm period, normal to the vial axis, on a base at
+# the projector's optical axis), built on a 2 mm base with a 1 mm spine; half-width 4 mm.
+FIN_BASE_MM, FIN_GAP0_MM, FIN_PERIOD_MM, FIN_THICK_MM, FIN_HALF_MM = 2.0, 1.25, 2.25, 1.0, 4.0
+
+
+def fin_bottoms_mm(n_fins: int) -> np.ndarray:
+    """z of the lower face of each fin (the base spans z in [0, 2] mm)."""
+    return FIN_BASE_MM + FIN_GAP0_MM + FIN_PERIOD_MM * np.arange(n_fins)
+
+
+def fins_workload(n_fins: int = 9) -> Workload:
+    """The non-telecentric printer of Sec. 2.6.1 for the fin part: pupil (ideal lens at the
+    aperture stop) 99.5 mm from the axis, chief rays only (low etendue), vial OD 25 / ID
+    23.6 mm, 0.216 mm voxels (the paper's minimum after its 4 x 4 downsampling) and pixels
+    of the same pitch, 360 angles.  The grid is centred on z = 0 (the optical axis) and
+    tall enough for the part above it.  Unstated values (indices, absorption) as in the
+    256^3 workload."""
+    h = 0.216
+    top = float(fin_bottoms_mm(n_fins)[-1]) + FIN_THICK_MM + 1.0
+    nz = 2 * int(math.ceil(top / h))
+    return Workload(name=f"fins{n_fins}_nontelecentric_{nz}z", nx=112, ny=112, nz=nz, voxel_mm=h,
+                    nu=112, nv=nz, pixel_u_mm=h, pixel_v_mm=h, n_angles=360, pupil_mm=99.5, f_number=INF,
+                    pupil_pattern="chief", rays_per_pixel=1, r_inner_mm=11.8, wall_mm=0.7, n_outside=1.0,
+                    n_glass=1.47, n_resin=1.50, mu_per_mm=0.03, target=f"fins{n_fins}", osmo_iters=40)
+
+
 def radon_workload(w: Workload) -> Workload:
     """The printer the Radon method assumes (Sec. 2.3): parallel chief rays (telecentric,
     zero etendue), no refraction (all indices 1) and no attenuation, on w's grid, pixels
@@ -317,6 +343,14 @@ def make_target(w: Workload, kind: Optional[str] = None, seed: Optional[int] = N
             else:
                 m |= p
         m &= X * X + Y * Y <= reach * reach
+    elif kind.startswith("fins"):
+        n_fins = int(kind[4:])
+        hx = FIN_HALF_MM
+        zt = float(fin_bottoms_mm(n_fins)[-1]) + FIN_THICK_MM
+        m = _box(Z, Y, X, (0.0, 0.0, FIN_BASE_MM / 2), (hx, hx, FIN_BASE_MM / 2))           # base
+        m |= _box(Z, Y, X, (0.0, hx - 0.5, zt / 2), (hx, 0.5, zt / 2))                      # spine
+        for zb in fin_bottoms_mm(n_fins):
+            m |= _box(Z, Y, X, (0.0, 0.0, zb + FIN_THICK_MM / 2), (hx, hx, FIN_THICK_MM / 2))
     else:
         raise ValueError(f"unknown target {kind!r}")
     return m.astype(np.float32)
