@@ -47,6 +47,17 @@ typedef struct {
     const double *angles;   /* radians */
     double step_vox;        /* nominal sample spacing in voxels */
     int32_t unattenuated;   /* projection only: weight delta / M, no Fresnel or Beer-Lambert (Sec. 2.4 as printed) */
+    /* Optional lens train between the pixel array and the vial (Sec. 2.1: rays refract at
+     * every optical element; Sec. 2.6.2: two plano-spherical lenses and an iris).  When
+     * n_surf > 0 it replaces the pupil model: pixel (u,v) sits at Q_uv / mag in the plane
+     * y = obj_y, aperture sample (xi, eta) leaves it with direction proportional to
+     * (xi r_s / aim, 1, eta r_s / aim) (r_s the stop radius), and the ray is refracted by
+     * Snell's law at each surface (transmission 1: coated lenses), blocked by any clear
+     * aperture it falls outside of, and handed to the vial in air. */
+    int32_t n_surf;
+    const double *surf;     /* n_surf x 5: vertex y, radius (INFINITY = plane; centre at y + radius),
+                               index after, clear semi-aperture, stop flag */
+    double obj_y, mag, aim;
 } orc_geom;
 
 typedef struct {
@@ -99,6 +110,66 @@ static int refract(const double p[3], double r, const double d[3], double n1, do
     return 1;
 }
 
+/* Snell's law in vector form for a unit normal nrm (either orientation) and unit
+ * direction d, index n1 -> n2.  Returns 0 on total internal reflection. */
+static int refract_normal(const double nrm[3], const double d[3], double n1, double n2, double out[3])
+{
+    double n[3] = {nrm[0], nrm[1], nrm[2]};
+    double cn = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+    if (cn > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; cn = -cn; }
+    double c1 = -cn, eta = n1 / n2;
+    double k = 1.0 - eta * eta * (1.0 - c1 * c1);
+    if (k < 0.0) return 0;
+    double c2 = sqrt(k);
+    for (int i = 0; i < 3; ++i) out[i] = eta * d[i] + (eta * c1 - c2) * n[i];
+    return 1;
+}
+
+/* Carry the ray (o, d) through the lens train; on return o is its point on the last
+ * surface and d its direction in the air behind it.  Returns 0 when a surface is missed
+ * or a clear aperture blocks the ray (or on total internal reflection). */
+int orc_lens_train(const orc_geom *g, double o[3], double d[3])
+{
+    double n_cur = g->n_out;
+    for (int s = 0; s < g->n_surf; ++s) {
+        const double *S = g->surf + 5 * s;
+        double yv = S[0], R = S[1], n2 = S[2], clear = S[3];
+        int stop = S[4] != 0.0;
+        double t, p[3], nrm[3];
+        if (isinf(R)) {
+            if (d[1] == 0.0) return 0;
+            t = (yv - o[1]) / d[1];
+        } else {
+            /* sphere of radius |R| centred at (0, yv + R, 0): the root on the vertex side */
+            double c[3] = {0.0, yv + R, 0.0};
+            double oc[3] = {o[0] - c[0], o[1] - c[1], o[2] - c[2]};
+            double b = d[0] * oc[0] + d[1] * oc[1] + d[2] * oc[2];
+            double cc = oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2] - R * R;
+            double disc = b * b - cc;
+            if (disc < 0.0) return 0;
+            double sq = sqrt(disc), roots[2] = {-b - sq, -b + sq};
+            t = -1.0;
+            for (int k = 0; k < 2 && t < 0.0; ++k) {
+                double py = o[1] + roots[k] * d[1];
+                if (roots[k] > 0.0 && (py - c[1]) * (yv - c[1]) > 0.0) t = roots[k];
+            }
+        }
+        if (!(t > 0.0)) return 0;
+        for (int i = 0; i < 3; ++i) p[i] = o[i] + t * d[i];
+        if (p[0] * p[0] + p[2] * p[2] > clear * clear) return 0;
+        if (!stop) {
+            if (isinf(R)) { nrm[0] = 0.0; nrm[1] = 1.0; nrm[2] = 0.0; }
+            else { nrm[0] = p[0] / R; nrm[1] = (p[1] - (yv + R)) / R; nrm[2] = p[2] / R; }
+            double out[3];
+            if (!refract_normal(nrm, d, n_cur, n2, out)) return 0;
+            for (int i = 0; i < 3; ++i) d[i] = out[i];
+        }
+        for (int i = 0; i < 3; ++i) o[i] = p[i];
+        n_cur = n2;
+    }
+    return 1;
+}
+
 /* Trace one ray (pixel u, v, aperture sample a) in the vial frame at theta = 0. */
 int orc_trace(const orc_geom *g, int32_t u, int32_t v, int32_t a, orc_ray *ray)
 {
@@ -108,7 +179,16 @@ int orc_trace(const orc_geom *g, int32_t u, int32_t v, int32_t a, orc_ray *ray)
     double qz = (v - 0.5 * (g->nv - 1)) * g->pv;
     double xi = g->pupil_xy[2 * a], eta = g->pupil_xy[2 * a + 1];
     double *o = ray->origin, *d = ray->d0;
-    if (isinf(g->pupil)) {
+    if (g->n_surf > 0) {
+        double rs = 0.0;
+        for (int s = 0; s < g->n_surf; ++s)
+            if (g->surf[5 * s + 4] != 0.0) rs = g->surf[5 * s + 3];
+        double dx = xi * rs / g->aim, dy = 1.0, dz = eta * rs / g->aim;
+        double nrm = sqrt(dx * dx + dy * dy + dz * dz);
+        d[0] = dx / nrm; d[1] = dy / nrm; d[2] = dz / nrm;
+        o[0] = qx / g->mag; o[1] = g->obj_y; o[2] = qz / g->mag;
+        if (!orc_lens_train(g, o, d)) { ray->status = 0; return 0; }
+    } else if (isinf(g->pupil)) {
         /* telecentric: every ray crosses Q; the cone half-angle is atan(1/(2N)) */
         double ta = isinf(g->fnum) ? 0.0 : 1.0 / (2.0 * g->fnum);
         double dx = -xi * ta, dy = 1.0, dz = -eta * ta;

@@ -44,6 +44,8 @@ class OrcGeom(ctypes.Structure):
         ("n_angles", ctypes.c_int32), ("angles", _dp),
         ("step_vox", ctypes.c_double),
         ("unattenuated", ctypes.c_int32),
+        ("n_surf", ctypes.c_int32), ("surf", _dp),
+        ("obj_y", ctypes.c_double), ("mag", ctypes.c_double), ("aim", ctypes.c_double),
     ]
 
 
@@ -87,6 +89,8 @@ def lib():
         L.orc_sample_count.argtypes = [ctypes.POINTER(OrcGeom)]
         L.orc_sample_count.restype = ctypes.c_uint64
         L.orc_sizeof_geom.restype = ctypes.c_int32
+        L.orc_lens_train.argtypes = [ctypes.POINTER(OrcGeom), _dp, _dp]
+        L.orc_lens_train.restype = ctypes.c_int
         L.orc_sizeof_ray.restype = ctypes.c_int32
         assert L.orc_sizeof_geom() == ctypes.sizeof(OrcGeom)
         assert L.orc_sizeof_ray() == ctypes.sizeof(OrcRay)
@@ -113,6 +117,13 @@ class _Geom:
         g.angles = self.angles.ctypes.data_as(_dp)
         g.step_vox = w.step_vox
         g.unattenuated = 1 if unattenuated else 0
+        lens = getattr(w, "lens", None)
+        if lens is not None:
+            self.surf = np.array([[sf.y_mm, sf.radius_mm, sf.n_after, sf.clear_mm, 1.0 if sf.stop else 0.0]
+                                  for sf in lens.surfaces], dtype=np.float64).ravel()
+            g.n_surf = len(lens.surfaces)
+            g.surf = self.surf.ctypes.data_as(_dp)
+            g.obj_y, g.mag, g.aim = lens.object_y_mm, lens.magnification, lens.aim_mm
         self.g = g
 
     @property
@@ -169,6 +180,16 @@ def forward(w, proj, pupil_xy, angles=None) -> np.ndarray:
     out = np.zeros((w.nz, w.ny, w.nx), dtype=np.float64)
     lib().orc_forward(G.ref, p.ctypes.data_as(_dp), out.ctypes.data_as(_dp))
     return out
+
+
+def lens_trace(w, origin, direction):
+    """The oracle's lens-train stage alone: (ok, point on the last surface, direction
+    behind it) for a ray (origin, unit direction) starting before the first surface."""
+    G = geom(w, np.zeros((1, 2)), np.zeros(1))
+    o = np.array(origin, dtype=np.float64)
+    d = np.array(direction, dtype=np.float64)
+    ok = lib().orc_lens_train(G.ref, o.ctypes.data_as(_dp), d.ctypes.data_as(_dp))
+    return bool(ok), o, d
 
 
 def sample_count(w, pupil_xy, angles=None) -> int:

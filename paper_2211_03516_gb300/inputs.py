@@ -22,6 +22,75 @@ INF = float("inf")
 
 
 @dataclass(frozen=True)
+class Surface:
+    """One rotationally symmetric surface of a lens train on the optical axis (the y axis
+    through x = z = 0): vertex at y_mm, radius of curvature radius_mm (centre at
+    y_mm + radius_mm; INF = plane), index n_after behind it, clear semi-aperture clear_mm;
+    stop: the aperture stop (an iris: a plane that blocks, no refraction)."""
+
+    y_mm: float
+    radius_mm: float
+    n_after: float
+    clear_mm: float
+    stop: bool = False
+
+
+@dataclass(frozen=True)
+class LensTrain:
+    """Surfaces between the pixel array (at object_y_mm) and the vial, in increasing y.
+    Pixel (u, v) sits at Q_uv / magnification in the object plane (Q_uv its nominal image
+    point in the best-focus plane y = 0); aperture sample (xi, eta) leaves it with
+    direction proportional to (xi r_s / aim_mm, 1, eta r_s / aim_mm), r_s = the stop radius
+    (object-space telecentric launch aimed paraxially at the stop)."""
+
+    surfaces: tuple
+    object_y_mm: float
+    magnification: float
+    aim_mm: float
+
+
+def _abcd(surfaces, n0, y0, y1):
+    """Paraxial (height, n * angle) transfer matrix from plane y0 to plane y1 through the
+    surfaces between them."""
+    M = np.eye(2)
+    y, n = y0, n0
+    for sf in surfaces:
+        M = np.array([[1.0, (sf.y_mm - y) / n], [0.0, 1.0]]) @ M
+        if not sf.stop and math.isfinite(sf.radius_mm):
+            M = np.array([[1.0, 0.0], [-(sf.n_after - n) / sf.radius_mm, 1.0]]) @ M
+        y, n = sf.y_mm, sf.n_after
+    return np.array([[1.0, (y1 - y) / n], [0.0, 1.0]]) @ M
+
+
+def telecentric_relay(lens_radius_mm: float = 38.6, lens_thickness_mm: float = 4.1, n_lens: float = 1.5302,
+                      lens_clear_mm: float = 12.7, iris_diameter_mm: float = 16.0, n_air: float = 1.0) -> LensTrain:
+    """The telecentric printer of Sec. 2.6.2 as a parameterised 4f relay: two identical
+    plano-convex lenses, convex faces towards the iris midway between them, the pixel array
+    at the front focal plane of the first and the best-focus plane y = 0 at the back focal
+    plane of the second (paraxial), so unit magnification, object and image space
+    telecentric.  The paper names the lens (a 75 mm plano-convex singlet) but not its
+    prescription; the defaults are a stock 75 mm N-BK7 plano-convex lens (index at 405 nm),
+    with which the pixel array lands near the paper's y = -294 mm."""
+    R, tc, n = lens_radius_mm, lens_thickness_mm, n_lens
+    # first lens: plane face at y = 0 (reference), convex face at y = tc bulging towards +y
+    l1 = [Surface(0.0, INF, n, lens_clear_mm), Surface(tc, -R, n_air, lens_clear_mm)]
+    # paraxial matrix of the first lens from its plane face to its convex vertex
+    M = _abcd(l1, n_air, 0.0, tc)
+    f_eff = -n_air / M[1, 0]
+    bfd = -M[0, 0] / M[1, 0] * n_air             # convex vertex -> back focus (parallel input)
+    ffd = -M[1, 1] / M[1, 0] * n_air             # front focus -> plane face (parallel output)
+    stop_y = tc + bfd
+    # second lens mirrored about the stop
+    l2 = [Surface(2 * stop_y - tc, R, n, lens_clear_mm), Surface(2 * stop_y, INF, n_air, lens_clear_mm)]
+    image_y = 2 * stop_y + ffd
+    obj_y = -ffd
+    shift = -image_y                             # put the image plane at y = 0
+    surfs = tuple(Surface(sf.y_mm + shift, sf.radius_mm, sf.n_after, sf.clear_mm, sf.stop)
+                  for sf in l1 + [Surface(stop_y, INF, n_air, iris_diameter_mm / 2, True)] + l2)
+    return LensTrain(surfaces=surfs, object_y_mm=obj_y + shift, magnification=-1.0, aim_mm=f_eff)
+
+
+@dataclass(frozen=True)
 class Workload:
     """One printer + vial + grid configuration (units: mm, radians, 1/mm).
 
@@ -56,6 +125,7 @@ class Workload:
     target: str = "sphere_cube"
     seed: int = 0
     osmo_iters: int = 10
+    lens: Optional[LensTrain] = None   # a lens train replacing the ideal pupil model
 
     def scaled(self, **kw) -> "Workload":
         return replace(self, **kw)

@@ -18,6 +18,7 @@ from scipy.ndimage import map_coordinates
 from oracle import optics as OP
 from oracle import osmo as OS
 from oracle import vam_oracle as O
+from paper_2211_03516_gb300 import inputs as I
 from paper_2211_03516_gb300.inputs import INF, Workload, default_angles, pupil_samples, voxel_centres
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -402,6 +403,78 @@ def test_osmo_momentum_adds_the_previous_step():
     assert np.abs(m1 - f).max() > 0.05
     _, _, m2_two, _ = OS.osmo(f, project, dose, n_iter=2, tol=0.0, beta=2.0, mu=0.5)
     np.testing.assert_allclose(m2_two, m2_mu, rtol=0, atol=1e-15)
+
+
+# --- lens train (Sec. 2.1, 2.6.2) -------------------------------------------------------
+def _lens_w(surfaces, **kw):
+    L = I.LensTrain(surfaces=tuple(surfaces), object_y_mm=-100.0, magnification=-1.0, aim_mm=50.0)
+    return I.TINY.scaled(lens=L, **kw)
+
+
+def test_thick_lens_focus_matches_the_lensmaker_formula():
+    """A paraxial ray parallel to the axis through a biconvex thick lens crosses the axis at
+    the back focal distance f (1 - (n - 1) t / (n R1)), 1/f = (n - 1)(1/R1 - 1/R2 +
+    (n - 1) t / (n R1 R2))."""
+    R1, R2, t, n = 50.0, -50.0, 5.0, 1.5
+    w = _lens_w([I.Surface(0.0, R1, n, 20.0), I.Surface(t, R2, 1.0, 20.0)])
+    f = 1.0 / ((n - 1) * (1 / R1 - 1 / R2 + (n - 1) * t / (n * R1 * R2)))
+    bfd = f * (1 - (n - 1) * t / (n * R1))
+    ok, o, d = O.lens_trace(w, [0.01, -50.0, 0.0], [0.0, 1.0, 0.0])
+    assert ok
+    y_cross = o[1] - o[0] * d[1] / d[0]
+    assert abs((y_cross - t) - bfd) < 1e-5 * f
+
+
+def test_plane_parallel_plate_shifts_without_deviating():
+    """A tilted ray through a plate of thickness t and index n leaves parallel to itself,
+    displaced by t sin(a) (1 - cos(a) / sqrt(n^2 - sin^2(a)))."""
+    t, n, a = 3.0, 1.6, 0.3
+    w = _lens_w([I.Surface(0.0, I.INF, n, 50.0), I.Surface(t, I.INF, 1.0, 50.0)])
+    d0 = np.array([np.sin(a), np.cos(a), 0.0])
+    o0 = np.array([0.0, -10.0, 0.0])
+    ok, o, d = O.lens_trace(w, o0, d0)
+    assert ok and np.allclose(d, d0, atol=1e-15)
+    # distance between the exit line and the undeviated line
+    shift = np.linalg.norm(np.cross(o - o0, d0))
+    assert abs(shift - t * np.sin(a) * (1 - np.cos(a) / np.sqrt(n * n - np.sin(a) ** 2))) < 1e-12
+
+
+def test_lens_train_conserves_the_skew_invariant_and_blocks_outside_apertures():
+    """Refraction at surfaces symmetric about the optical axis conserves n (z d_x - x d_z);
+    a ray outside a clear aperture is blocked."""
+    L = I.telecentric_relay()
+    w = I.TINY.scaled(lens=L)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        o0 = np.array([rng.uniform(-3, 3), L.object_y_mm, rng.uniform(-3, 3)])
+        d0 = np.array([rng.uniform(-0.05, 0.05), 1.0, rng.uniform(-0.05, 0.05)])
+        d0 /= np.linalg.norm(d0)
+        ok, o, d = O.lens_trace(w, o0, d0)
+        if not ok:
+            continue
+        L0 = o0[2] * d0[0] - o0[0] * d0[2]
+        L1 = o[2] * d[0] - o[0] * d[2]
+        assert abs(L1 - L0) < 1e-12 and abs(np.linalg.norm(d) - 1) < 1e-14
+    ok, _, _ = O.lens_trace(w, [0.0, L.object_y_mm, 0.0], [0.2, 1.0, 0.0] / np.linalg.norm([0.2, 1.0, 0.0]))
+    assert not ok                                    # 0.2 rad misses the 12.7 mm lens / 8 mm iris
+
+
+def test_telecentric_relay_images_and_stays_telecentric():
+    """Sec. 2.6.2's printer as a 4f relay: near the axis every aperture ray of a pixel
+    lands on the pixel's image point in y = 0 and the chief ray leaves parallel to the
+    axis (unit magnification, image-space telecentric)."""
+    w = I.TINY.scaled(lens=I.telecentric_relay(iris_diameter_mm=2.5), pupil_pattern="hex13", rays_per_pixel=13,
+                      f_number=4.0)
+    pup = I.workload_pupil(w)
+    for u, v in ((32, 32), (33, 31)):
+        q = np.array([(u - (w.nu - 1) / 2) * w.pixel_u_mm, 0.0, (v - (w.nv - 1) / 2) * w.pixel_v_mm])
+        for a in range(13):
+            r = O.trace(w, pup, u, v, a)
+            o, d = r["origin"], r["d0"]
+            p = o - o[1] / d[1] * d
+            assert np.linalg.norm(p - q) < 2e-3, (u, v, a)
+            if a == 0:
+                assert abs(d[0]) < 1e-4 and abs(d[2]) < 1e-4
 
 
 # --- Radon-method baseline (Sec. 2.3) ---------------------------------------------------
