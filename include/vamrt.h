@@ -74,8 +74,28 @@ typedef enum {
  *   step_vox    nominal spacing of the samples on a ray, in voxels (0 = 0.5, the 2x
  *               super-sampling of Sec. 2.2).  Each in-resin segment of length ell gets
  *               K = ceil(ell / (step_vox h) - 1e-9) midpoint samples s_j = (j+1/2) ell/K.
+ *   n_surfaces  0: the ideal-pupil model above.  > 0: a lens train of n_surfaces surfaces
+ *               (HOST array `surfaces`, copied) between the pixel array and the vial
+ *               replaces it (Sec. 2.1: rays refract at every optical element; Sec. 2.6.2:
+ *               the telecentric printer's lenses and iris).  Pixel (u,v) then sits at
+ *               Q_uv / magnification in the plane y = object_y_mm (Q_uv its image point in
+ *               y = 0); aperture sample (xi, eta) leaves it with direction proportional to
+ *               (xi r_s / aim_mm, 1, eta r_s / aim_mm), r_s = the stop's clear_mm (an
+ *               object-space telecentric launch aimed paraxially at the stop; for a
+ *               telecentric relay aim_mm is the focal length before the stop).  At each
+ *               surface the ray refracts by the vector Snell law (transmission 1: coated
+ *               lenses) and is blocked outside the clear aperture; blocked rays carry no
+ *               light.  pupil_mm and f_number are then ignored.
  * The grid must enclose the resin cylinder: r_inner_mm / voxel_mm <= (min(nx,ny)+1)/2 - 0.01.
  */
+typedef struct {
+    double y_mm;               /* vertex on the optical axis (the y axis through x = z = 0) */
+    double radius_mm;          /* radius of curvature, centre at y_mm + radius_mm; INFINITY = plane */
+    double n_after;            /* index behind the surface (in front: the previous surface's, or n_outside) */
+    double clear_mm;           /* clear semi-aperture (the stop: its radius) */
+    int32_t is_stop;           /* nonzero: the aperture stop, a plane that blocks and does not refract */
+} vamrt_surface;
+
 typedef struct {
     int32_t nx, ny, nz;
     double voxel_mm;
@@ -91,6 +111,11 @@ typedef struct {
     int32_t n_angles;
     const double *angles_rad;
     double step_vox;
+    int32_t n_surfaces;              /* 0 = ideal pupil; 1..64 = lens train (see above) */
+    const vamrt_surface *surfaces;   /* HOST array in increasing y_mm, exactly one stop, last n_after = n_outside */
+    double object_y_mm;              /* pixel array plane, before the first surface */
+    double magnification;            /* paraxial image / object height (nonzero) */
+    double aim_mm;                   /* launch aim distance (> 0) */
 } vamrt_geometry;
 
 typedef struct vamrt_projector vamrt_projector;   /* opaque */

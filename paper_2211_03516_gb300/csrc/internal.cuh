@@ -52,6 +52,9 @@ struct TraceParams {
     int telecentric, chief_only;
     double r_in, r_out, n_out, n_glass, n_resin;
     double h, ds;
+    const double *surf;       // device, n_surf x (y, radius, n_after, clear, stop flag); n_surf = 0: pupil model
+    int n_surf;
+    double obj_y, mag, aim, stop_r;
 };
 
 }  // namespace vamrt

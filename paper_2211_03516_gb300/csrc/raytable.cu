@@ -1,7 +1,8 @@
 // Ray generation and refraction through the vial (Sec. 2.1), once per projector, FP64.
 //
 // One thread per (pixel, aperture sample).  The ray leaves the aperture stop (or, for a
-// telecentric projector, arrives parallel to its cone direction), meets the outer
+// telecentric projector, arrives parallel to its cone direction; or, with a lens train,
+// leaves the pixel and refracts through every lens surface), meets the outer
 // cylinder, refracts into the glass by the vector form of Snell's law with the
 // unpolarised Fresnel transmission, does the same at the inner cylinder, and runs
 // straight through the resin to the inner wall on the far side.  Everything up to the
@@ -55,6 +56,54 @@ __device__ bool snell(d3 p, double R, d3 d, double n1, double n2, d3 &out, doubl
     return true;
 }
 
+__device__ inline double dot3(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Lens train (Sec. 2.1: rays refract at every optical element on the way to the vial).
+// Surface k: sv[5k..5k+4] = vertex y, radius of curvature (centre at y + radius; INF =
+// plane), index behind, clear semi-aperture, stop flag.  The ray (o, d) starts in front
+// of the first surface in the outside medium; on success o is its point on the last
+// surface and d its direction behind it.  False when a surface is missed, a clear
+// aperture blocks the ray, or it is totally reflected.
+__device__ bool through_lenses(const double *sv, int n_surf, double n0, d3 &o, d3 &d)
+{
+    double n_in = n0;
+    for (int k = 0; k < n_surf; ++k) {
+        const double yv = sv[5 * k], R = sv[5 * k + 1], n_out = sv[5 * k + 2], ap = sv[5 * k + 3];
+        const bool iris = sv[5 * k + 4] != 0.0;
+        double t = -1.0;
+        d3 c = {0.0, yv + R, 0.0};
+        if (isinf(R)) {
+            if (d.y != 0.0) t = (yv - o.y) / d.y;
+        } else {
+            // |o + t d - c| = |R|: of the two crossings take the one on the vertex's side of c
+            const d3 oc = {o.x - c.x, o.y - c.y, o.z - c.z};
+            const double half_b = dot3(d, oc);
+            const double disc = half_b * half_b - (dot3(oc, oc) - R * R);
+            if (disc >= 0.0) {
+                const double root = sqrt(disc);
+                const double ta = -half_b - root, tb = -half_b + root;
+                if (ta > 0.0 && (o.y + ta * d.y - c.y) * (yv - c.y) > 0.0) t = ta;
+                else if (tb > 0.0 && (o.y + tb * d.y - c.y) * (yv - c.y) > 0.0) t = tb;
+            }
+        }
+        if (!(t > 0.0)) return false;
+        const d3 p = o + t * d;
+        if (p.x * p.x + p.z * p.z > ap * ap) return false;           // vignetted
+        if (!iris) {
+            d3 nrm = isinf(R) ? d3{0.0, 1.0, 0.0} : d3{p.x / R, (p.y - c.y) / R, p.z / R};
+            double cosi = -dot3(nrm, d);
+            if (cosi < 0.0) { nrm = -1.0 * nrm; cosi = -cosi; }
+            const double mu = n_in / n_out;
+            const double rad = 1.0 - mu * mu * (1.0 - cosi * cosi);
+            if (rad < 0.0) return false;
+            d = mu * d + (mu * cosi - sqrt(rad)) * nrm;
+        }
+        o = p;
+        n_in = n_out;
+    }
+    return true;
+}
+
 __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *__restrict__ B,
                                 int2 *__restrict__ J, unsigned long long *__restrict__ counters)
 {
@@ -73,7 +122,13 @@ __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *_
     const d3 Q = {(u - 0.5 * (P.nu - 1)) * P.pu, 0.0, (v - 0.5 * (P.nv - 1)) * P.pv};
     const double xi = P.pupil_xy[2 * a], et = P.pupil_xy[2 * a + 1];
     d3 o, d;
-    if (P.telecentric) {
+    if (P.n_surf > 0) {
+        // pixel in the object plane, launched telecentric in object space towards the stop
+        o = {Q.x / P.mag, P.obj_y, Q.z / P.mag};
+        d = {xi * P.stop_r / P.aim, 1.0, et * P.stop_r / P.aim};
+        d = (1.0 / sqrt(dot3(d, d))) * d;
+        if (!through_lenses(P.surf, P.n_surf, P.n_out, o, d)) return;          // blocked
+    } else if (P.telecentric) {
         const double t = P.chief_only ? 0.0 : 1.0 / (2.0 * P.f_number);
         d = {-xi * t, 1.0, -et * t};
         d = (1.0 / sqrt(d.x * d.x + d.y * d.y + d.z * d.z)) * d;

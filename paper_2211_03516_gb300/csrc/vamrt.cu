@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -71,6 +72,34 @@ vamrt_status validate(const vamrt_geometry *g)
     if (g->angles_rad)
         for (int k = 0; k < g->n_angles; ++k)
             if (!isfinite(g->angles_rad[k])) return fail(VAMRT_EINVAL, "angle %d is not finite", k);
+    if (g->n_surfaces < 0 || g->n_surfaces > 64) return fail(VAMRT_EINVAL, "n_surfaces must be in 0..64");
+    if (g->n_surfaces > 0) {
+        if (!g->surfaces) return fail(VAMRT_EINVAL, "surfaces is NULL");
+        if (!isfinite(g->object_y_mm) || !(g->object_y_mm < g->surfaces[0].y_mm))
+            return fail(VAMRT_EINVAL, "object_y_mm must be finite and before the first surface");
+        if (!isfinite(g->magnification) || g->magnification == 0.0)
+            return fail(VAMRT_EINVAL, "magnification must be finite and nonzero");
+        if (!finite_pos(g->aim_mm)) return fail(VAMRT_EINVAL, "aim_mm must be finite and > 0");
+        int stops = 0;
+        for (int s = 0; s < g->n_surfaces; ++s) {
+            const vamrt_surface &S = g->surfaces[s];
+            if (!isfinite(S.y_mm) || (s > 0 && !(S.y_mm > g->surfaces[s - 1].y_mm)))
+                return fail(VAMRT_EINVAL, "surface %d: y_mm must be finite and increasing", s);
+            if (isnan(S.radius_mm) || S.radius_mm == 0.0 || (isinf(S.radius_mm) && S.radius_mm < 0.0))
+                return fail(VAMRT_EINVAL, "surface %d: radius_mm must be nonzero (INFINITY = plane)", s);
+            if (!finite_pos(S.n_after) || !finite_pos(S.clear_mm))
+                return fail(VAMRT_EINVAL, "surface %d: n_after and clear_mm must be finite and > 0", s);
+            if (S.is_stop) {
+                ++stops;
+                if (!isinf(S.radius_mm)) return fail(VAMRT_EINVAL, "surface %d: the stop must be a plane", s);
+            }
+        }
+        if (stops != 1) return fail(VAMRT_EINVAL, "the lens train needs exactly one stop (found %d)", stops);
+        if (g->surfaces[g->n_surfaces - 1].n_after != g->n_outside)
+            return fail(VAMRT_EINVAL, "the last surface must leave the ray in the outside medium (n_outside)");
+        if (!(g->surfaces[g->n_surfaces - 1].y_mm < -(g->r_inner_mm + g->wall_mm)))
+            return fail(VAMRT_EINVAL, "the lens train must end before the vial");
+    }
     const int nmin = g->nx < g->ny ? g->nx : g->ny;
     if (!(g->r_inner_mm / g->voxel_mm <= 0.5 * (nmin + 1) - 0.01))
         return fail(VAMRT_EINVAL, "grid (%d x %d voxels of %g mm) does not enclose the resin radius %g mm",
@@ -158,6 +187,7 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     p->g = *geom;
     p->g.pupil_xy = nullptr;
     p->g.angles_rad = nullptr;
+    p->g.surfaces = nullptr;          // host array, used only while tracing below
     if (p->g.step_vox == 0.0) p->g.step_vox = 0.5;
     const vamrt_geometry &g = p->g;
     const int M = g.rays_per_pixel;
@@ -192,14 +222,28 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     free(hcs);
     if (e != cudaSuccess) return cuda_fail(e, "angle table upload");
 
-    // pupil samples and counters in one temporary device block
+    // pupil samples, counters and the lens train (5 doubles per surface) in one temporary
+    // device block
     const size_t pupil_bytes = sizeof(double) * 2 * M;
+    const int n_surf = geom->n_surfaces;
+    std::vector<double> hsurf(5 * (size_t)n_surf);
+    double stop_r = 0.0;
+    for (int k = 0; k < n_surf; ++k) {
+        const vamrt_surface &S = geom->surfaces[k];
+        hsurf[5 * k] = S.y_mm; hsurf[5 * k + 1] = S.radius_mm; hsurf[5 * k + 2] = S.n_after;
+        hsurf[5 * k + 3] = S.clear_mm; hsurf[5 * k + 4] = S.is_stop ? 1.0 : 0.0;
+        if (S.is_stop) stop_r = S.clear_mm;
+    }
+    const size_t surf_bytes = sizeof(double) * hsurf.size();
     void *tmp = nullptr;
-    CK(cudaMalloc(&tmp, pupil_bytes + 2 * sizeof(unsigned long long)), "cudaMalloc(tmp)");
+    CK(cudaMalloc(&tmp, pupil_bytes + surf_bytes + 2 * sizeof(unsigned long long)), "cudaMalloc(tmp)");
     double *d_pupil = (double *)tmp;
-    unsigned long long *d_cnt = (unsigned long long *)((char *)tmp + pupil_bytes);
+    double *d_surf = d_pupil + 2 * M;
+    unsigned long long *d_cnt = (unsigned long long *)((char *)tmp + pupil_bytes + surf_bytes);
     double chief[2] = {0.0, 0.0};
     e = cudaMemcpyAsync(d_pupil, geom->pupil_xy ? geom->pupil_xy : chief, pupil_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_surf > 0)
+        e = cudaMemcpyAsync(d_surf, hsurf.data(), surf_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s);
 
     vamrt::TraceParams T;
@@ -212,6 +256,8 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     T.r_in = g.r_inner_mm; T.r_out = g.r_inner_mm + g.wall_mm;
     T.n_out = g.n_outside; T.n_glass = g.n_glass; T.n_resin = g.n_resin;
     T.h = g.voxel_mm; T.ds = g.step_vox * g.voxel_mm;
+    T.surf = d_surf; T.n_surf = n_surf;
+    T.obj_y = geom->object_y_mm; T.mag = geom->magnification; T.aim = geom->aim_mm; T.stop_r = stop_r;
     if (e == cudaSuccess) e = vamrt::launch_raytable(T, p->tabA, p->tabB, p->tabJ, d_cnt, s);
     unsigned long long cnt[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s);

@@ -33,6 +33,11 @@ class VamrtError(RuntimeError):
         self.status = status
 
 
+class Surface(ctypes.Structure):
+    _fields_ = [("y_mm", ctypes.c_double), ("radius_mm", ctypes.c_double), ("n_after", ctypes.c_double),
+                ("clear_mm", ctypes.c_double), ("is_stop", ctypes.c_int32)]
+
+
 class Geometry(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
@@ -46,6 +51,8 @@ class Geometry(ctypes.Structure):
         ("mu_per_mm", ctypes.c_double),
         ("n_angles", ctypes.c_int32), ("angles_rad", _dp),
         ("step_vox", ctypes.c_double),
+        ("n_surfaces", ctypes.c_int32), ("surfaces", ctypes.POINTER(Surface)),
+        ("object_y_mm", ctypes.c_double), ("magnification", ctypes.c_double), ("aim_mm", ctypes.c_double),
     ]
 
 
@@ -159,6 +166,7 @@ class GeometrySpec:
     n_angles: int
     angles_rad: Optional[np.ndarray] = None
     step_vox: float = 0.5
+    lens: object = None          # inputs.LensTrain or None (ideal pupil)
 
     @classmethod
     def from_workload(cls, w, pupil_xy, angles_rad=None) -> "GeometrySpec":
@@ -169,16 +177,26 @@ class GeometrySpec:
                    n_glass=w.n_glass, n_resin=w.n_resin, mu_per_mm=w.mu_per_mm,
                    n_angles=w.n_angles if angles_rad is None else len(angles_rad),
                    angles_rad=None if angles_rad is None else np.asarray(angles_rad, dtype=np.float64),
-                   step_vox=w.step_vox)
+                   step_vox=w.step_vox, lens=getattr(w, "lens", None))
 
 
 def _to_struct(spec: GeometrySpec):
     keep = []
     g = Geometry()
     for name, _ in Geometry._fields_:
-        if name in ("pupil_xy", "angles_rad", "rays_per_pixel"):
+        if name in ("pupil_xy", "angles_rad", "rays_per_pixel", "n_surfaces", "surfaces", "object_y_mm",
+                    "magnification", "aim_mm"):
             continue
         setattr(g, name, getattr(spec, name))
+    if spec.lens is not None:
+        surfs = (Surface * len(spec.lens.surfaces))(
+            *[Surface(sf.y_mm, sf.radius_mm, sf.n_after, sf.clear_mm, 1 if sf.stop else 0) for sf in spec.lens.surfaces])
+        keep.append(surfs)
+        g.n_surfaces = len(spec.lens.surfaces)
+        g.surfaces = ctypes.cast(surfs, ctypes.POINTER(Surface))
+        g.object_y_mm = spec.lens.object_y_mm
+        g.magnification = spec.lens.magnification
+        g.aim_mm = spec.lens.aim_mm
     pupil = np.ascontiguousarray(spec.pupil_xy, dtype=np.float64).reshape(-1, 2)
     keep.append(pupil)
     g.rays_per_pixel = pupil.shape[0]

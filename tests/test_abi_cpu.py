@@ -76,6 +76,37 @@ def test_make_projector_rejects_bad_geometry(L, field, value, msg):
     assert msg in str(ei.value)
 
 
+def _lens(**changes):
+    from dataclasses import replace
+    from paper_2211_03516_gb300 import inputs as I
+    L0 = I.telecentric_relay()
+    surfs = list(L0.surfaces)
+    for i, kw in changes.pop("surf", {}).items():
+        surfs[i] = replace(surfs[i], **kw)
+    return replace(L0, surfaces=tuple(surfs), **changes)
+
+
+@pytest.mark.parametrize("lens,msg", [
+    (dict(surf={1: dict(y_mm=-230.0)}), "increasing"),
+    (dict(surf={2: dict(stop=False)}), "exactly one stop"),
+    (dict(surf={2: dict(radius_mm=100.0)}), "stop must be a plane"),
+    (dict(surf={0: dict(clear_mm=0.0)}), "clear_mm"),
+    (dict(surf={4: dict(n_after=1.5)}), "outside medium"),
+    (dict(object_y_mm=-100.0), "before the first surface"),
+    (dict(magnification=0.0), "magnification"),
+    (dict(aim_mm=-1.0), "aim_mm"),
+])
+def test_make_projector_rejects_bad_lens_train(L, lens, msg):
+    """Lens-train geometry is checked on the host before anything runs on a device."""
+    from paper_2211_03516_gb300 import vamrt
+    spec = _spec()
+    spec.lens = _lens(**lens)
+    with pytest.raises(vamrt.VamrtError) as ei:
+        vamrt.vamrt_make_projector(spec)
+    assert ei.value.status == vamrt.VAMRT_EINVAL
+    assert msg in str(ei.value)
+
+
 def test_make_projector_rejects_pupil_outside_disk(L):
     from paper_2211_03516_gb300 import vamrt
     spec = _spec()

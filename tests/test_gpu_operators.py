@@ -49,6 +49,9 @@ MID_CROP = I.MID.scaled(nx=73, ny=72, nz=41, voxel_mm=0.36, nu=71, nv=45, pixel_
 REFRACT_SMALL = I.TINY.scaled(nx=33, ny=34, nz=23, voxel_mm=0.4, nu=37, nv=23, pixel_u_mm=0.38,
                               pixel_v_mm=0.41, n_angles=10, f_number=3.5, pupil_pattern="sunflower",
                               rays_per_pixel=4, pupil_mm=60.0)
+# The same grid behind the telecentric 4f relay of Sec. 2.6.2 (16 mm iris, 13 hexagonal
+# rays per pixel): aberrated, partly vignetted lens-train rays.
+LENS_SMALL = REFRACT_SMALL.scaled(lens=I.telecentric_relay(), pupil_pattern="hex13", rays_per_pixel=13)
 
 
 def _oracle_table(w, pupil):
@@ -76,7 +79,7 @@ def _oracle_table(w, pupil):
 
 
 @pytest.mark.parametrize("w", [REFRACT_SMALL, REFRACT_SMALL.scaled(pupil_mm=math.inf, f_number=5.0),
-                               I.TINY], ids=["nontelecentric", "telecentric", "tiny"])
+                               I.TINY, LENS_SMALL], ids=["nontelecentric", "telecentric", "tiny", "lens_train"])
 def test_ray_table_matches_oracle_trace(vamrt, w):
     pupil = I.workload_pupil(w)
     P = vamrt.Projector.from_workload(w, pupil)
@@ -90,7 +93,8 @@ def test_ray_table_matches_oracle_trace(vamrt, w):
         (J[:, 1] == J[:, 0]) & (B[:, 3] > 0)))
 
 
-@pytest.mark.parametrize("w", [I.TINY, REFRACT_SMALL, MID_CROP], ids=["tiny", "refract_small", "mid_crop"])
+@pytest.mark.parametrize("w", [I.TINY, REFRACT_SMALL, MID_CROP, LENS_SMALL],
+                         ids=["tiny", "refract_small", "mid_crop", "lens_train"])
 def test_adjoint_and_dose_parity(vamrt, w):
     pupil = I.workload_pupil(w)
     P = vamrt.Projector.from_workload(w, pupil)
