@@ -460,6 +460,8 @@ def run_gpu(args, rank, world):
         if not args.no_fins:
             from paper_2211_03516_gb300 import fins as FN
             ttt["fins"] = [FN.fins_experiment(n, beta=args.ttt_beta, mu=args.ttt_mu) for n in (9, 18)]
+            from paper_2211_03516_gb300 import etendue as ET
+            ttt["etendue"] = [ET.etendue_experiment(d, beta=args.ttt_beta, mu=args.ttt_mu) for d in (2.5, 16.0)]
         if args.ws_train > 0:
             ttt["warm_start"] = warm_start_time_to_target(args)
 
@@ -522,7 +524,7 @@ def main():
     ap.add_argument("--ttt-beta", type=float, default=4.0,
                     help="model step of the over-relaxed optimiser variant in the time-to-target comparison")
     ap.add_argument("--no-fins", action="store_true",
-                    help="skip the fin-part comparison (Radon method vs ray-traced optimiser, 9 and 18 fins)")
+                    help="skip the fin-part (9 and 18 fins) and etendue (2.5 and 16 mm iris) comparisons")
     ap.add_argument("--ttt-mu", type=float, default=0.5,
                     help="heavy-ball momentum of the over-relaxed optimiser variant")
     ap.add_argument("--ttt-iters", type=int, default=30,

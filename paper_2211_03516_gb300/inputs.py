@@ -277,6 +277,19 @@ def fins_workload(n_fins: int = 9) -> Workload:
                     n_glass=1.47, n_resin=1.50, mu_per_mm=0.03, target=f"fins{n_fins}", osmo_iters=40)
 
 
+def etendue_workload(iris_diameter_mm: float = 16.0, rays: str = "hex13") -> Workload:
+    """The telecentric printer of Sec. 2.6.2 (the parameterised 4f relay of
+    `telecentric_relay` with the given iris; vial OD 8 / ID 6.6 mm) on a 0.05 mm grid
+    (coarser than the paper's 0.0432 mm) 3.2 mm tall, 360 angles.  rays: "hex13" (13
+    rays per pixel, the paper's etendue model) or "chief" (one ray, zero etendue)."""
+    n = 13 if rays == "hex13" else 1
+    return Workload(name=f"telecentric_iris{iris_diameter_mm:g}_{rays}", nx=136, ny=136, nz=64, voxel_mm=0.05,
+                    nu=136, nv=64, pixel_u_mm=0.05, pixel_v_mm=0.05, n_angles=360, pupil_mm=INF, f_number=INF,
+                    pupil_pattern=rays, rays_per_pixel=n, r_inner_mm=3.3, wall_mm=0.7, n_outside=1.0,
+                    n_glass=1.47, n_resin=1.50, mu_per_mm=0.05, target="csg_shells", osmo_iters=20,
+                    lens=telecentric_relay(iris_diameter_mm=iris_diameter_mm))
+
+
 def radon_workload(w: Workload) -> Workload:
     """The printer the Radon method assumes (Sec. 2.3): parallel chief rays (telecentric,
     zero etendue), no refraction (all indices 1) and no attenuation, on w's grid, pixels
