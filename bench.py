@@ -461,7 +461,8 @@ def run_gpu(args, rank, world):
             from paper_2211_03516_gb300 import fins as FN
             ttt["fins"] = [FN.fins_experiment(n, beta=args.ttt_beta, mu=args.ttt_mu) for n in (9, 18)]
             from paper_2211_03516_gb300 import etendue as ET
-            ttt["etendue"] = [ET.etendue_experiment(d, beta=args.ttt_beta, mu=args.ttt_mu) for d in (2.5, 16.0)]
+            ttt["etendue"] = [ET.etendue_experiment(d, beta=args.ttt_beta, mu=args.ttt_mu, kind=k)
+                              for k in ("csg", "csg_shells") for d in (2.5, 16.0)]
         if args.ws_train > 0:
             ttt["warm_start"] = warm_start_time_to_target(args)
 

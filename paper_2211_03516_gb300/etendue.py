@@ -19,14 +19,14 @@ def _optimise(P, f, iters, beta, mu):
 
 
 def etendue_experiment(iris_diameter_mm: float, seed: int = 0, iters: int = 20, beta: float = 4.0,
-                       mu: float = 0.5) -> dict:
+                       mu: float = 0.5, kind: str = "csg") -> dict:
     w13 = I.etendue_workload(iris_diameter_mm, "hex13")
     w1 = I.etendue_workload(iris_diameter_mm, "chief")
     P13 = V.Projector.from_workload(w13, I.workload_pupil(w13))
     P1 = V.Projector.from_workload(w1, I.workload_pupil(w1))
     try:
-        f = torch.from_numpy(I.make_target(w13, seed=seed)).to("cuda")
-        out = {"iris_mm": iris_diameter_mm, "workload": w13.name, "seed": seed,
+        f = torch.from_numpy(I.make_target(w13, kind=kind, seed=seed)).to("cuda")
+        out = {"iris_mm": iris_diameter_mm, "workload": w13.name, "target": kind, "seed": seed,
                "optimiser": f"object space, step {beta:g}, momentum {mu:g}, {iters} iterations",
                "rays_in_resin_13": P13.info()["rays_in_resin"], "rays_total_13": P13.info()["n_rays"]}
         for name, P in (("chief_ray_model", P1), ("thirteen_ray_model", P13)):
