@@ -225,6 +225,43 @@ struct SmemSrc {
     __device__ __forceinline__ float operator()(int i) const { return p[i]; }
 };
 
+// Packed FP32 pairs (sm_100 family): one instruction performs two independent
+// round-to-nearest operations, so the results are bit-identical to the scalar forms while
+// the issue-bound sample loops spend fewer instructions.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ void upk2i(f32x2 v, int &lo, int &hi) { asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v)); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Beer-Lambert factor of samples jl, jl+1, ...: exact exp2 at the start of each run,
 // then one multiply per sample (runs are one chunk long, ~30 samples, so the product
 // drifts by a few 1e-7 at most).
@@ -247,12 +284,13 @@ __device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, in
         const float v010 = src(b + sx), v110 = src(b + sx + 1);
         const float v001 = src(b + sxy), v101 = src(b + sxy + 1);
         const float v011 = src(b + sxy + sx), v111 = src(b + sxy + sx + 1);
-        const float x00 = fmaf(c.fx, v100 - v000, v000);
-        const float x10 = fmaf(c.fx, v110 - v010, v010);
-        const float x01 = fmaf(c.fx, v101 - v001, v001);
-        const float x11 = fmaf(c.fx, v111 - v011, v011);
-        const float y0 = fmaf(c.fy, x10 - x00, x00);
-        const float y1 = fmaf(c.fy, x11 - x01, x01);
+        // x-lerps of the z = 0 and z = 1 corners in pairs, then the y-lerps, then z
+        const f32x2 fx2 = pk2(c.fx, c.fx);
+        const f32x2 a0 = pk2(v000, v001), a1 = pk2(v010, v011);
+        const f32x2 x0 = fma2(fx2, sub2(pk2(v100, v101), a0), a0);   // (x00, x01)
+        const f32x2 x1 = fma2(fx2, sub2(pk2(v110, v111), a1), a1);   // (x10, x11)
+        float y0, y1;
+        upk2(fma2(pk2(c.fy, c.fy), sub2(x1, x0), x0), y0, y1);
         const float val = fmaf(c.fz, y1 - y0, y0);
         acc = fmaf(att, val, acc);
         att *= ratio;
@@ -332,15 +370,27 @@ __device__ __forceinline__ void walk_scatter_box(const OpParams &P, const Ray &R
     for (int j = jl; j < jh; ++j) {
         const Cell c = cell_of(P, qx, qy, qz);
         int *p = box + addr(c);
-        const Shares S = shares(ws * att, c);
-        atomicAdd(p, to_fixed(S.s000, 1.f));
-        atomicAdd(p + 1, to_fixed(S.s100, 1.f));
-        atomicAdd(p + sx, to_fixed(S.s010, 1.f));
-        atomicAdd(p + sx + 1, to_fixed(S.s110, 1.f));
-        atomicAdd(p + sxy, to_fixed(S.s001, 1.f));
-        atomicAdd(p + sxy + 1, to_fixed(S.s101, 1.f));
-        atomicAdd(p + sxy + sx, to_fixed(S.s011, 1.f));
-        atomicAdd(p + sxy + sx + 1, to_fixed(S.s111, 1.f));
+        // the eight shares of shares() in pairs (z = 0, z = 1), converted to fixed point by
+        // the same 1.5 * 2^23 addition
+        const float w = ws * att, wz1 = w * c.fz, wz0 = w - wz1;
+        const f32x2 fx2 = pk2(c.fx, c.fx), magic = pk2(12582912.0f, 12582912.0f);
+        const f32x2 z = pk2(wz0, wz1);
+        const f32x2 w1 = mul2(z, pk2(c.fy, c.fy));         // (w01, w11)
+        const f32x2 w0 = sub2(z, w1);                      // (w00, w10)
+        const f32x2 s1a = mul2(w0, fx2), s1b = mul2(w1, fx2);   // (s100, s101), (s110, s111)
+        int i000, i001, i100, i101, i010, i011, i110, i111;
+        upk2i(add2(sub2(w0, s1a), magic), i000, i001);
+        upk2i(add2(s1a, magic), i100, i101);
+        upk2i(add2(sub2(w1, s1b), magic), i010, i011);
+        upk2i(add2(s1b, magic), i110, i111);
+        atomicAdd(p, i000 - 0x4B400000);
+        atomicAdd(p + 1, i100 - 0x4B400000);
+        atomicAdd(p + sx, i010 - 0x4B400000);
+        atomicAdd(p + sx + 1, i110 - 0x4B400000);
+        atomicAdd(p + sxy, i001 - 0x4B400000);
+        atomicAdd(p + sxy + 1, i101 - 0x4B400000);
+        atomicAdd(p + sxy + sx, i011 - 0x4B400000);
+        atomicAdd(p + sxy + sx + 1, i111 - 0x4B400000);
         att *= ratio;
         qx += R.sx;
         qy += R.sy;
