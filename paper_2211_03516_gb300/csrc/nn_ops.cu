@@ -21,6 +21,8 @@ inline unsigned grid_n(int64_t n)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+inline bool aligned16(const void *p, const void *q) { return (((uintptr_t)p | (uintptr_t)q) & 15) == 0; }
+
 #define GRID_STRIDE(i, n) for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 // fine grid [D][H][W][C] <-> coarse grid [D/2][H/2][W/2][C]
@@ -41,6 +43,132 @@ __global__ void avgpool2_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloa
         }
         out[i] = tobf(0.125f * s);
     }
+}
+
+// ---- 16-byte variants: eight channels per thread (C a multiple of 8, 16-byte aligned
+// pointers), the same per-element arithmetic in the same order as the scalar kernels, so
+// bit-identical results with one vector load / store instead of eight scalar ones ----
+__device__ __forceinline__ void unpack8(const uint4 v, float f[8])
+{
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 t = __bfloat1622float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float f[8])
+{
+    uint4 v;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    return v;
+}
+
+// op 0: average pool (scale 0.125), op 3: sum of 8 (scale 1); G = C / 8 groups
+__global__ void pool8_kernel(const uint4 *__restrict__ in, uint4 *__restrict__ out, int D, int H, int W, int G,
+                             float scale)
+{
+    const int d = D / 2, h = H / 2, w = W / 2;
+    const int64_t n = (int64_t)d * h * w * G;
+    GRID_STRIDE(i, n)
+    {
+        const int g = (int)(i % G);
+        const int64_t q = i / G;
+        const int x = (int)(q % w), y = (int)((q / w) % h), z = (int)(q / ((int64_t)w * h));
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 8; ++k) {
+            const int zz = 2 * z + (k >> 2), yy = 2 * y + ((k >> 1) & 1), xx = 2 * x + (k & 1);
+            float f[8];
+            unpack8(in[(((int64_t)zz * H + yy) * W + xx) * G + g], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += f[e];
+        }
+        if (scale != 1.f) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] = scale * s[e];
+        }
+        out[i] = pack8(s);
+    }
+}
+
+// fine voxel <- scale x its coarse voxel (scale 1: nearest upsample; 1/8: pool backward)
+__global__ void spread8_kernel(const uint4 *__restrict__ coarse, uint4 *__restrict__ fine, int D, int H, int W, int G,
+                               float scale)
+{
+    const int64_t n = (int64_t)D * H * W * G;
+    const int h = H / 2, w = W / 2;
+    GRID_STRIDE(i, n)
+    {
+        const int g = (int)(i % G);
+        const int64_t q = i / G;
+        const int x = (int)(q % W), y = (int)((q / W) % H), z = (int)(q / ((int64_t)W * H));
+        const uint4 v = coarse[(((int64_t)(z / 2) * h + y / 2) * w + x / 2) * G + g];
+        if (scale == 1.f) {
+            fine[i] = v;
+        } else {
+            float f[8];
+            unpack8(v, f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) f[e] = scale * f[e];
+            fine[i] = pack8(f);
+        }
+    }
+}
+
+__global__ void concat8_kernel(const uint4 *__restrict__ a, int ga, const uint4 *__restrict__ b, int gb,
+                               uint4 *__restrict__ out, int64_t npos, int backward)
+{
+    const int G = ga + gb;
+    GRID_STRIDE(i, npos * G)
+    {
+        const int g = (int)(i % G);
+        const int64_t p = i / G;
+        if (!backward)
+            out[i] = g < ga ? a[p * ga + g] : b[p * gb + (g - ga)];
+        else if (g < ga)
+            const_cast<uint4 *>(a)[p * ga + g] = out[i];
+        else
+            const_cast<uint4 *>(b)[p * gb + (g - ga)] = out[i];
+    }
+}
+
+__global__ void relu_bwd8_kernel(const uint4 *__restrict__ y, uint4 *__restrict__ dy, int64_t n8)
+{
+    GRID_STRIDE(i, n8)
+    {
+        float fy[8], fd[8];
+        unpack8(y[i], fy);
+        const uint4 d = dy[i];
+        unpack8(d, fd);
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (!(fy[e] > 0.f)) { fd[e] = 0.f; any = true; }
+        if (any) dy[i] = pack8(fd);
+    }
+}
+
+// db[c] += sum_p dy[p][c], 256 / G positions per block step (G = C / 8 divides 256)
+__global__ void bias_grad8_kernel(const uint4 *__restrict__ dy, float *__restrict__ db, int64_t npos, int G)
+{
+    __shared__ float acc[256];
+    const int C = 8 * G, per = kT / G, g = threadIdx.x % G, p0 = threadIdx.x / G;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) acc[c] = 0.f;
+    __syncthreads();
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t p = (int64_t)blockIdx.x * per + p0; p < npos; p += (int64_t)gridDim.x * per) {
+        float f[8];
+        unpack8(dy[p * G + g], f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s[e] += f[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) atomicAdd(&acc[8 * g + e], s[e]);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], acc[c]);
 }
 
 // mode 0: average-pool backward (each fine voxel gets coarse / 8)
@@ -238,6 +366,20 @@ cudaError_t nn_resample(int op, const void *in, void *out, int D, int H, int W, 
     const __nv_bfloat16 *a = (const __nv_bfloat16 *)in;
     __nv_bfloat16 *b = (__nv_bfloat16 *)out;
     const int64_t fine = (int64_t)D * H * W * C, coarse = fine / 8;
+    if (C % 8 == 0 && aligned16(in, out)) {
+        const uint4 *a8 = (const uint4 *)in;
+        uint4 *b8 = (uint4 *)out;
+        const int G = C / 8;
+        switch (op) {
+        case 0: pool8_kernel<<<grid_n(coarse / 8), kT, 0, s>>>(a8, b8, D, H, W, G, 0.125f); break;
+        case 1: spread8_kernel<<<grid_n(fine / 8), kT, 0, s>>>(a8, b8, D, H, W, G, 0.125f); break;
+        case 2: spread8_kernel<<<grid_n(fine / 8), kT, 0, s>>>(a8, b8, D, H, W, G, 1.0f); break;
+        case 3: pool8_kernel<<<grid_n(coarse / 8), kT, 0, s>>>(a8, b8, D, H, W, G, 1.0f); break;
+        default: return cudaErrorInvalidValue;
+        }
+        count_launches(1);
+        return cudaGetLastError();
+    }
     switch (op) {
     case 0: avgpool2_kernel<<<grid_n(coarse), kT, 0, s>>>(a, b, D, H, W, C); break;
     case 1: spread2_kernel<<<grid_n(fine), kT, 0, s>>>(a, b, D, H, W, C, 0.125f); break;
@@ -252,6 +394,12 @@ cudaError_t nn_resample(int op, const void *in, void *out, int D, int H, int W, 
 cudaError_t nn_concat(const void *a, int ca, const void *b, int cb, void *out, int64_t npos, int backward,
                       cudaStream_t s)
 {
+    if (ca % 8 == 0 && cb % 8 == 0 && aligned16(a, b) && aligned16(out, out)) {
+        concat8_kernel<<<grid_n(npos * (ca + cb) / 8), kT, 0, s>>>((const uint4 *)a, ca / 8, (const uint4 *)b, cb / 8,
+                                                                   (uint4 *)out, npos, backward);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     if (!backward)
         concat_kernel<<<grid_n(npos * (ca + cb)), kT, 0, s>>>((const __nv_bfloat16 *)a, ca, (const __nv_bfloat16 *)b,
                                                               cb, (__nv_bfloat16 *)out, npos);
@@ -264,14 +412,20 @@ cudaError_t nn_concat(const void *a, int ca, const void *b, int cb, void *out, i
 
 cudaError_t nn_relu_bwd(const void *y, void *dy, int64_t n, cudaStream_t s)
 {
-    relu_bwd_kernel<<<grid_n(n), kT, 0, s>>>((const __nv_bfloat16 *)y, (__nv_bfloat16 *)dy, n);
+    if (n % 8 == 0 && aligned16(y, dy))
+        relu_bwd8_kernel<<<grid_n(n / 8), kT, 0, s>>>((const uint4 *)y, (uint4 *)dy, n / 8);
+    else
+        relu_bwd_kernel<<<grid_n(n), kT, 0, s>>>((const __nv_bfloat16 *)y, (__nv_bfloat16 *)dy, n);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t nn_bias_grad(const void *dy, float *db, int64_t npos, int C, cudaStream_t s)
 {
-    bias_grad_kernel<<<grid_n(npos * C), kT, 0, s>>>((const __nv_bfloat16 *)dy, db, npos, C);
+    if (C % 8 == 0 && kT % (C / 8) == 0 && aligned16(dy, dy))
+        bias_grad8_kernel<<<grid_n(npos * C / 8), kT, 0, s>>>((const uint4 *)dy, db, npos, C / 8);
+    else
+        bias_grad_kernel<<<grid_n(npos * C), kT, 0, s>>>((const __nv_bfloat16 *)dy, db, npos, C);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -107,3 +107,58 @@ def test_unet_forward_backward_matches_fp64_reference(U):
         gw, gb = g_ref[n]
         assert rel_l2(L.gW.cpu().numpy(), gw) <= 5e-2, n
         assert rel_l2(L.gb.cpu().numpy(), gb) <= 5e-2, n
+
+
+def _offset_copy(x):
+    """The same values at a 2-byte offset (not 16-byte aligned): the ops then take their
+    one-element-per-thread kernels instead of the 16-byte ones."""
+    buf = torch.empty(x.numel() + 8, device=x.device, dtype=x.dtype)
+    v = buf[1:1 + x.numel()].view(x.shape)
+    v.copy_(x)
+    return v
+
+
+def test_glue_ops_vector_and_scalar_kernels_agree_bitwise(U):
+    """Pooling, upsampling, their backwards, concatenation, split and the ReLU backward:
+    the 16-byte kernels against the scalar kernels (bit for bit) and against numpy."""
+    nn = U._nn()
+    s = torch.cuda.current_stream().cuda_stream
+    rng = np.random.default_rng(5)
+    D, H, W, C = 6, 10, 24, 16
+    x = torch.from_numpy(rng.standard_normal((D, H, W, C)).astype(np.float32)).to(torch.bfloat16).to(DEV)
+    c = torch.from_numpy(rng.standard_normal((D // 2, H // 2, W // 2, C)).astype(np.float32)).to(torch.bfloat16).to(DEV)
+    for op, src, out_shape in ((0, x, c.shape), (1, c, x.shape), (2, c, x.shape), (3, x, c.shape)):
+        y_vec = torch.empty(out_shape, device=DEV, dtype=torch.bfloat16)
+        y_sca = _offset_copy(torch.zeros(out_shape, device=DEV, dtype=torch.bfloat16))
+        src_sca = _offset_copy(src)
+        assert nn.vamrt_nn_resample(op, src.data_ptr(), y_vec.data_ptr(), D, H, W, C, s) == 0
+        assert nn.vamrt_nn_resample(op, src_sca.data_ptr(), y_sca.data_ptr(), D, H, W, C, s) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(y_vec, y_sca), op
+    xf = x.float().cpu().numpy()
+    pooled = xf.reshape(D // 2, 2, H // 2, 2, W // 2, 2, C).mean(axis=(1, 3, 5))
+    np.testing.assert_allclose(U.avgpool2(x).float().cpu().numpy(), pooled, rtol=1e-2, atol=1e-2)
+    up = U.upsample2(c).float().cpu().numpy()
+    np.testing.assert_array_equal(up, np.repeat(np.repeat(np.repeat(c.float().cpu().numpy(), 2, 0), 2, 1), 2, 2))
+    b = torch.from_numpy(rng.standard_normal((D, H, W, 32)).astype(np.float32)).to(torch.bfloat16).to(DEV)
+    ab = U.concat(x, b)
+    ab_sca = _offset_copy(torch.zeros_like(ab))
+    xs, bs = _offset_copy(x), _offset_copy(b)
+    assert nn.vamrt_nn_concat(xs.data_ptr(), C, bs.data_ptr(), 32, ab_sca.data_ptr(), D * H * W, 0, s) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(ab, ab_sca) and torch.equal(ab, torch.cat([x, b], dim=-1))
+    a2, b2 = U.split(ab, C)
+    assert torch.equal(a2, x) and torch.equal(b2, b)
+    dy = torch.from_numpy(rng.standard_normal((D, H, W, C)).astype(np.float32)).to(torch.bfloat16).to(DEV)
+    dy_vec, dy_sca = dy.clone(), _offset_copy(dy)
+    x_sca = _offset_copy(x)
+    assert nn.vamrt_nn_relu_backward(x.data_ptr(), dy_vec.data_ptr(), dy.numel(), s) == 0
+    assert nn.vamrt_nn_relu_backward(x_sca.data_ptr(), dy_sca.data_ptr(), dy.numel(), s) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(dy_vec, dy_sca) and torch.equal(dy_vec, torch.where(x > 0, dy, torch.zeros_like(dy)))
+    for ch in (16, 48, 128):
+        g = torch.from_numpy(rng.standard_normal((D * H * W, ch)).astype(np.float32)).to(torch.bfloat16).to(DEV)
+        db = torch.zeros(ch, device=DEV)
+        assert nn.vamrt_nn_bias_grad(g.data_ptr(), db.data_ptr(), D * H * W, ch, s) == 0
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(db.cpu().numpy(), g.double().sum(0).cpu().numpy(), rtol=1e-4, atol=1e-3)
