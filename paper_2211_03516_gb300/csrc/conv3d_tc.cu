@@ -164,165 +164,7 @@ __global__ void __launch_bounds__(kConvThreads)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// Weight gradient of the same convolution on the tensor cores:
-//   dW[co][t][ci] = sum_p dY[p][co] X[p + off(t)][ci]
-// as C[m][n] = sum_k A[m][k] B[n][k] with m = t Cin + ci (M tiles of 128 rows), n = co,
-// k = output positions in chunks of 16 consecutive x (W % 16 == 0, so a chunk stays in one
-// row of the volume).  The K range is split across blocks (grid.y); each block adds its
-// FP32 partial into dW with atomics.  Thread r gathers row r of A (16 positions of one
-// (tap, channel), coalesced across the warp's consecutive channels) and rows of B.
-template <int TAPS>
-__global__ void __launch_bounds__(kConvThreads)
-    conv3d_wgrad_tc_kernel(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ dY,
-                           float *__restrict__ dW, int D, int H, int W, int Cin, int Cout, int chunks_per_block,
-                           int *__restrict__ err)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + 2 * kStageA;
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t s_tmem;
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t P = (int64_t)D * H * W;
-    const int Mtot = TAPS * Cin;
-    const int m = blockIdx.x * kM + tid;          // this thread's A row
-    const int64_t nchunk_all = P / 16;
-    const int64_t c_begin = (int64_t)blockIdx.y * chunks_per_block;
-    int64_t c_end = c_begin + chunks_per_block;
-    if (c_end > nchunk_all) c_end = nchunk_all;
-    const int nchunks = (int)(c_end > c_begin ? c_end - c_begin : 0);
-    int ncols = 32;
-    while (ncols < Cout) ncols <<= 1;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(ncols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = s_tmem;
-
-    int t = 0, ci = 0, dz = 0, dy = 0, dx = 0;
-    const bool mvalid = m < Mtot;
-    if (mvalid) {
-        t = m / Cin;
-        ci = m - t * Cin;
-        if (TAPS == 27) { dz = t / 9 - 1; dy = (t / 3) % 3 - 1; dx = t % 3 - 1; }
-    }
-    const uint32_t idesc = instr_desc(Cout);
-    bool ok = true;
-
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c & 1;
-        if (c >= 2) {
-            const bool mine = mbar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1);
-            if (!__syncthreads_and(mine)) { ok = false; break; }
-        }
-        const int64_t pc = (c_begin + c) * 16;                  // first position of the chunk
-        const int x0 = (int)(pc % W);
-        const int y = (int)((pc / W) % H);
-        const int z = (int)(pc / ((int64_t)W * H));
-        // A row m: X[(z+dz, y+dy, x0+k+dx)][ci], k = 0..15
-        unsigned short a[16];
-        const int zz = z + dz, yy = y + dy;
-        const bool rowok = mvalid && zz >= 0 && zz < D && yy >= 0 && yy < H;
-        const unsigned short *xs = reinterpret_cast<const unsigned short *>(X);
-        const int64_t rowbase = (((int64_t)zz * H + yy) * W) * Cin + ci;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int xx = x0 + k + dx;
-            a[k] = (rowok && xx >= 0 && xx < W) ? __ldg(xs + rowbase + (int64_t)xx * Cin) : (unsigned short)0;
-        }
-        unsigned char *A = sA + s * kStageA;
-        uint4 lo, hi;
-        lo.x = a[0] | (a[1] << 16); lo.y = a[2] | (a[3] << 16); lo.z = a[4] | (a[5] << 16); lo.w = a[6] | (a[7] << 16);
-        hi.x = a[8] | (a[9] << 16); hi.y = a[10] | (a[11] << 16); hi.z = a[12] | (a[13] << 16); hi.w = a[14] | (a[15] << 16);
-        *reinterpret_cast<uint4 *>(A + core_off(tid, 0)) = lo;
-        *reinterpret_cast<uint4 *>(A + core_off(tid, 1)) = hi;
-        // B rows co: dY[pc + k][co]
-        unsigned char *Bs = sB + s * kStageB;
-        const unsigned short *ds = reinterpret_cast<const unsigned short *>(dY);
-        for (int co = tid; co < Cout; co += kConvThreads) {
-            unsigned short b[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) b[k] = __ldg(ds + (pc + k) * Cout + co);
-            lo.x = b[0] | (b[1] << 16); lo.y = b[2] | (b[3] << 16); lo.z = b[4] | (b[5] << 16); lo.w = b[6] | (b[7] << 16);
-            hi.x = b[8] | (b[9] << 16); hi.y = b[10] | (b[11] << 16); hi.z = b[12] | (b[13] << 16); hi.w = b[14] | (b[15] << 16);
-            *reinterpret_cast<uint4 *>(Bs + core_off(co, 0)) = lo;
-            *reinterpret_cast<uint4 *>(Bs + core_off(co, 1)) = hi;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            mma_bf16(tmem, smem_desc(smem_u32(A)), smem_desc(smem_u32(Bs)), idesc, c > 0 ? 1u : 0u);
-            mma_commit(smem_u32(&bars[s]));
-        }
-    }
-    if (ok && nchunks > 0) {
-        const int c = nchunks - 1;
-        const bool mine = mbar_wait(smem_u32(&bars[c & 1]), (c >> 1) & 1);
-        ok = __syncthreads_and(mine);
-    }
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            for (int s2 = 0; s2 < 2; ++s2) (void)mbar_wait(smem_u32(&bars[s2]), 0);
-        }
-    } else if (nchunks > 0) {
-        tc_fence_after();
-        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int n0 = 0; n0 < Cout; n0 += 16) {
-            float v[16];
-            tmem_ld16(row_addr + (uint32_t)n0, v);
-            if (mvalid) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) atomicAdd(dW + (int64_t)(n0 + i) * Mtot + m, v[i]);
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
-}
-
 }  // namespace
-
-cudaError_t launch_conv3d_wgrad_tc(const void *X, const void *dY, float *dW, int D, int H, int W, int Cin, int Cout,
-                                   int taps, int *err, cudaStream_t s)
-{
-    const int64_t P = (int64_t)D * H * W;
-    const int64_t nchunk = P / 16;
-    const int mt = (taps * Cin + kM - 1) / kM;
-    int per = 64;                                  // chunks (1024 positions) per block
-    while ((nchunk + per - 1) / per > 65535) per *= 2;
-    const unsigned gy = (unsigned)((nchunk + per - 1) / per);
-    const size_t smem = 2 * kStageA + 2 * kStageB;
-    const __nv_bfloat16 *x = (const __nv_bfloat16 *)X, *dy = (const __nv_bfloat16 *)dY;
-    cudaError_t e;
-    if (taps == 27) {
-        e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            conv3d_wgrad_tc_kernel<27><<<dim3(mt, gy), kConvThreads, smem, s>>>(x, dy, dW, D, H, W, Cin, Cout, per, err);
-    } else {
-        e = cudaFuncSetAttribute(conv3d_wgrad_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            conv3d_wgrad_tc_kernel<1><<<dim3(mt, gy), kConvThreads, smem, s>>>(x, dy, dW, D, H, W, Cin, Cout, per, err);
-    }
-    if (e != cudaSuccess) return e;
-    count_launches(1);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s)

@@ -61,10 +61,19 @@ def test_conv3d_matches_direct_convolution(U, shape, cin, cout, taps):
     assert rel_l2(yr.float().cpu().numpy(), np.maximum(ref, 0)) <= 4e-3
 
 
-@pytest.mark.parametrize("cin,cout,taps", [(16, 16, 27), (48, 16, 27), (16, 32, 27), (16, 16, 1)])
-def test_conv3d_weight_gradient_matches_direct_sum(U, cin, cout, taps):
-    rng = np.random.default_rng(cin * 7 + cout)
-    D, H, W = 3, 5, 32
+@pytest.mark.parametrize("shape,cin,cout,taps", [
+    ((3, 5, 32), 16, 16, 27), ((3, 5, 32), 48, 16, 27), ((3, 5, 32), 16, 32, 27), ((3, 5, 32), 16, 16, 1),
+    ((2, 3, 16), 16, 16, 27),        # 32-position stages span two rows
+    ((1, 1, 16), 32, 48, 27),        # a single partial stage
+    ((2, 2, 48), 192, 64, 27),       # 21 groups of two M tiles
+    ((2, 3, 16), 128, 256, 27),      # N = 256
+    ((4, 3, 32), 96, 32, 27),
+    ((2, 2, 16), 1024, 16, 1),       # one block per SM
+    ((24, 32, 64), 16, 16, 27),      # hundreds of blocks, several stages each
+])
+def test_conv3d_weight_gradient_matches_direct_sum(U, shape, cin, cout, taps):
+    rng = np.random.default_rng(cin * 7 + cout + shape[2])
+    D, H, W = shape
     x = torch.from_numpy(rng.standard_normal((D, H, W, cin)).astype(np.float32)).to(torch.bfloat16)
     dy = torch.from_numpy(rng.standard_normal((D, H, W, cout)).astype(np.float32)).to(torch.bfloat16)
     xs, dys = x.double().numpy(), dy.double().numpy()
