@@ -43,6 +43,7 @@ constexpr int kTileBytes = 128 * kKS * 2;  // one M tile of A per stage: 8 KB
 constexpr int kRowGroupBytes = kKS * 16;   // 8 rows x 32 positions: 512 B
 constexpr int kMaxTpg = 8;
 constexpr int kMaxItems = kMaxTpg * 16 + 256 / 8;
+constexpr int kBatch = 8;                  // strips a warp transposes per batch
 
 struct WgradArgs {
     const __nv_bfloat16 *X, *dY;
@@ -222,20 +223,30 @@ __global__ void __launch_bounds__(kWThreads, 2) conv3d_wgrad_kernel(const WgradA
         const uint32_t ry = rawY + buf * rawY_bytes + lane * a.ystride;
         const uint32_t ca = canonA + buf * canonA_bytes + lane * 16;
         const uint32_t cb = canonB + buf * canonB_bytes + lane * 16;
-        for (int it = warp; it < nitems; it += kWThreads / 32) {
-            const int4 e = items[it];
-            uint32_t src, dst;
-            if (e.z & 256) {
-                src = ry + e.x;
-                dst = cb + e.y;
-            } else {
-                const unsigned v = (zok >> (e.z & 3)) & (yok >> ((e.z >> 2) & 3)) & (xok >> ((e.z >> 4) & 3)) & 1u;
-                src = v ? rx + e.x : zero_addr;
-                dst = ca + e.y;
+        // kBatch items per warp at a time: every load issued before the first store
+        for (int it0 = warp; it0 < nitems; it0 += kBatch * (kWThreads / 32)) {
+            uint32_t r[kBatch][4], dst[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int it = it0 + u * (kWThreads / 32);
+                if (it < nitems) {
+                    const int4 e = items[it];
+                    uint32_t src;
+                    if (e.z & 256) {
+                        src = ry + e.x;
+                        dst[u] = cb + e.y;
+                    } else {
+                        const unsigned v =
+                            (zok >> (e.z & 3)) & (yok >> ((e.z >> 2) & 3)) & (xok >> ((e.z >> 4) & 3)) & 1u;
+                        src = v ? rx + e.x : zero_addr;
+                        dst[u] = ca + e.y;
+                    }
+                    ldsm_x4_trans(src, r[u][0], r[u][1], r[u][2], r[u][3]);
+                }
             }
-            uint32_t r0, r1, r2, r3;
-            ldsm_x4_trans(src, r0, r1, r2, r3);
-            stsm_x4(dst, r0, r1, r2, r3);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (it0 + u * (kWThreads / 32) < nitems) stsm_x4(dst[u], r[u][0], r[u][1], r[u][2], r[u][3]);
         }
         fence_proxy_async();
         __syncthreads();
@@ -346,8 +357,9 @@ cudaError_t launch_conv3d_wgrad_tc(const void *X, const void *dY, float *dW, int
     int ncols = 32;
     while (ncols < a.tpg * Cout) ncols <<= 1;
     a.ncols = ncols;
+    // at most one wave: a block more than the resident slots would double the time
     const int target = per_sm * sms;
-    int nsplit = std::max(1, (target + ngroups - 1) / ngroups);
+    int nsplit = std::max(1, target / ngroups);
     a.spb = (a.nstage + nsplit - 1) / nsplit;
     nsplit = (a.nstage + a.spb - 1) / a.spb;
     cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
