@@ -65,12 +65,12 @@ def test_conv3d_matches_direct_convolution(U, shape, cin, cout, taps):
     ((3, 5, 32), 16, 16, 27), ((3, 5, 32), 48, 16, 27), ((3, 5, 32), 16, 32, 27), ((3, 5, 32), 16, 16, 1),
     ((2, 3, 16), 16, 16, 27),        # 32-position stages span two rows
     ((1, 1, 16), 32, 48, 27),        # a single partial stage
-    ((2, 2, 48), 192, 64, 27),       # block-synchronous kernel: 21 groups of two M tiles
-    ((2, 3, 16), 128, 256, 27),      # block-synchronous kernel, N = 256
-    ((5, 4, 64), 16, 16, 27),        # warp-specialised kernel, a stage = one row of W = 64
+    ((2, 2, 48), 192, 64, 27),       # 21 groups of two M tiles
+    ((2, 3, 16), 128, 256, 27),      # N = 256
+    ((5, 4, 64), 16, 16, 27),        # W = 64: half a row per stage
     ((4, 3, 32), 96, 32, 27),
-    ((2, 2, 16), 1024, 16, 1),       # block-synchronous kernel, one block per SM
-    ((1, 2, 16), 512, 16, 27),       # block-synchronous kernel, 27 taps
+    ((2, 2, 16), 1024, 16, 1),       # one block per SM
+    ((1, 2, 16), 512, 16, 27),       # one M tile per group, wide raw rows
     ((24, 32, 64), 16, 16, 27),      # hundreds of blocks, several stages each
 ])
 def test_conv3d_weight_gradient_matches_direct_sum(U, shape, cin, cout, taps):
