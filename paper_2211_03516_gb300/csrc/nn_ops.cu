@@ -2,6 +2,8 @@
 // around its tensor-core convolutions).  Activations are channels-last BF16
 // [D][H][W][C]; master weights and optimiser moments are FP32.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "internal.cuh"
@@ -151,7 +153,9 @@ __global__ void relu_bwd8_kernel(const uint4 *__restrict__ y, uint4 *__restrict_
     }
 }
 
-// db[c] += sum_p dy[p][c], 256 / G positions per block step (G = C / 8 divides 256)
+// db[c] += sum_p dy[p][c], 256 / G positions per block step (G = C / 8 divides 256).  A
+// few blocks per SM, each streaming many positions with four loads in flight per thread:
+// every block ends in C same-address global atomics, which serialise in L2.
 __global__ void bias_grad8_kernel(const uint4 *__restrict__ dy, float *__restrict__ db, int64_t npos, int G)
 {
     __shared__ float acc[256];
@@ -159,7 +163,21 @@ __global__ void bias_grad8_kernel(const uint4 *__restrict__ dy, float *__restric
     for (int c = threadIdx.x; c < C; c += blockDim.x) acc[c] = 0.f;
     __syncthreads();
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int64_t p = (int64_t)blockIdx.x * per + p0; p < npos; p += (int64_t)gridDim.x * per) {
+    const int64_t step = (int64_t)gridDim.x * per;
+    int64_t p = (int64_t)blockIdx.x * per + p0;
+    for (; p + 3 * step < npos; p += 4 * step) {
+        uint4 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = dy[(p + k * step) * G + g];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float f[8];
+            unpack8(q[k], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += f[e];
+        }
+    }
+    for (; p < npos; p += step) {
         float f[8];
         unpack8(dy[p * G + g], f);
 #pragma unroll
@@ -423,7 +441,7 @@ cudaError_t nn_relu_bwd(const void *y, void *dy, int64_t n, cudaStream_t s)
 cudaError_t nn_bias_grad(const void *dy, float *db, int64_t npos, int C, cudaStream_t s)
 {
     if (C % 8 == 0 && kT % (C / 8) == 0 && aligned16(dy, dy))
-        bias_grad8_kernel<<<grid_n(npos * C / 8), kT, 0, s>>>((const uint4 *)dy, db, npos, C / 8);
+        bias_grad8_kernel<<<std::min(grid_n(npos * C / 8), 152u * 4u), kT, 0, s>>>((const uint4 *)dy, db, npos, C / 8);
     else
         bias_grad_kernel<<<grid_n(npos * C), kT, 0, s>>>((const __nv_bfloat16 *)dy, db, npos, C);
     count_launches(1);

@@ -173,3 +173,10 @@ def test_glue_ops_vector_and_scalar_kernels_agree_bitwise(U):
         assert nn.vamrt_nn_bias_grad(g.data_ptr(), db.data_ptr(), D * H * W, ch, s) == 0
         torch.cuda.synchronize()
         np.testing.assert_allclose(db.cpu().numpy(), g.double().sum(0).cpu().numpy(), rtol=1e-4, atol=1e-3)
+    # many positions per thread: the four-deep unrolled loop and its tail
+    for npos, ch in ((1 << 20, 16), (300001, 48)):
+        g = torch.from_numpy(rng.standard_normal((npos, ch)).astype(np.float32)).to(torch.bfloat16).to(DEV)
+        db = torch.zeros(ch, device=DEV)
+        assert nn.vamrt_nn_bias_grad(g.data_ptr(), db.data_ptr(), npos, ch, s) == 0
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(db.cpu().numpy(), g.double().sum(0).cpu().numpy(), rtol=1e-4, atol=1e-2)
