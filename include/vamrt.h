@@ -327,8 +327,9 @@ vamrt_status vamrt_conv3d_tiling(int32_t d, int32_t h, int32_t wd, int32_t cin, 
  *
  * vamrt_conv3d_wgrad_bf16: dw[co][t][ci] += sum_p dy[p][co] x[p + off(t)][ci] for the
  *   convolution of vamrt_conv3d_bf16 (same x layout; dy [d][h][wd][cout]); tensor cores
- *   (rows t cin + ci in M, cout in N, positions in K), split over positions with FP32
- *   atomics (caller zeroes dw).  wd a multiple of 16, cin 16..1024, cout 16..256.
+ *   (rows t cin + ci in M, cout in N, positions in K; operands loaded by TMA), split over
+ *   positions with FP32 atomics (caller zeroes dw).  wd a multiple of 16, d h wd < 2^31,
+ *   cin 16..1024, cout 16..256; x and dy 16-byte aligned.
  * vamrt_nn_resample: op 0 = 2x2x2 average pool (fine -> coarse), 1 = its backward (coarse
  *   -> fine, /8), 2 = nearest 2x upsample (coarse -> fine), 3 = its backward (sum of 8);
  *   d, h, w are the FINE extents (even).

@@ -3,30 +3,19 @@
 //   dW[co][t][ci] += sum_p dY[p][co] X[p + off(t)][ci]      (zero outside the volume)
 //
 // GEMM mapping: C[m][n] = sum_k A[m][k] B[n][k] with m = t Cin + ci (A = X^T with the taps
-// stacked, in M tiles of 128 rows), n = co (B = dY^T, N = Cout), k = output positions.
-// A block owns a group of consecutive M tiles (their FP32 accumulators side by side in
-// TMEM, Cout columns each) and a range of positions, walked in stages of 32.  Per stage:
-//   1. cp.async copies raw channels-last rows into shared memory: for every (dz, dy) that
-//      the group's taps use, the 34 positions p0 + dz H W + dy W - 1 ... p0 + dz H W + dy W
-//      + 32 (all Cin channels, zeros beyond the array), and the stage's 32 rows of dY.
-//      Two raw buffers: the copies for stage c + 1 fly while stage c is transposed.
-//   2. every warp transposes 8-channel x 32-position strips into the canonical no-swizzle
-//      K-major layout (8-row x 16-byte core matrices, K groups 128 B apart, row groups
-//      512 B apart) with ldmatrix.trans + stmatrix.  Lane l supplies the row address of
-//      position p0 + l, so the dx shift is an address offset, and a position whose
-//      neighbour lies outside the volume (including the wrap across a row end) points
-//      at a zero row.
-//   3. one issuing thread per tile (lane 0 of warp w issues tiles w, w + nis, ...) issues
-//      the stage's two K = 16 MMAs into its tile's accumulator and commits them to the
-//      stage's mbarrier, which frees that canonical buffer for stage c + 2.
-// At the end each warp reads its TMEM lane quarter and adds the block's partial sums into
-// dW with FP32 atomics (consecutive lanes = consecutive rows t Cin + ci of dW: coalesced).
+// stacked, in M tiles of 128 rows), n = co (B = dY^T, N = Cout), k = output positions.  A
+// block owns a group of consecutive M tiles (FP32 accumulators side by side in TMEM) and
+// a range of positions walked in stages of KS; at the end it adds its partial sums into
+// dW with FP32 atomics (consecutive lanes = consecutive rows t Cin + ci: coalesced).
 // Every wait is bounded (2 s): on timeout the block sets the error flag, waits (bounded)
 // for its own MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 #include "tcgen05.cuh"
@@ -36,49 +25,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kWThreads = 256;             // 8 warps
-constexpr int kKS = 32;                    // positions per stage (= lanes)
-constexpr int kRawRows = kKS + 2;          // positions per raw (dz, dy) row
-constexpr int kTileBytes = 128 * kKS * 2;  // one M tile of A per stage: 8 KB
-constexpr int kRowGroupBytes = kKS * 16;   // 8 rows x 32 positions: 512 B
 constexpr int kMaxTpg = 8;
-constexpr int kMaxItems = kMaxTpg * 16 + 256 / 8;
-constexpr int kBatch = 8;                  // strips a warp transposes per batch
-
-struct WgradArgs {
-    const __nv_bfloat16 *X, *dY;
-    float *dW;
-    int *err;
-    int D, H, W, Cin, Cout, taps;
-    int Mtot, nmt, tpg;        // A rows (taps x Cin), M tiles, tiles per group
-    long long P;               // positions
-    int nstage, spb;           // stages of 32 positions in all, per block
-    int pairs;                 // (dz, dy) rows per raw X buffer
-    int xstride, ystride;      // raw row strides in bytes: 2 Cin + 16, 2 Cout + 16
-    int ncols;                 // TMEM columns allocated
-};
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// four 8x8 b16 matrices; lane l gives the address of row l % 8 of matrix l / 8.  After
-// .trans register j of lane l holds column l / 4, rows 2 (l % 4) and 2 (l % 4) + 1.
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                              uint32_t &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr)
-                 : "memory");
-}
-// the inverse placement without transposition: register j of lane l is row l / 4,
-// columns 2 (l % 4) and 2 (l % 4) + 1 of matrix j, whose row r goes to lane 8 j + r's address
-__device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3)
-{
-    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r0), "r"(r1),
-                 "r"(r2), "r"(r3)
-                 : "memory");
-}
 
 // tap t -> (dz, dy, dx) in -1..1 (taps == 1: the centre)
 __device__ __forceinline__ void tap_offset(int taps, int t, int &dz, int &dy, int &dx)
@@ -92,218 +39,300 @@ __device__ __forceinline__ void tap_offset(int taps, int t, int &dz, int &dy, in
     }
 }
 
-__global__ void __launch_bounds__(kWThreads, 2) conv3d_wgrad_kernel(const WgradArgs a)
+// ---------------------------------------------------------------------------------
+// TMA-fed kernel: no transposition.  The tensor cores also take operands MN-major (M or N
+// contiguous).  For A = X^T (M = t Cin + ci, K = positions) a column block of cw rows
+// (tap t, channels c0 .. c0 + cw - 1) over a stage's KS positions is X[p + off(t)][c0 ..
+// c0 + cw - 1], p = p0 .. p0 + KS - 1: KS rows of 2 cw bytes -- exactly what a TMA tile
+// load of box {cw channels, BX x, 1 y, 1 z} at (c0, x + dx, y + dy, z + dz) writes, with
+// the zero fill of out-of-range coordinates supplying the convolution's zero padding
+// (including x = -1 and x = W).  cw = 16, 32 or 64 channels (the widest dividing Cin), so
+// rows are 32, 64 or 128 bytes in the matching TMA swizzle, which is the tensor cores'
+// swizzled MN-major layout: column blocks LBO = KS x 2 cw bytes apart, 8-row K groups
+// SBO = 16 cw bytes apart.  B = dY^T likewise, blocks of cwB output channels, boxes
+// {cwB, KS} of dY viewed as [P][Cout].
+// Block: warp 0 issues the stage's boxes (lane 0 arms the stage's mbarrier with the byte
+// count), lane 0 of warps 4-7 issues the MMAs (accumulator = one M tile x K-step part, kp
+// parts per tile so that small groups still keep several issuers), all warps run the
+// epilogue.  A ring of stage slots, full/empty mbarriers per slot, bounded waits.
+// ---------------------------------------------------------------------------------
+constexpr int kTThreads = 256;
+constexpr int kTIssuer0 = 4, kTIssuers = 4;
+constexpr int kTMaxSlots = 4;
+
+struct TmaArgs {
+    float *dW;
+    int *err;
+    int D, H, W, Cin, Cout, taps;
+    int Mtot, nmt, tpg, kp;    // A rows, M tiles, tiles per group, accumulators per tile
+    int KS, BX;                // positions per stage and per X box (BX divides W and KS)
+    int nstage, spb;           // stages in all, per block
+    int slots, slot_bytes;     // ring of stage slots: B blocks, then the group's A blocks
+    int cwA, cwB;              // channels per column block (16, 32 or 64: 32/64/128-byte rows)
+    int ncols;
+};
+
+// UMMA layout type of a swizzled MN-major operand whose rows are cw x 2 bytes
+__host__ __device__ __forceinline__ uint32_t swizzle_layout(int cw) { return cw == 64 ? 2u : cw == 32 ? 4u : 6u; }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kTThreads, 2)
+    conv3d_wgrad_tma_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
+                            const TmaArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ __align__(8) unsigned long long bars[2 * kTMaxSlots + 1];   // full[slots], empty[slots], done
     __shared__ uint32_t s_tmem;
-    __shared__ int4 items[kMaxItems];
-    __shared__ __align__(16) uint4 zero16;
+    __shared__ volatile int s_abort;
+    __shared__ int s_fin;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // group of M tiles
-    const int g = blockIdx.x;
-    const int tile0 = g * a.tpg;
+    const int tile0 = blockIdx.x * a.tpg;
     const int ntile = min(a.tpg, a.nmt - tile0);
-    const int row0 = tile0 * 128;
-    const int row_end = min(a.Mtot, row0 + ntile * 128);
-    const int nis = min(ntile, 8);               // issuing warps
-    int t_first = row0 / a.Cin, t_last = (row_end - 1) / a.Cin;
-    int dzf, dyf, dxf, dzl, dyl, dxl;
-    tap_offset(a.taps, t_first, dzf, dyf, dxf);
-    tap_offset(a.taps, t_last, dzl, dyl, dxl);
-    const int pair_first = (dzf + 1) * 3 + (dyf + 1);
-    const int npairs = (dzl + 1) * 3 + (dyl + 1) - pair_first + 1;
-    const long long HW = (long long)a.H * a.W;
+    const int row0 = tile0 * 128, row_end = min(a.Mtot, row0 + ntile * 128);
+    const int nAb = (row_end - row0) / a.cwA, nBb = a.Cout / a.cwB;     // column blocks loaded
+    const int nacc = ntile * a.kp, nis = min(kTIssuers, nacc);
+    const int rowA = 2 * a.cwA, rowB = 2 * a.cwB;                          // bytes per K row
+    const int blkA = a.KS * rowA, blkB = a.KS * rowB;
+    const int Bbytes = nBb * blkB;
+    const uint32_t base = smem_u32(smem_raw);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kTMaxSlots]);
+    const uint32_t done = smem_u32(&bars[2 * kTMaxSlots]);
 
-    // shared-memory carve-up (dynamic part 1024-aligned)
-    unsigned char *base = smem_raw;
-    const uint32_t canonA = smem_u32(base);
-    const uint32_t canonA_bytes = (uint32_t)a.tpg * kTileBytes;
-    const uint32_t canonB = canonA + 2 * canonA_bytes;
-    const uint32_t canonB_bytes = (uint32_t)a.Cout / 8 * kRowGroupBytes;
-    const uint32_t rawX = canonB + 2 * canonB_bytes;
-    const uint32_t rawX_bytes = (uint32_t)a.pairs * kRawRows * a.xstride;
-    const uint32_t rawY = rawX + 2 * rawX_bytes;
-    const uint32_t rawY_bytes = (uint32_t)kKS * a.ystride;
-    const uint32_t zero_addr = smem_u32(&zero16);
-
-    // work items: A row groups (8 rows = 8 channels of one tap) then B row groups
-    const int nA = (row_end - row0) / 8, nB = a.Cout / 8, nitems = nA + nB;
-    for (int it = tid; it < nitems; it += kWThreads) {
-        int4 e;
-        if (it < nA) {
-            const int r = row0 + it * 8;
-            const int t = r / a.Cin, ci0 = r - t * a.Cin;
-            int dz, dy, dx;
-            tap_offset(a.taps, t, dz, dy, dx);
-            const int slot = (dz + 1) * 3 + (dy + 1) - pair_first;
-            e.x = slot * kRawRows * a.xstride + (dx + 1) * a.xstride + ci0 * 2;
-            e.y = it * kRowGroupBytes;                        // tile (it / 16) x 8 KB + (it % 16) x 512
-            e.z = (dz + 1) | (dy + 1) << 2 | (dx + 1) << 4;
-        } else {
-            const int cg = it - nA;
-            e.x = cg * 16;
-            e.y = cg * kRowGroupBytes;
-            e.z = 256;
-        }
-        e.w = 0;
-        items[it] = e;
-    }
     if (tid == 0) {
-        zero16 = make_uint4(0, 0, 0, 0);
-        mbar_init(smem_u32(&bars[0]), nis);
-        mbar_init(smem_u32(&bars[1]), nis);
+        for (int s = 0; s < a.slots; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, nis);
+        }
+        mbar_init(done, nis);
         mbar_init_fence();
+        s_abort = 0;
+        s_fin = 0;
     }
-    if (warp == 0) tmem_alloc(smem_u32(&s_tmem), a.ncols);
+    if (warp == kTIssuer0) tmem_alloc(smem_u32(&s_tmem), a.ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-
     const int s_begin = blockIdx.y * a.spb;
     const int n = max(0, min(a.spb, a.nstage - s_begin));
-    const uint32_t idesc = instr_desc(128, a.Cout);
 
-    // raw-row copies of stage st into buffer b (issued by every thread, one commit group)
-    const int cpr = a.Cin / 8, cpy = a.Cout / 8;
-    const int xr0 = tid / cpr, xh = tid - xr0 * cpr, xstep = kWThreads / cpr;
-    const int yr0 = tid / cpy, yh = tid - yr0 * cpy, ystep = kWThreads / cpy;
-    auto load_raw = [&](int st, int b) {
-        const long long p0 = (long long)st * kKS;
-        if (xr0 < xstep) {
-            for (int r = xr0; r < npairs * kRawRows; r += xstep) {
-                const int j = r / kRawRows, q = r - j * kRawRows;
-                const int pair = pair_first + j;
-                const long long src = p0 + (long long)(pair / 3 - 1) * HW + (long long)(pair % 3 - 1) * a.W - 1 + q;
-                const bool ok = src >= 0 && src < a.P;
-                cp_async16_zfill(rawX + b * rawX_bytes + (uint32_t)(j * kRawRows + q) * a.xstride + xh * 16,
-                                 ok ? (const void *)(a.X + src * a.Cin + xh * 8) : (const void *)a.X, ok ? 16 : 0);
+    if (warp == 0) {
+        // ---- producer: the stage's A boxes (plane it, box b) and B planes, spread over the lanes ----
+        const long long HW = (long long)a.H * a.W;
+        const int nbx = a.KS / a.BX;
+        const uint32_t tx = (uint32_t)(nAb * blkA + Bbytes);
+        for (int c = 0; c < n; ++c) {
+            const int slot = c % a.slots;
+            bool ok = true;
+            if (c >= a.slots) ok = mbar_wait(empty0 + 8 * slot, (c / a.slots - 1) & 1);
+            if (!__all_sync(0xffffffffu, ok) || __any_sync(0xffffffffu, s_abort)) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(a.err, 1);
+                }
+                break;
             }
-        }
-        if (yr0 < ystep) {
-            for (int q = yr0; q < kKS; q += ystep) {
-                const long long src = p0 + q;
-                const bool ok = src < a.P;
-                cp_async16_zfill(rawY + b * rawY_bytes + (uint32_t)q * a.ystride + yh * 16,
-                                 ok ? (const void *)(a.dY + src * a.Cout + yh * 8) : (const void *)a.dY,
-                                 ok ? 16 : 0);
-            }
-        }
-        cp_async_commit();
-    };
-
-    // this lane's position p0 + lane as (z, y, x), advanced by 32 per stage
-    long long p = (long long)s_begin * kKS + lane;
-    int z = (int)(p / HW);
-    int y = (int)((p - (long long)z * HW) / a.W);
-    int x = (int)(p - (long long)z * HW - (long long)y * a.W);
-
-    bool ok = true;
-    int c_done = -1;                                  // last stage whose MMAs were issued
-    if (n > 0) load_raw(s_begin, 0);
-    for (int c = 0; c < n; ++c) {
-        const int buf = c & 1;
-        if (c + 1 < n) load_raw(s_begin + c + 1, buf ^ 1);
-        else cp_async_commit();
-        cp_async_wait_1();
-        bool mine = true;
-        if (c >= 2) mine = mbar_wait(smem_u32(&bars[buf]), ((c - 2) >> 1) & 1);
-        if (!__syncthreads_and(mine)) { ok = false; break; }
-
-        // neighbour validity of this lane's position: bit d + 1 for offset d
-        const unsigned zok = ((unsigned)(z - 1) < (unsigned)a.D) | ((unsigned)z < (unsigned)a.D) << 1 |
-                             ((unsigned)(z + 1) < (unsigned)a.D) << 2;
-        const unsigned yok = ((unsigned)(y - 1) < (unsigned)a.H) | ((unsigned)y < (unsigned)a.H) << 1 |
-                             ((unsigned)(y + 1) < (unsigned)a.H) << 2;
-        const unsigned xok = ((unsigned)(x - 1) < (unsigned)a.W) | ((unsigned)x < (unsigned)a.W) << 1 |
-                             ((unsigned)(x + 1) < (unsigned)a.W) << 2;
-        const uint32_t rx = rawX + buf * rawX_bytes + lane * a.xstride;
-        const uint32_t ry = rawY + buf * rawY_bytes + lane * a.ystride;
-        const uint32_t ca = canonA + buf * canonA_bytes + lane * 16;
-        const uint32_t cb = canonB + buf * canonB_bytes + lane * 16;
-        // kBatch items per warp at a time: every load issued before the first store
-        for (int it0 = warp; it0 < nitems; it0 += kBatch * (kWThreads / 32)) {
-            uint32_t r[kBatch][4], dst[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int it = it0 + u * (kWThreads / 32);
-                if (it < nitems) {
-                    const int4 e = items[it];
-                    uint32_t src;
-                    if (e.z & 256) {
-                        src = ry + e.x;
-                        dst[u] = cb + e.y;
-                    } else {
-                        const unsigned v =
-                            (zok >> (e.z & 3)) & (yok >> ((e.z >> 2) & 3)) & (xok >> ((e.z >> 4) & 3)) & 1u;
-                        src = v ? rx + e.x : zero_addr;
-                        dst[u] = ca + e.y;
-                    }
-                    ldsm_x4_trans(src, r[u][0], r[u][1], r[u][2], r[u][3]);
+            const uint32_t sb = base + slot * a.slot_bytes, bar = full0 + 8 * slot;
+            if (lane == 0) mbar_arrive_expect_tx(bar, tx);
+            __syncwarp();
+            const long long p0 = (long long)(s_begin + c) * a.KS;
+            for (int k = lane; k < nAb * nbx + nBb; k += 32) {
+                if (k < nBb) {
+                    tma_load_2d(sb + k * blkB, &ymap, a.cwB * k, (int)p0, bar);
+                } else {
+                    const int j = (k - nBb) / nbx, b = k - nBb - j * nbx;
+                    const int r = row0 + j * a.cwA, t = r / a.Cin, c0 = r - t * a.Cin;
+                    int dz, dy, dx;
+                    tap_offset(a.taps, t, dz, dy, dx);
+                    const long long p = p0 + (long long)b * a.BX;
+                    const int z = (int)(p / HW);
+                    const long long rem = p - (long long)z * HW;
+                    const int y = (int)(rem / a.W), x = (int)(rem - (long long)y * a.W);
+                    tma_load_4d(sb + Bbytes + j * blkA + b * a.BX * rowA, &xmap, c0, x + dx, y + dy, z + dz, bar);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                if (it0 + u * (kWThreads / 32) < nitems) stsm_x4(dst[u], r[u][0], r[u][1], r[u][2], r[u][3]);
         }
-        fence_proxy_async();
-        __syncthreads();
-        if (lane == 0 && warp < nis) {
-            tc_fence_after();
-            const uint32_t a0 = canonA + buf * canonA_bytes, b0 = canonB + buf * canonB_bytes;
-            for (int i = warp; i < ntile; i += nis) {
-#pragma unroll
-                for (int s = 0; s < 2; ++s)
-                    mma_bf16(tmem + (uint32_t)(i * a.Cout), smem_desc(a0 + i * kTileBytes + s * 256, 128, 512),
-                             smem_desc(b0 + s * 256, 128, 512), idesc, (c > 0 || s > 0) ? 1u : 0u);
+    } else if (warp >= kTIssuer0 && warp - kTIssuer0 < nis) {
+        // ---- issuers: accumulators k0, k0 + nis, ... = (tile acc / kp, K-step part acc % kp) ----
+        if (lane == 0) {
+            const int k0 = warp - kTIssuer0, nks = a.KS / 16;
+            const uint32_t idesc = instr_desc(128, a.Cout) | (1u << 15) | (1u << 16);   // A, B MN-major
+            const uint64_t swA = (uint64_t)swizzle_layout(a.cwA) << 61, swB = (uint64_t)swizzle_layout(a.cwB) << 61;
+            for (int c = 0; c < n; ++c) {
+                const int slot = c % a.slots;
+                if (!mbar_wait(full0 + 8 * slot, (c / a.slots) & 1) || s_abort) {
+                    s_abort = 1;
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sb = base + slot * a.slot_bytes;
+                for (int acc = k0; acc < nacc; acc += nis) {
+                    const int i = acc / a.kp, part = acc - i * a.kp;
+                    for (int s = part; s < nks; s += a.kp)
+                        mma_bf16(tmem + (uint32_t)(acc * a.Cout),
+                                 smem_desc(sb + Bbytes + i * (128 / a.cwA) * blkA + s * 16 * rowA, blkA, 8 * rowA) | swA,
+                                 smem_desc(sb + s * 16 * rowB, blkB, 8 * rowB) | swB, idesc,
+                                 (c > 0 || s != part) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * slot);
             }
-            mma_commit(smem_u32(&bars[buf]));
+            mma_commit(done);
         }
-        c_done = c;
-        x += kKS;
-        while (x >= a.W) {
-            x -= a.W;
-            if (++y == a.H) { y = 0; ++z; }
-        }
+        __syncwarp();
     }
-    cp_async_wait_all();
-    if (ok && c_done >= 0) {
-        const bool mine = mbar_wait(smem_u32(&bars[c_done & 1]), (c_done >> 1) & 1);
-        ok = __syncthreads_and(mine);
+    __syncthreads();
+    if (tid == 0) {
+        s_fin = mbar_wait(done, 0) ? 1 : 0;     // every MMA issued has completed
+        if (!s_fin) atomicExch(a.err, 1);
     }
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(a.err, 1);
-            if (c_done >= 0) (void)mbar_wait(smem_u32(&bars[c_done & 1]), (c_done >> 1) & 1);
-        }
-    } else if (c_done >= 0) {
-        tc_fence_after();
+    __syncthreads();
+    tc_fence_after();
+    if (s_fin && !s_abort && n > 0) {
         const int q = warp & 3;
-        for (int i = warp >> 2; i < ntile; i += 2) {
+        for (int i = warp >> 2; i < ntile; i += kTThreads / 128) {
             const int R = row0 + i * 128 + q * 32 + lane;
             for (int co0 = 0; co0 < a.Cout; co0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(i * a.Cout + co0), v);
+                float sum[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(i * a.kp * a.Cout + co0), sum);
+                for (int part = 1; part < a.kp; ++part) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((i * a.kp + part) * a.Cout + co0), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[j] += v[j];
+                }
                 if (R < row_end) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) atomicAdd(a.dW + (long long)(co0 + j) * a.Mtot + R, v[j]);
+                    for (int j = 0; j < 16; ++j) atomicAdd(a.dW + (long long)(co0 + j) * a.Mtot + R, sum[j]);
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, a.ncols);
+    if (warp == kTIssuer0) tmem_dealloc(tmem, a.ncols);
 }
 
-// number of (dz, dy) rows the taps of rows [r0, r1) use
-int pairs_of(int taps, int Cin, int r0, int r1)
+int sm_count_wgrad()
 {
-    if (taps == 1) return 1;
-    const int tf = r0 / Cin, tl = (r1 - 1) / Cin;
-    return tl / 3 - tf / 3 + 1;
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 148;
+    return sms;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// TMA-fed kernel: stages of 64 positions where W allows (else 32), the largest tile group
+// whose ring of three slots and accumulators fit two blocks per SM (else one); returns
+// cudaErrorNotSupported for what it cannot take
+cudaError_t launch_wgrad_tma(const void *X, const void *dY, float *dW, int D, int H, int W, int Cin, int Cout,
+                             int taps, int *err, cudaStream_t s)
+{
+    const long long P = (long long)D * H * W;
+    if (((uintptr_t)X & 15) || ((uintptr_t)dY & 15) || P >= (1ll << 31)) return cudaErrorNotSupported;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    TmaArgs a{};
+    a.dW = dW;
+    a.err = err;
+    a.D = D; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.taps = taps;
+    a.Mtot = taps * Cin;
+    a.nmt = (a.Mtot + 127) / 128;
+    a.KS = W % 64 == 0 ? 64 : 32;
+    a.BX = W % a.KS == 0 ? a.KS : 16;
+    a.nstage = (int)((P + a.KS - 1) / a.KS);
+    a.cwA = Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16;
+    a.cwB = Cout % 64 == 0 ? 64 : Cout % 32 == 0 ? 32 : 16;
+    int per_sm = 0;
+    for (int bps = 2; bps >= 1 && !per_sm; --bps) {
+        const size_t budget = bps == 2 ? 108 * 1024 : 220 * 1024;
+        for (int tpg = std::min(kMaxTpg, std::min(a.nmt, (512 / bps) / Cout)); tpg >= 1; --tpg) {
+            const int ng = (a.nmt + tpg - 1) / tpg;
+            const int t2 = (a.nmt + ng - 1) / ng;
+            const int slot = ((Cout + 128 * t2) * a.KS * 2 + 1023) / 1024 * 1024;
+            const int slots = std::min(kTMaxSlots, (int)(budget / slot));
+            if (slots < 3) continue;
+            int kp = std::min(a.KS / 16, std::max(1, kTIssuers / t2));
+            while (kp > 1 && t2 * kp * Cout > 512 / bps) --kp;
+            a.tpg = t2;
+            a.kp = kp;
+            a.slots = slots;
+            a.slot_bytes = slot;
+            per_sm = bps;
+            break;
+        }
+    }
+    if (!per_sm) return cudaErrorNotSupported;
+    int ncols = 32;
+    while (ncols < a.tpg * a.kp * Cout) ncols <<= 1;
+    a.ncols = ncols;
+
+    CUtensorMap xmap, ymap;
+    const cuuint64_t xdims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+    const cuuint64_t xstr[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    const cuuint32_t xbox[4] = {(cuuint32_t)a.cwA, (cuuint32_t)a.BX, 1, 1};
+    const cuuint64_t ydims[2] = {(cuuint64_t)Cout, (cuuint64_t)P};
+    const cuuint64_t ystr[1] = {(cuuint64_t)Cout * 2};
+    const cuuint32_t ybox[2] = {(cuuint32_t)a.cwB, (cuuint32_t)a.KS};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    auto swz = [](int cw) {
+        return cw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : cw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+    };
+    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(X), xdims, xstr, xbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz(a.cwA), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(dY), ydims, ystr, ybox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz(a.cwB), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorNotSupported;
+
+    const int ngroups = (a.nmt + a.tpg - 1) / a.tpg;
+    const int target = per_sm * sm_count_wgrad();
+    int nsplit = std::max(1, target / ngroups);      // at most one wave
+    a.spb = (a.nstage + nsplit - 1) / nsplit;
+    nsplit = (a.nstage + a.spb - 1) / a.spb;
+    const size_t smem = (size_t)a.slots * a.slot_bytes;
+    cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    conv3d_wgrad_tma_kernel<<<dim3(ngroups, nsplit), kTThreads, smem, s>>>(xmap, ymap, a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -311,62 +340,9 @@ int pairs_of(int taps, int Cin, int r0, int r1)
 cudaError_t launch_conv3d_wgrad_tc(const void *X, const void *dY, float *dW, int D, int H, int W, int Cin, int Cout,
                                    int taps, int *err, cudaStream_t s)
 {
-    WgradArgs a{};
-    a.X = (const __nv_bfloat16 *)X;
-    a.dY = (const __nv_bfloat16 *)dY;
-    a.dW = dW;
-    a.err = err;
-    a.D = D; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.taps = taps;
-    a.Mtot = taps * Cin;
-    a.nmt = (a.Mtot + 127) / 128;
-    a.P = (long long)D * H * W;
-    a.nstage = (int)((a.P + kKS - 1) / kKS);
-    a.xstride = 2 * Cin + 16;
-    a.ystride = 2 * Cout + 16;
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-
-    // tiles per group: two blocks per SM if their shared memory and TMEM columns allow it,
-    // else one; groups balanced in size
-    int per_sm = 0;
-    size_t smem = 0;
-    for (int bps = 2; bps >= 1 && !per_sm; --bps) {
-        const size_t budget = bps == 2 ? 108 * 1024 : 220 * 1024;   // beside ~3 KB static + 1 KB reserved
-        const int colcap = 512 / bps;
-        for (int tpg = std::min(kMaxTpg, std::min(a.nmt, colcap / Cout)); tpg >= 1; --tpg) {
-            const int ng = (a.nmt + tpg - 1) / tpg;
-            const int t2 = (a.nmt + ng - 1) / ng;
-            int pairs = 0;
-            for (int gi = 0; gi * t2 < a.nmt; ++gi)
-                pairs = std::max(pairs, pairs_of(taps, Cin, gi * t2 * 128, std::min(a.Mtot, (gi + 1) * t2 * 128)));
-            const size_t need = 2 * ((size_t)t2 * kTileBytes + (size_t)Cout / 8 * kRowGroupBytes +
-                                     (size_t)pairs * kRawRows * a.xstride + (size_t)kKS * a.ystride);
-            if (need <= budget) {
-                a.tpg = t2;
-                a.pairs = pairs;
-                smem = need;
-                per_sm = bps;
-                break;
-            }
-        }
-    }
-    if (!per_sm) return cudaErrorNotSupported;
-    const int ngroups = (a.nmt + a.tpg - 1) / a.tpg;
-    int ncols = 32;
-    while (ncols < a.tpg * Cout) ncols <<= 1;
-    a.ncols = ncols;
-    // at most one wave: a block more than the resident slots would double the time
-    const int target = per_sm * sms;
-    int nsplit = std::max(1, target / ngroups);
-    a.spb = (a.nstage + nsplit - 1) / nsplit;
-    nsplit = (a.nstage + a.spb - 1) / a.spb;
-    cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    conv3d_wgrad_kernel<<<dim3(ngroups, nsplit), kWThreads, smem, s>>>(a);
-    count_launches(1);
-    return cudaGetLastError();
+    const cudaError_t e = launch_wgrad_tma(X, dY, dW, D, H, W, Cin, Cout, taps, err, s);
+    if (e == cudaSuccess) count_launches(1);
+    return e;
 }
 
 }  // namespace vamrt

@@ -27,9 +27,11 @@ vamrt_status vamrt_conv3d_wgrad_bf16(const void *x, const void *dy, float *dw, i
 {
     if (!x || !dy || !dw || !err_flag) return einval("NULL argument");
     if (d < 1 || h < 1 || wd < 16 || wd % 16) return einval("extents: d, h >= 1 and wd a multiple of 16");
+    if ((int64_t)d * h * wd >= ((int64_t)1 << 31)) return einval("d h wd must stay below 2^31 positions");
     if (cin < 16 || cin % 16 || cin > 1024 || cout < 16 || cout % 16 || cout > 256)
         return einval("channel counts: cin 16..1024, cout 16..256, multiples of 16");
     if (taps != 1 && taps != 27) return einval("taps must be 1 or 27");
+    if (((uintptr_t)x | (uintptr_t)dy) & 15) return einval("x and dy must be 16-byte aligned");
     return cuda_status(vamrt::launch_conv3d_wgrad_tc(x, dy, dw, d, h, wd, cin, cout, taps, (int *)err_flag,
                                                      (cudaStream_t)stream));
 }

@@ -126,6 +126,22 @@ def test_null_arguments_are_einval(L):
     L.vamrt_destroy_projector(None)  # no-op
 
 
+def test_conv3d_weight_gradient_rejects_bad_arguments(L):
+    """Host-side checks of vamrt_conv3d_wgrad_bf16 return EINVAL before any CUDA call (the
+    addresses are never dereferenced)."""
+    from paper_2211_03516_gb300 import vamrt
+    f = L.vamrt_conv3d_wgrad_bf16
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int32] * 6 + [ctypes.c_void_p] * 2
+    good = dict(x=0x10000, dy=0x20000, dw=0x30000, d=2, h=3, w=16, cin=16, cout=16, taps=27, err=0x40000)
+    cases = [dict(x=0x10008), dict(dy=0x20004), dict(x=None), dict(err=None), dict(w=24), dict(w=8),
+             dict(cin=24), dict(cin=1040), dict(cout=272), dict(taps=9), dict(d=0),
+             dict(d=1 << 14, h=1 << 13, w=16)]
+    for bad in cases:
+        a = {**good, **bad}
+        st = f(a["x"], a["dy"], a["dw"], a["d"], a["h"], a["w"], a["cin"], a["cout"], a["taps"], a["err"], None)
+        assert st == vamrt.VAMRT_EINVAL, bad
+
+
 def test_missing_library_fails_loudly(monkeypatch):
     from paper_2211_03516_gb300 import vamrt
     monkeypatch.setattr(vamrt, "_lib", None)

@@ -63,14 +63,14 @@ def test_conv3d_matches_direct_convolution(U, shape, cin, cout, taps):
 
 @pytest.mark.parametrize("shape,cin,cout,taps", [
     ((3, 5, 32), 16, 16, 27), ((3, 5, 32), 48, 16, 27), ((3, 5, 32), 16, 32, 27), ((3, 5, 32), 16, 16, 1),
-    ((2, 3, 16), 16, 16, 27),        # 32-position stages span two rows
-    ((1, 1, 16), 32, 48, 27),        # a single partial stage
-    ((2, 2, 48), 192, 64, 27),       # 21 groups of two M tiles
+    ((2, 3, 16), 16, 16, 27),        # W = 16: a 32-position stage is two 16-position boxes
+    ((1, 1, 16), 32, 48, 27),        # a single stage; 32-byte dY rows at Cout = 48
+    ((2, 2, 48), 192, 64, 27),       # W = 48: 16-position boxes; 128-byte X rows
     ((2, 3, 16), 128, 256, 27),      # N = 256
-    ((5, 4, 64), 16, 16, 27),        # W = 64: half a row per stage
-    ((4, 3, 32), 96, 32, 27),
-    ((2, 2, 16), 1024, 16, 1),       # one block per SM
-    ((1, 2, 16), 512, 16, 27),       # one M tile per group, wide raw rows
+    ((5, 4, 64), 16, 16, 27),        # W = 64: stages of 64 positions
+    ((4, 3, 32), 96, 32, 27),        # 64-byte rows
+    ((2, 2, 16), 1024, 16, 1),       # 1^3 taps, wide Cin
+    ((1, 2, 16), 512, 16, 27),       # many tile groups
     ((24, 32, 64), 16, 16, 27),      # hundreds of blocks, several stages each
 ])
 def test_conv3d_weight_gradient_matches_direct_sum(U, shape, cin, cout, taps):
