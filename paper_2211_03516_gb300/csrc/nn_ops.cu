@@ -327,7 +327,7 @@ __global__ void prepare_input_kernel(const float *__restrict__ proj, __nv_bfloat
 __global__ void head_mse_kernel(const float *__restrict__ zin, int cz, const float *__restrict__ base, float in_scale,
                                 const float *__restrict__ target, float target_scale, float *__restrict__ out,
                                 float out_scale, __nv_bfloat16 *__restrict__ dz, int A, int V, int U, int Dp,
-                                double *__restrict__ loss)
+                                double *__restrict__ loss, bool dz16)
 {
     const int64_t n = (int64_t)Dp * V * U;
     const double inv_n = 1.0 / ((double)A * V * U);
@@ -346,13 +346,28 @@ __global__ void head_mse_kernel(const float *__restrict__ zin, int cz, const flo
             }
         }
         if (dz) {
-            dz[q * cz] = tobf(g);
-            for (int c = 1; c < cz; ++c) dz[q * cz + c] = tobf(0.f);
+            if (cz == 16 && dz16) {
+                // the 16-channel row (g, 0, ..., 0) as two 16-byte stores
+                uint4 *d = reinterpret_cast<uint4 *>(dz + q * 16);
+                d[0] = make_uint4((unsigned)__bfloat16_as_ushort(tobf(g)), 0u, 0u, 0u);
+                d[1] = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                dz[q * cz] = tobf(g);
+                for (int c = 1; c < cz; ++c) dz[q * cz + c] = tobf(0.f);
+            }
         }
     }
     if (loss && target) {
+        // one atomic per block: warps reduce by shuffles, then warp 0 over the warps
+        __shared__ double part[kT / 32];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv_n);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            acc = threadIdx.x < (int)(blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (threadIdx.x == 0) atomicAdd(loss, acc * inv_n);
+        }
     }
 }
 
@@ -480,8 +495,10 @@ cudaError_t nn_head_mse(const float *z, int cz, const float *base, float in_scal
         cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    head_mse_kernel<<<grid_n((int64_t)Dp * V * U), kT, 0, s>>>(z, cz, base, in_scale, target, target_scale, out,
-                                                                out_scale, (__nv_bfloat16 *)dz, A, V, U, Dp, loss);
+    // few blocks: each ends in one same-address FP64 atomic on the loss
+    const bool dz16 = dz && ((uintptr_t)dz & 15) == 0;
+    head_mse_kernel<<<std::min(grid_n((int64_t)Dp * V * U), 152u * 4u), kT, 0, s>>>(
+        z, cz, base, in_scale, target, target_scale, out, out_scale, (__nv_bfloat16 *)dz, A, V, U, Dp, loss, dz16);
     count_launches(1);
     return cudaGetLastError();
 }
