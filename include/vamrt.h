@@ -312,8 +312,9 @@ vamrt_status vamrt_ramlak_filter(const float *proj, float *out, int64_t rows, in
 
 /*
  * vamrt_conv3d_tiling: which kernel vamrt_conv3d_bf16 runs for this shape on the current
- * device, written to out[4] (host array): out[0] = 1 for the halo-tile kernel (W % 8 == 0;
- * regions of out[1] planes x out[2] rows, out[3] output channels per work item), 0 for the
+ * device, written to out[4] (host array): out[0] = 1 for the halo-tile kernel (W % 8 == 0
+ * and W <= 240, x 16-byte aligned at run time; regions of out[1] planes x out[2] rows,
+ * out[3] output channels per work item), 0 for the
  * gather kernel (out[1..3] = 0).  Host-only query, launches nothing.  Errors: EINVAL (NULL or
  * sizes vamrt_conv3d_bf16 rejects), ECUDA (no device).
  */

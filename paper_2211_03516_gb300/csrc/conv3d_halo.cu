@@ -52,7 +52,8 @@ using namespace tc;
 
 constexpr int kLoadWarp0 = 4, kLoadWarps = 4, kMmaWarp0 = 8, kMmaWarps = 4;
 constexpr int kHaloThreads = 384;   // 4 epilogue warps, 4 loader warps, 4 MMA warps
-constexpr int kGuard = 8;          // zero slots ahead of each staged half
+constexpr int kPadX = 8;           // zero slots ahead of x = 0 in every staged row (x = -8 .. -1)
+constexpr int kRowBytes = 32;      // one staged slot: 16 bf16 channels of one voxel
 constexpr int kMaxTiles = 32;
 constexpr int kSmemLimit = 225 * 1024;
 
@@ -64,7 +65,7 @@ struct HaloArgs {
     int D, H, W, Cin, Cout, relu;
     int TZ, TY, WP, PT, T, Nt;      // region planes / rows, slot pitches, M tiles, channels per item
     int NX, rowtile, mg, adv;       // dx taps per MMA; tile = one 128-voxel row; tile margin, advance
-    int half_bytes, stage_bytes, ncols;
+    int a_bytes, box_bytes, stage_bytes, ncols;   // staged input tile (with slack), its TMA bytes, stage
     int ry, nslice, nitems;         // regions along y, channel slices, work items
 };
 
@@ -76,17 +77,31 @@ __device__ void halo_fail(volatile int *abort_flag, int *err)
     atomicExch(err, 1);
 }
 
-// warps 4-7: cp.async copies of the input tile (both 8-channel halves; pairs of lanes
-// cover the 32 bytes of a voxel's chunk, a warp 16 consecutive voxels of one row; rows
-// outside the volume are zero-filled) and of the weights, into two stages
+// raise the phase's expected transaction bytes (no arrival)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// warps 4-7: per 16-channel chunk, one TMA box of the input tile (thread 0 adds its byte
+// count to the stage's mbarrier before any arrival; the box's zero fill supplies every pad
+// and out-of-volume halo voxel) and cp.async copies of the weights, into two stages
 template <int TAPS>
-__device__ void role_load(const HaloArgs &a, uint32_t sbase, uint32_t full0, uint32_t empty0,
-                          volatile int *abort_flag)
+__device__ void role_load(const CUtensorMap *xmap, const HaloArgs &a, uint32_t sbase, uint32_t full0,
+                          uint32_t empty0, volatile int *abort_flag)
 {
     constexpr int kHalo = TAPS == 27 ? 1 : 0;
-    const int lt = threadIdx.x - kLoadWarp0 * 32, lane = lt & 31, lw = lt >> 5;
+    const int lt = threadIdx.x - kLoadWarp0 * 32, lane = lt & 31;
     const int nc = a.Cin >> 4;
-    const int RY = a.TY + 2 * kHalo, R = (a.TZ + 2 * kHalo) * RY;
     int i = 0;
     for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
         const int slice = item % a.nslice, r = item / a.nslice;
@@ -103,23 +118,17 @@ __device__ void role_load(const HaloArgs &a, uint32_t sbase, uint32_t full0, uin
             }
             if (__any_sync(0xffffffffu, *abort_flag)) return;
             const uint32_t xs = sbase + s * a.stage_bytes;
-            for (int row = lw; row < R; row += kLoadWarps) {
-                const int zb = row / RY, yb = row - zb * RY, z = z0 + zb, y = y0 + yb;
-                const bool in = z >= 0 && z < a.D && y >= 0 && y < a.H;
-                const __nv_bfloat16 *src = in ? a.X + (((int64_t)z * a.H + y) * a.W * a.Cin + c * 16) : a.X;
-                const uint32_t dst = xs + (uint32_t)(kGuard + row * a.WP) * 16;
-                for (int e = lane; e < 2 * a.W; e += 32) {
-                    const int x = e >> 1, h = e & 1;
-                    cp_async16_zfill(dst + h * a.half_bytes + x * 16, in ? src + (x * a.Cin + h * 8) : src, in ? 16 : 0);
-                }
-            }
-            const uint32_t wb = xs + 2 * a.half_bytes;
+            const uint32_t wb = xs + a.a_bytes;
             const int ng = TAPS * a.Nt * 2;
             for (int g = lt; g < ng; g += kLoadWarps * 32) {
                 const int t = g / (2 * a.Nt), rem = g - t * 2 * a.Nt, co = rem >> 1, h = rem & 1;
                 const int grp = t / a.NX, dxi = t - grp * a.NX;      // B rows n = dxi Nt + co
                 cp_async16(wb + grp * a.NX * a.Nt * 32 + core_off(dxi * a.Nt + co, h),
                            a.Wt + (((int64_t)(co0 + co) * TAPS + t) * a.Cin + c * 16 + h * 8));
+            }
+            if (lt == 0) {
+                mbar_expect_tx(full, (uint32_t)a.box_bytes);     // before this thread's own arrival
+                tma_load_4d(xs, xmap, c * 16, -kPadX, y0, z0, full);
             }
             cp_async_wait_all();
             fence_proxy_async();
@@ -156,12 +165,12 @@ __device__ void role_mma(const HaloArgs &a, int k0, uint32_t sbase, uint32_t tme
                 return;
             }
             tc_fence_after();
-            const uint32_t wb = sbase + s * a.stage_bytes + 2 * a.half_bytes;
+            const uint32_t wb = sbase + s * a.stage_bytes + a.a_bytes;
             for (int g = 0; g < ngroups; ++g) {
                 int off = 0;
                 if (TAPS == 27) off = (g / 3 - 1) * a.PT + (g % 3 - 1) * a.WP;
                 // stage and (dz, dy) shift added to the descriptors' 16-byte address field
-                const int64_t dt = (int64_t)(s * a.stage_bytes / 16 + off);
+                const int64_t dt = (int64_t)(s * a.stage_bytes / 16 + off * (kRowBytes / 16));
                 const uint64_t bdesc = smem_desc(wb + g * NN * 32, 128, 256);
                 const uint32_t acc = (c | g) ? 1u : 0u;
                 uint32_t d = dcol + (uint32_t)(k0 * NN);
@@ -247,10 +256,10 @@ __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, 
         const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * a.T * NN);
         for (int j = 0; j < a.T; ++j) {
             const int q = s_q[j] + tid;
-            const int oz = q >= 0 ? q / a.PT : -1, rem = q - oz * a.PT, oy = rem / a.WP, x = rem - oy * a.WP;
+            const int oz = q >= 0 ? q / a.PT : -1, rem = q - oz * a.PT, oy = rem / a.WP, x = rem - oy * a.WP - kPadX;
             const int z = z0 + oz, y = y0 + oy;
-            const bool valid = tid >= a.mg && tid < 128 - a.mg && oz == s_oz[j] && oy < a.TY && x < a.W &&
-                               z < a.D && y < a.H;
+            const bool valid = tid >= a.mg && tid < a.mg + a.adv && oz == s_oz[j] && oy < a.TY && x >= 0 &&
+                               x < a.W && z < a.D && y < a.H;
             OT *dst = (OT *)a.Y + ((((int64_t)z * a.H + y) * a.W + x) * a.Cout + co0);
             for (int n0 = 0; n0 < a.Nt; n0 += 16, ++step) {
                 const uint32_t col = lanes + (uint32_t)(j * NN + n0);
@@ -306,7 +315,7 @@ __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, 
 
 template <int TAPS, typename OT>
 __global__ void __launch_bounds__(kHaloThreads, 1)
-    conv3d_halo_kernel(const HaloArgs a)
+    conv3d_halo_kernel(const __grid_constant__ CUtensorMap xmap, const HaloArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[8];   // full[2], empty[2], acc_full[2], acc_empty[2]
@@ -319,38 +328,29 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = smem_u32(smem);
 
-    // zero slots that no load writes: the guard ahead of each staged half (x = -1 of its
-    // first row) and the 8 pad slots closing every row (x = W of the row, x = -1 of the next)
-    {
-        const int R = (a.TZ + (TAPS == 27 ? 2 : 0)) * (a.TY + (TAPS == 27 ? 2 : 0));
-        const int per_half = kGuard + R * 8;
-        for (int i = tid; i < 4 * per_half; i += kHaloThreads) {
-            const int sh = i / per_half, k = i - sh * per_half;
-            const int slot = k < kGuard ? k : kGuard + ((k - kGuard) >> 3) * a.WP + a.W + ((k - kGuard) & 7);
-            *(uint4 *)(smem + (sh >> 1) * a.stage_bytes + (sh & 1) * a.half_bytes + slot * 16) = make_uint4(0, 0, 0, 0);
-        }
-    }
-    // first slot of each M tile, relative to output voxel (0, 0, 0) of the region, and the
-    // output plane the tile belongs to (rows that run on into the next plane are dropped)
+    // first slot of each M tile (slot of the region's output voxel (0, 0, x) is x + kPadX),
+    // and the output plane the tile belongs to (rows that run on into the next plane are
+    // dropped); every start is a multiple of 8 slots, one 256-byte swizzle atom
     for (int j = tid; j < a.T; j += kHaloThreads) {
         int q, oz;
-        if (a.rowtile) {          // W = 128: tile j is row (oz, oy)
+        if (a.rowtile) {          // W = 128: tile j is row (oz, oy), x = 0 .. 127
             oz = j / a.TY;
-            q = oz * a.PT + (j - oz * a.TY) * a.WP;
-        } else {                  // runs through each plane's rows, advancing 128 - 2 mg slots
+            q = oz * a.PT + (j - oz * a.TY) * a.WP + kPadX;
+        } else {                  // runs through each plane's rows, advancing adv slots
             const int per_plane = (a.TY * a.WP + a.adv - 1) / a.adv;
             oz = j / per_plane;
-            q = oz * a.PT + a.adv * (j - oz * per_plane) - a.mg;
+            q = oz * a.PT + a.adv * (j - oz * per_plane);
         }
         s_q[j] = q;
         s_oz[j] = oz;
-        // A operand of tile j at stage 0, centre tap: slot kGuard + halo (PT + WP) + q
-        s_adesc[j] = smem_desc(sbase + (uint32_t)(kGuard + (TAPS == 27 ? a.PT + a.WP : 0) + q) * 16,
-                               (uint32_t)a.half_bytes, 128);
+        // A operand of tile j at stage 0, centre tap: slot halo (PT + WP) + q, K-major with
+        // 32-byte swizzled rows (layout type 6), 8-row groups 256 B apart
+        s_adesc[j] = smem_desc(sbase + (uint32_t)((TAPS == 27 ? a.PT + a.WP : 0) + q) * kRowBytes, 16, 256) |
+                     ((uint64_t)6 << 61);
     }
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&bars[s]), kLoadWarps * 32);   // full: every loader thread
+            mbar_init(smem_u32(&bars[s]), kLoadWarps * 32);   // full: every loader thread (one with the box's bytes)
             mbar_init(smem_u32(&bars[2 + s]), kMmaWarps);     // empty: one commit per issuer
             mbar_init(smem_u32(&bars[4 + s]), kMmaWarps);     // accumulator full: likewise
             mbar_init(smem_u32(&bars[6 + s]), 4);      // accumulator empty: 4 epilogue warps
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     if (warp < 4)
         role_epilogue<OT>(a, tmem, s_q, s_oz, s_xch, accf0, acce0, &s_abort);
     else if (warp < kMmaWarp0)
-        role_load<TAPS>(a, sbase, full0, empty0, &s_abort);
+        role_load<TAPS>(&xmap, a, sbase, full0, empty0, &s_abort);
     else if ((tid & 31) == 0)
         role_mma<TAPS>(a, warp - kMmaWarp0, sbase, tmem, s_adesc, full0, empty0, accf0, acce0, &s_abort);
 
@@ -403,8 +403,11 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
 {
     if (W % 8 != 0 || Cin % 16 || Cout % 16 || Cout > 256 || sms < 1) return false;
     if (taps != 1 && taps != 27) return false;
-    const int halo = taps == 27 ? 1 : 0, NX = taps == 27 ? 3 : 1, WP = W + 8, nc = Cin / 16;
-    const int rowtile = W == 128, mg = (taps == 27 && !rowtile) ? 1 : 0, adv = 128 - 2 * mg;
+    // rows of WP slots, x = -8 .. W + 7 (one TMA box dimension: at most 256); margin tiles
+    // advance by whole 8-slot swizzle atoms
+    const int halo = taps == 27 ? 1 : 0, NX = taps == 27 ? 3 : 1, WP = W + 2 * kPadX, nc = Cin / 16;
+    if (WP > 256) return false;
+    const int rowtile = W == 128, mg = (taps == 27 && !rowtile) ? 1 : 0, adv = mg ? 120 : 128;
     double best = 0.0;
     bool found = false;
     for (int Nt = Cout; Nt >= 16; Nt -= 16) {
@@ -416,28 +419,30 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
                 int T, qmax;
                 if (rowtile) {
                     T = TZ * TY;
-                    qmax = (TZ - 1) * PT + (TY - 1) * WP;
+                    qmax = (TZ - 1) * PT + (TY - 1) * WP + kPadX;
                 } else {
                     const int per = (TY * WP + adv - 1) / adv;
                     T = TZ * per;
-                    qmax = (TZ - 1) * PT + (per - 1) * adv - mg;
+                    qmax = (TZ - 1) * PT + (per - 1) * adv;
                 }
                 if (T > kMaxTiles || 2 * T * NX * Nt > 512) continue;     // two accumulators
-                const int64_t maxslot = kGuard + halo * (PT + WP) + qmax + 127 + (halo ? PT + WP : 0);
-                int64_t hs = kGuard + NSX > maxslot + 1 ? kGuard + NSX : maxslot + 1;
+                // rows past the TMA box (read only by discarded outputs) are slack
+                const int64_t maxslot = halo * (PT + WP) + qmax + 127 + (halo ? PT + WP : 0);
+                int64_t hs = NSX > maxslot + 1 ? NSX : maxslot + 1;
                 hs = (hs + 7) / 8 * 8;
-                const int64_t half_bytes = hs * 16;
-                if (half_bytes >= (1 << 18)) continue;          // descriptor LBO / address range
-                int64_t stage = 2 * half_bytes + (int64_t)taps * Nt * 32;
+                const int64_t a_bytes = hs * kRowBytes;
+                if (a_bytes >= (1 << 18)) continue;             // descriptor address range
+                int64_t stage = a_bytes + (int64_t)taps * Nt * 32;
                 stage = (stage + 1023) / 1024 * 1024;
                 if (2 * stage > kSmemLimit) continue;
                 // cycles per work item: each issuer keeps one MMA (~185 cycles) in flight and
-                // the pipe sustains about 11.5 cycles per 128 x 16 x 16; staging moves about
-                // 24 B/cycle/SM; the epilogue about 200 cycles per 16 channels of a tile
+                // the pipe sustains about 11.5 cycles per 128 x 16 x 16; TMA boxes of 32-byte
+                // rows move about 40 B/cycle/SM; the epilogue about 200 cycles per 16
+                // channels of a tile
                 const double issue = (double)((T + kMmaWarps - 1) / kMmaWarps) * 185.0;
                 const double pipe = (double)T * NX * Nt / 16.0 * 11.5;
                 const double mma = (double)nc * (taps / NX) * (issue > pipe ? issue : pipe);
-                const double load = (double)nc * stage / 24.0;
+                const double load = (double)nc * stage / 40.0;
                 const double epi = (double)T * Nt / 16.0 * 200.0;
                 double cost = mma > load ? mma : load;
                 cost = (cost > epi ? cost : epi) + 500.0;
@@ -450,7 +455,8 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
                     while (ncols < 2 * T * NX * Nt) ncols <<= 1;
                     pl->TZ = TZ; pl->TY = TY; pl->Nt = Nt; pl->T = T; pl->WP = WP; pl->PT = PT;
                     pl->NX = NX; pl->rowtile = rowtile; pl->mg = mg; pl->adv = adv;
-                    pl->half_bytes = (int)half_bytes;
+                    pl->a_bytes = (int)a_bytes;
+                    pl->box_bytes = (int)(NSX * kRowBytes);
                     pl->stage_bytes = (int)stage;
                     pl->ncols = ncols;
                     pl->ry = (H + TY - 1) / TY;
@@ -467,7 +473,21 @@ cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias,
 {
     const int sms = sm_count();
     ConvHaloPlan pl;
-    if (!plan_conv3d_halo(D, H, W, Cin, Cout, taps, sms, &pl)) return cudaErrorNotSupported;
+    if (((uintptr_t)X & 15) || !plan_conv3d_halo(D, H, W, Cin, Cout, taps, sms, &pl)) return cudaErrorNotSupported;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    // the input tile of a region: box {16 channels, WP x from -8, TY (+ 2) rows, TZ (+ 2)
+    // planes}, 32-byte swizzle, zero fill outside the volume
+    const int halo = taps == 27 ? 1 : 0;
+    CUtensorMap xmap;
+    const cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+    const cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+    const cuuint32_t box[4] = {16, (cuuint32_t)pl.WP, (cuuint32_t)(pl.TY + 2 * halo), (cuuint32_t)(pl.TZ + 2 * halo)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(X), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorNotSupported;
     HaloArgs a;
     a.X = (const __nv_bfloat16 *)X;
     a.Wt = (const __nv_bfloat16 *)Wt;
@@ -477,7 +497,7 @@ cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias,
     a.D = D; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.relu = relu;
     a.TZ = pl.TZ; a.TY = pl.TY; a.WP = pl.WP; a.PT = pl.PT; a.T = pl.T; a.Nt = pl.Nt;
     a.NX = pl.NX; a.rowtile = pl.rowtile; a.mg = pl.mg; a.adv = pl.adv;
-    a.half_bytes = pl.half_bytes; a.stage_bytes = pl.stage_bytes;
+    a.a_bytes = pl.a_bytes; a.box_bytes = pl.box_bytes; a.stage_bytes = pl.stage_bytes;
     a.ncols = pl.ncols;
     a.ry = pl.ry; a.nslice = pl.nslice; a.nitems = pl.nitems;
     // at least 116 KB of shared memory keeps one block per SM, so TMEM is never oversubscribed
@@ -489,7 +509,7 @@ cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias,
     do {                                                                                                       \
         e = cudaFuncSetAttribute(conv3d_halo_kernel<T, OT>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                  (int)smem);                                                                   \
-        if (e == cudaSuccess) conv3d_halo_kernel<T, OT><<<grid, kHaloThreads, smem, s>>>(a);              \
+        if (e == cudaSuccess) conv3d_halo_kernel<T, OT><<<grid, kHaloThreads, smem, s>>>(xmap, a);        \
     } while (0)
     if (taps == 27) {
         if (out_f32) VAMRT_HALO(27, float); else VAMRT_HALO(27, __nv_bfloat16);

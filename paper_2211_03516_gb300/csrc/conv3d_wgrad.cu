@@ -244,21 +244,6 @@ int sm_count_wgrad()
     return sms;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
-
 // TMA-fed kernel: stages of 64 positions where W allows (else 32), the largest tile group
 // whose ring of three slots and accumulators fit two blocks per SM (else one); returns
 // cudaErrorNotSupported for what it cannot take
@@ -267,7 +252,7 @@ cudaError_t launch_wgrad_tma(const void *X, const void *dY, float *dW, int D, in
 {
     const long long P = (long long)D * H * W;
     if (((uintptr_t)X & 15) || ((uintptr_t)dY & 15) || P >= (1ll << 31)) return cudaErrorNotSupported;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
     if (!enc) return cudaErrorNotSupported;
     TmaArgs a{};
     a.dW = dW;
@@ -336,6 +321,21 @@ cudaError_t launch_wgrad_tma(const void *X, const void *dY, float *dW, int D, in
 }
 
 }  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
 
 cudaError_t launch_conv3d_wgrad_tc(const void *X, const void *dY, float *dW, int D, int H, int W, int Cin, int Cout,
                                    int taps, int *err, cudaStream_t s)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "../../include/vamrt.h"
@@ -122,10 +123,14 @@ cudaError_t launch_ramlak(const float *in, float *out, int64_t rows, int nu, dou
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s);
 
+// conv3d_wgrad.cu: the driver's tensor-map encoder (cuTensorMapEncodeTiled, through the
+// runtime's driver entry point); NULL when the driver does not provide it
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder();
+
 // conv3d_halo.cu (persistent halo-tile variant; W % 8 == 0).  launch returns
 // cudaErrorNotSupported for shapes it does not take.
 struct ConvHaloPlan {
-    int TZ, TY, Nt, T, WP, PT, NX, rowtile, mg, adv, half_bytes, stage_bytes, ncols, ry, nslice, nitems;
+    int TZ, TY, Nt, T, WP, PT, NX, rowtile, mg, adv, a_bytes, box_bytes, stage_bytes, ncols, ry, nslice, nitems;
 };
 bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms, ConvHaloPlan *pl);
 cudaError_t launch_conv3d_halo(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
