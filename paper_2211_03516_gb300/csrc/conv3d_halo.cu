@@ -4,16 +4,15 @@
 //   Y[p][co] = act( bias[co] + sum_{t, ci} X[p + off(t)][ci] * Wt[co][t][ci] )
 //
 // Same operation and layouts as conv3d_tc.cu (X [D][H][W][Cin] bf16, Wt [Cout][taps][Cin],
-// Y [D][H][W][Cout] bf16 or fp32, zero padding); this kernel needs W % 8 == 0.
+// Y [D][H][W][Cout] bf16 or fp32, zero padding); this kernel needs W % 8 == 0, W <= 240
+// (a row is one TMA box dimension) and a 16-byte aligned X.
 //
 // Slot layout.  A work item is a region of TZ output planes x TY output rows x all W
 // columns (and a slice of Nt output channels).  Its input tile -- (TZ + 2) planes x
-// (TY + 2) rows with the one-voxel halo -- is staged one 16-channel chunk at a time as two
-// 8-channel halves; each half is a run of 16-byte "slots" (8 bf16 channels of one voxel).
-// A row takes WP = W + 8 slots: W voxels, then 8 zero slots, which are at once the x = W
-// neighbour of this row and the x = -1 neighbour of the next (8 zero guard slots precede
-// the first row).  Pads and guard are zeroed once per launch; halo rows and planes outside
-// the volume are zero-filled by the copies.
+// (TY + 2) rows with the one-voxel halo -- is staged one 16-channel chunk at a time as a
+// run of 32-byte "slots" (16 bf16 channels of one voxel).  A row takes WP = W + 16 slots,
+// x = -8 .. W + 7: voxel x sits in slot x + 8, and the zero slots around it are its x = -1
+// and x = W neighbours.
 //
 // GEMM mapping.  M = 128 consecutive slots of the region (TMEM lanes), K = 16 channels per
 // MMA.  Because the slot index is linear in (z, y, x), the A operand of taps (dz, dy, *)
@@ -21,22 +20,23 @@
 // descriptor per (tile, dz, dy), no data movement.  The three dx taps share that A and are
 // stacked in N (N = 3 Nt: columns dx, then output channel), so row m of the accumulator
 // holds, per dx, the (dz, dy)-summed product at slot m; the epilogue forms
-// Y[m] = D[m - 1][dx = -1] + D[m][0] + D[m + 1][+1].  A core matrix is 8 consecutive slots
-// (128 contiguous bytes); SBO = 128 B, LBO = the distance between the two halves.  For
-// W = 128 a tile is one row (its neighbours beyond the tile are pads); otherwise tiles run
-// through each plane's rows 126 slots apart with one margin row at either end.  Rows in
+// Y[m] = D[m - 1][dx = -1] + D[m][0] + D[m + 1][+1].  A is K-major in the 32-byte swizzle
+// (8-slot atoms of 256 bytes, SBO = 256 B); every tile start and shift is a whole atom.
+// For W = 128 a tile is one row (its neighbours beyond the tile are pads); otherwise tiles
+// run through each plane's rows 120 slots apart with one margin row at either end.  Rows in
 // padding or beyond the region are computed and discarded.  B (weights of one chunk, all
-// taps) is staged in the canonical K-major layout.
+// taps) is staged in the canonical K-major no-swizzle layout.
 //
-// Staging is by cp.async from four loader warps: pairs of lanes move the 32 bytes of a
-// voxel's 16-channel chunk, so each warp instruction is one coalesced 512-byte run.  (A
-// tensor-map box over channels-last activations moves 16-byte elements -- one half of one
-// voxel -- and was no faster here.)
+// Staging: one TMA tile load per chunk, box {16 channels, WP x from -8, TY + 2 rows, TZ + 2
+// planes}, writes the whole input tile in that swizzled layout; its zero fill supplies the
+// row pads and the halo outside the volume.  The weights come by cp.async from four loader
+// warps.  (Boxes of 16-byte rows -- 8 channels -- and cp.async copies of the tile both moved
+// about 24 B/cycle/SM; 32-byte rows roughly double that.)
 //
 // Roles (384 threads): warps 0-3 drain TMEM (warp w owns lanes 32w..32w+31) and write Y;
-// warps 4-7 copy input tiles and weights into two shared-memory stages; lane 0 of each of
-// warps 8-11 issues the MMAs of every fourth tile.  Two TMEM accumulators let the epilogue
-// of one region overlap the MMAs of the next.  Every wait is bounded: on timeout the block
+// warps 4-7 stage input tiles (TMA) and weights (cp.async) into two shared-memory stages;
+// lane 0 of each of warps 8-11 issues the MMAs of every fourth tile.  Two TMEM accumulators
+// let the epilogue of one region overlap the MMAs of the next.  Every wait is bounded: on timeout the block
 // sets the error flag, the other roles run out of their own waits, TMEM is freed and the
 // block returns.
 #include <cuda_bf16.h>
