@@ -33,12 +33,12 @@
 // warps.  (Boxes of 16-byte rows -- 8 channels -- and cp.async copies of the tile both moved
 // about 24 B/cycle/SM; 32-byte rows roughly double that.)
 //
-// Roles (384 threads): warps 0-3 drain TMEM (warp w owns lanes 32w..32w+31) and write Y;
-// warps 4-7 stage input tiles (TMA) and weights (cp.async) into two shared-memory stages;
-// lane 0 of each of warps 8-11 issues the MMAs of every fourth tile.  Two TMEM accumulators
-// let the epilogue of one region overlap the MMAs of the next.  Every wait is bounded: on timeout the block
-// sets the error flag, the other roles run out of their own waits, TMEM is freed and the
-// block returns.
+// Roles (512 threads): warps 0-7 drain TMEM in two sets of four, alternate tiles (warp
+// 4 s + w owns lanes 32w..32w+31) and write Y; warps 8-11 stage input tiles (TMA) and
+// weights (cp.async) into two shared-memory stages; lane 0 of each of warps 12-15 issues
+// the MMAs of every fourth tile.  Two TMEM accumulators let the epilogue of one region
+// overlap the MMAs of the next.  Every wait is bounded: on timeout the block sets the error
+// flag, the other roles run out of their own waits, TMEM is freed and the block returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -50,8 +50,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int kLoadWarp0 = 4, kLoadWarps = 4, kMmaWarp0 = 8, kMmaWarps = 4;
-constexpr int kHaloThreads = 384;   // 4 epilogue warps, 4 loader warps, 4 MMA warps
+constexpr int kEpiSets = 2;         // epilogue warp sets of 4 (one per TMEM lane quarter)
+constexpr int kLoadWarp0 = 4 * kEpiSets, kLoadWarps = 4, kMmaWarp0 = kLoadWarp0 + kLoadWarps, kMmaWarps = 4;
+constexpr int kHaloThreads = 32 * (kMmaWarp0 + kMmaWarps);   // 8 epilogue, 4 loader, 4 MMA warps
 constexpr int kPadX = 8;           // zero slots ahead of x = 0 in every staged row (x = -8 .. -1)
 constexpr int kRowBytes = 32;      // one staged slot: 16 bf16 channels of one voxel
 constexpr int kMaxTiles = 32;
@@ -216,37 +217,40 @@ __device__ __forceinline__ void store16(OT *dst, const uint32_t *v, const float 
     }
 }
 
-// all 128 epilogue threads (warps 0-3) agree on a flag (named barrier 1)
-__device__ __forceinline__ bool epi_all(bool v)
+// the 128 threads of epilogue set `set` (warps 4 set .. 4 set + 3) agree on a flag
+// (named barrier 1 + set)
+__device__ __forceinline__ bool epi_all(bool v, int set)
 {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "bar.red.and.pred q, %2, 128, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "r"(1 + set)
         : "memory");
     return r != 0;
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync(int set) { asm volatile("bar.sync %0, 128;" ::"r"(1 + set) : "memory"); }
 
-// warps 0-3: TMEM -> Y.  Row m of a tile holds, for each dx, the (dz, dy)-summed partial
-// product of slot m; output slot m takes D[m - 1][dx = -1] + D[m][0] + D[m + 1][+1]
+// warps 0-7: TMEM -> Y, two sets of four warps taking alternate tiles (warp 4 s + w of set
+// s reads TMEM lane quarter w).  Row m of a tile holds, for each dx, the (dz, dy)-summed
+// partial product of slot m; output slot m takes D[m - 1][dx = -1] + D[m][0] + D[m + 1][+1]
 // (warp shuffles, and shared memory across the warps' 32-row boundaries).  Rows beyond a
 // tile are pads (zero) for one-row tiles and are never outputs for margin tiles.
 template <typename OT>
 __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, const int *s_oz, float *s_xch,
                               uint32_t accf0, uint32_t acce0, volatile int *abort_flag)
 {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int set = threadIdx.x >> 7, tid = threadIdx.x & 127, warp = tid >> 5, lane = tid & 31;
     const int NN = a.NX * a.Nt;
+    float *xch = s_xch + set * 256;
     int k = 0, step = 0;
     for (int item = blockIdx.x; item < a.nitems; item += gridDim.x, ++k) {
         const int b = k & 1;
         const bool ok = mbar_wait(accf0 + 8 * b, (k >> 1) & 1) && !*abort_flag;
-        if (!epi_all(ok)) {
+        if (!epi_all(ok, set)) {
             if (tid == 0) halo_fail(abort_flag, a.err);
             return;
         }
@@ -254,7 +258,7 @@ __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, 
         const int slice = item % a.nslice, r = item / a.nslice;
         const int z0 = (r / a.ry) * a.TZ, y0 = (r % a.ry) * a.TY, co0 = slice * a.Nt;
         const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * a.T * NN);
-        for (int j = 0; j < a.T; ++j) {
+        for (int j = set; j < a.T; j += kEpiSets) {
             const int q = s_q[j] + tid;
             const int oz = q >= 0 ? q / a.PT : -1, rem = q - oz * a.PT, oy = rem / a.WP, x = rem - oy * a.WP - kPadX;
             const int z = z0 + oz, y = y0 + oy;
@@ -274,7 +278,7 @@ __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, 
                     // warp publishes its dx = -1 part, lane 0 its dx = +1 part; every lane then
                     // reads both edges (broadcast) and selects without branching, so the
                     // shuffle loop has no divergent shared-memory loads to wait on
-                    uint4 *xm = (uint4 *)(s_xch + (step & 1) * 128), *xp = xm + 16;   // [warp][4] x 16 B
+                    uint4 *xm = (uint4 *)(xch + (step & 1) * 128), *xp = xm + 16;   // [warp][4] x 16 B
                     if (lane == 31)
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
@@ -283,7 +287,7 @@ __device__ void role_epilogue(const HaloArgs &a, uint32_t tmem, const int *s_q, 
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
                             xp[warp * 4 + i] = make_uint4(dp[4 * i], dp[4 * i + 1], dp[4 * i + 2], dp[4 * i + 3]);
-                    epi_sync();
+                    epi_sync(set);
                     uint32_t el[16], er[16];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     __shared__ uint32_t s_tmem;
     __shared__ int s_q[kMaxTiles], s_oz[kMaxTiles];
     __shared__ uint64_t s_adesc[kMaxTiles];
-    __shared__ __align__(16) float s_xch[256];   // epilogue warp-boundary exchange, two buffers
+    __shared__ __align__(16) float s_xch[256 * kEpiSets];   // epilogue warp-boundary exchange, two buffers per set
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
             mbar_init(smem_u32(&bars[s]), kLoadWarps * 32);   // full: every loader thread (one with the box's bytes)
             mbar_init(smem_u32(&bars[2 + s]), kMmaWarps);     // empty: one commit per issuer
             mbar_init(smem_u32(&bars[4 + s]), kMmaWarps);     // accumulator full: likewise
-            mbar_init(smem_u32(&bars[6 + s]), 4);      // accumulator empty: 4 epilogue warps
+            mbar_init(smem_u32(&bars[6 + s]), 4 * kEpiSets);   // accumulator empty: every epilogue warp
         }
         mbar_init_fence();
         s_abort = 0;
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(kHaloThreads, 1)
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[2]);
     const uint32_t accf0 = smem_u32(&bars[4]), acce0 = smem_u32(&bars[6]);
 
-    if (warp < 4)
+    if (warp < kLoadWarp0)
         role_epilogue<OT>(a, tmem, s_q, s_oz, s_xch, accf0, acce0, &s_abort);
     else if (warp < kMmaWarp0)
         role_load<TAPS>(&xmap, a, sbase, full0, empty0, &s_abort);
@@ -437,13 +441,13 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
                 if (2 * stage > kSmemLimit) continue;
                 // cycles per work item: each issuer keeps one MMA (~185 cycles) in flight and
                 // the pipe sustains about 11.5 cycles per 128 x 16 x 16; TMA boxes of 32-byte
-                // rows move about 40 B/cycle/SM; the epilogue about 200 cycles per 16
-                // channels of a tile
+                // rows move about 40 B/cycle/SM; an epilogue set takes about 2000 cycles per
+                // 16 channels of a tile, two sets in parallel
                 const double issue = (double)((T + kMmaWarps - 1) / kMmaWarps) * 185.0;
                 const double pipe = (double)T * NX * Nt / 16.0 * 11.5;
                 const double mma = (double)nc * (taps / NX) * (issue > pipe ? issue : pipe);
                 const double load = (double)nc * stage / 40.0;
-                const double epi = (double)T * Nt / 16.0 * 200.0;
+                const double epi = (double)T * Nt / 16.0 * 2000.0 / kEpiSets;
                 double cost = mma > load ? mma : load;
                 cost = (cost > epi ? cost : epi) + 500.0;
                 const int64_t nreg = (int64_t)((D + TZ - 1) / TZ) * ((H + TY - 1) / TY) * (Cout / Nt);
