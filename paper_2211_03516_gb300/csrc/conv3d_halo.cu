@@ -439,11 +439,14 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
                 int64_t stage = a_bytes + (int64_t)taps * Nt * 32;
                 stage = (stage + 1023) / 1024 * 1024;
                 if (2 * stage > kSmemLimit) continue;
-                // cycles per work item: each issuer keeps one MMA (~185 cycles) in flight and
-                // the pipe sustains about 11.5 cycles per 128 x 16 x 16; TMA boxes of 32-byte
-                // rows move about 40 B/cycle/SM; an epilogue set takes about 2000 cycles per
-                // 16 channels of a tile, two sets in parallel
-                const double issue = (double)((T + kMmaWarps - 1) / kMmaWarps) * 185.0;
+                // cycles per work item: an MMA into the accumulator of the issuer's previous
+                // one waits about 470 cycles (in-kernel timers), independent ones (the issuer's
+                // other tiles) issue about 175 cycles apart, and the pipe sustains about 11.5
+                // cycles per 128 x 16 x 16; TMA boxes of 32-byte rows move about 40 B/cycle/SM;
+                // an epilogue set takes about 2000 cycles per 16 channels of a tile, two sets
+                // in parallel
+                const double per_issuer = (double)((T + kMmaWarps - 1) / kMmaWarps) * 175.0;
+                const double issue = per_issuer > 470.0 ? per_issuer : 470.0;
                 const double pipe = (double)T * NX * Nt / 16.0 * 11.5;
                 const double mma = (double)nc * (taps / NX) * (issue > pipe ? issue : pipe);
                 const double load = (double)nc * stage / 40.0;
