@@ -33,10 +33,11 @@
 // warps.  (Boxes of 16-byte rows -- 8 channels -- and cp.async copies of the tile both moved
 // about 24 B/cycle/SM; 32-byte rows roughly double that.)
 //
-// Roles (512 threads): warps 0-7 drain TMEM in two sets of four, alternate tiles (warp
+// Roles (544 threads): warps 0-7 drain TMEM in two sets of four, alternate tiles (warp
 // 4 s + w owns lanes 32w..32w+31) and write Y; warps 8-11 stage input tiles (TMA) and
-// weights (cp.async) into two shared-memory stages; lane 0 of each of warps 12-15 issues
-// the MMAs of every fourth tile.  Two TMEM accumulators let the epilogue of one region
+// weights (cp.async) into two shared-memory stages; lane 0 of each of warps 12-16 issues
+// the MMAs of every fifth tile (a tile's MMAs form one dependent chain into its
+// accumulator, so more issuers mean more chains in flight).  Two TMEM accumulators let the epilogue of one region
 // overlap the MMAs of the next.  Every wait is bounded: on timeout the block sets the error
 // flag, the other roles run out of their own waits, TMEM is freed and the block returns.
 #include <cuda_bf16.h>
@@ -51,8 +52,8 @@ namespace {
 using namespace tc;
 
 constexpr int kEpiSets = 2;         // epilogue warp sets of 4 (one per TMEM lane quarter)
-constexpr int kLoadWarp0 = 4 * kEpiSets, kLoadWarps = 4, kMmaWarp0 = kLoadWarp0 + kLoadWarps, kMmaWarps = 4;
-constexpr int kHaloThreads = 32 * (kMmaWarp0 + kMmaWarps);   // 8 epilogue, 4 loader, 4 MMA warps
+constexpr int kLoadWarp0 = 4 * kEpiSets, kLoadWarps = 4, kMmaWarp0 = kLoadWarp0 + kLoadWarps, kMmaWarps = 5;
+constexpr int kHaloThreads = 32 * (kMmaWarp0 + kMmaWarps);   // 8 epilogue, 4 loader, 5 MMA warps
 constexpr int kPadX = 8;           // zero slots ahead of x = 0 in every staged row (x = -8 .. -1)
 constexpr int kRowBytes = 32;      // one staged slot: 16 bf16 channels of one voxel
 constexpr int kMaxTiles = 32;
