@@ -37,9 +37,10 @@
 // 4 s + w owns lanes 32w..32w+31) and write Y; warps 8-11 stage input tiles (TMA) and
 // weights (cp.async) into two shared-memory stages; lane 0 of each of warps 12-16 issues
 // the MMAs of every fifth tile (a tile's MMAs form one dependent chain into its
-// accumulator, so more issuers mean more chains in flight).  Two TMEM accumulators let the epilogue of one region
-// overlap the MMAs of the next.  Every wait is bounded: on timeout the block sets the error
-// flag, the other roles run out of their own waits, TMEM is freed and the block returns.
+// accumulator, so more issuers mean more chains in flight).  Two TMEM accumulators let
+// the epilogue of one region overlap the MMAs of the next.  Every wait is bounded: on
+// timeout the block sets the error flag, the other roles run out of their own waits, TMEM
+// is freed and the block returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
