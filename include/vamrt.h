@@ -322,6 +322,28 @@ vamrt_status vamrt_conv3d_tiling(int32_t d, int32_t h, int32_t wd, int32_t cin, 
                                  int32_t *out);
 
 /*
+ * Host-only planning queries (no device, no launch): the tiling the convolution kernels use
+ * for a shape on a GPU with `sms` SMs, written to a host array.
+ * vamrt_conv3d_halo_plan: out[18] = {planned (0: the gather kernel takes the shape), TZ,
+ *   TY, Nt (output channels per work item), T (M tiles per region), WP (slots per staged
+ *   row), PT (slots per staged plane), NX (dx taps stacked in N), rowtile, mg (margin
+ *   rows), adv (slots between tiles), a_bytes (staged input tile with slack), box_bytes
+ *   (its TMA box), stage_bytes, ncols (TMEM), ry (regions along y), nslice, nitems}.
+ * vamrt_conv3d_wgrad_plan: out[17] = {planned, Mtot (taps x cin), nmt (M tiles), tpg
+ *   (tiles per group), kp (accumulators per tile), KS (positions per stage), BX (positions
+ *   per X box), nstage, cwA, cwB (channels per column block of X and dy), slots,
+ *   slot_bytes, per_sm (blocks per SM), ncols (TMEM), ngroups, nsplit, spb (stages per
+ *   block)}.
+ * Errors: EINVAL (NULL out, sms < 1, empty volume); an unsupported shape returns VAMRT_OK
+ * with out[0] = 0.
+ */
+vamrt_status vamrt_conv3d_halo_plan(int32_t d, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                    int32_t sms, int32_t *out);
+vamrt_status vamrt_conv3d_wgrad_plan(int32_t d, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                     int32_t sms, int32_t *out);
+
+
+/*
  * Building blocks of the learned warm start (a 3D U-Net on the projection stack; the paper
  * has no such network -- its optimiser starts from the target, Sec. 2.7).  Activations are
  * channels-last BF16 [d][h][w][c] device arrays; gradients of weights and biases are FP32.

@@ -254,40 +254,15 @@ cudaError_t launch_wgrad_tma(const void *X, const void *dY, float *dW, int D, in
     if (((uintptr_t)X & 15) || ((uintptr_t)dY & 15) || P >= (1ll << 31)) return cudaErrorNotSupported;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
     if (!enc) return cudaErrorNotSupported;
+    WgradPlan pl;
+    if (!plan_wgrad_tma(D, H, W, Cin, Cout, taps, sm_count_wgrad(), &pl)) return cudaErrorNotSupported;
     TmaArgs a{};
     a.dW = dW;
     a.err = err;
     a.D = D; a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.taps = taps;
-    a.Mtot = taps * Cin;
-    a.nmt = (a.Mtot + 127) / 128;
-    a.KS = W % 64 == 0 ? 64 : 32;
-    a.BX = W % a.KS == 0 ? a.KS : 16;
-    a.nstage = (int)((P + a.KS - 1) / a.KS);
-    a.cwA = Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16;
-    a.cwB = Cout % 64 == 0 ? 64 : Cout % 32 == 0 ? 32 : 16;
-    int per_sm = 0;
-    for (int bps = 2; bps >= 1 && !per_sm; --bps) {
-        const size_t budget = bps == 2 ? 108 * 1024 : 220 * 1024;
-        for (int tpg = std::min(kMaxTpg, std::min(a.nmt, (512 / bps) / Cout)); tpg >= 1; --tpg) {
-            const int ng = (a.nmt + tpg - 1) / tpg;
-            const int t2 = (a.nmt + ng - 1) / ng;
-            const int slot = ((Cout + 128 * t2) * a.KS * 2 + 1023) / 1024 * 1024;
-            const int slots = std::min(kTMaxSlots, (int)(budget / slot));
-            if (slots < 3) continue;
-            int kp = std::min(a.KS / 16, std::max(1, kTIssuers / t2));
-            while (kp > 1 && t2 * kp * Cout > 512 / bps) --kp;
-            a.tpg = t2;
-            a.kp = kp;
-            a.slots = slots;
-            a.slot_bytes = slot;
-            per_sm = bps;
-            break;
-        }
-    }
-    if (!per_sm) return cudaErrorNotSupported;
-    int ncols = 32;
-    while (ncols < a.tpg * a.kp * Cout) ncols <<= 1;
-    a.ncols = ncols;
+    a.Mtot = pl.Mtot; a.nmt = pl.nmt; a.tpg = pl.tpg; a.kp = pl.kp;
+    a.KS = pl.KS; a.BX = pl.BX; a.nstage = pl.nstage; a.spb = pl.spb;
+    a.slots = pl.slots; a.slot_bytes = pl.slot_bytes; a.cwA = pl.cwA; a.cwB = pl.cwB; a.ncols = pl.ncols;
 
     CUtensorMap xmap, ymap;
     const cuuint64_t xdims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
@@ -308,19 +283,62 @@ cudaError_t launch_wgrad_tma(const void *X, const void *dY, float *dW, int D, in
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
 
-    const int ngroups = (a.nmt + a.tpg - 1) / a.tpg;
-    const int target = per_sm * sm_count_wgrad();
-    int nsplit = std::max(1, target / ngroups);      // at most one wave
-    a.spb = (a.nstage + nsplit - 1) / nsplit;
-    nsplit = (a.nstage + a.spb - 1) / a.spb;
     const size_t smem = (size_t)a.slots * a.slot_bytes;
     cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    conv3d_wgrad_tma_kernel<<<dim3(ngroups, nsplit), kTThreads, smem, s>>>(xmap, ymap, a);
+    conv3d_wgrad_tma_kernel<<<dim3(pl.ngroups, pl.nsplit), kTThreads, smem, s>>>(xmap, ymap, a);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+// Plan of the TMA-fed weight gradient: stages of 64 positions where W allows (else 32;
+// boxes of BX positions, BX dividing W and KS), column blocks of cwA / cwB channels (the
+// widest of 64, 32, 16 dividing Cin / Cout), the largest tile group whose ring of three
+// or four slots and accumulators fit two blocks per SM (else one), groups balanced in
+// size, and the positions split so that the grid is at most one wave.
+bool plan_wgrad_tma(int D, int H, int W, int Cin, int Cout, int taps, int sms, WgradPlan *pl)
+{
+    if (W < 16 || W % 16 || Cin % 16 || Cout % 16 || Cout > 256 || sms < 1 || (taps != 1 && taps != 27))
+        return false;
+    const long long P = (long long)D * H * W;
+    if (P < 1 || P >= (1ll << 31)) return false;
+    WgradPlan a{};
+    a.Mtot = taps * Cin;
+    a.nmt = (a.Mtot + 127) / 128;
+    a.KS = W % 64 == 0 ? 64 : 32;
+    a.BX = W % a.KS == 0 ? a.KS : 16;
+    a.nstage = (int)((P + a.KS - 1) / a.KS);
+    a.cwA = Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16;
+    a.cwB = Cout % 64 == 0 ? 64 : Cout % 32 == 0 ? 32 : 16;
+    for (int bps = 2; bps >= 1 && !a.per_sm; --bps) {
+        const int budget = bps == 2 ? 108 * 1024 : 220 * 1024;
+        for (int tpg = std::min(kMaxTpg, std::min(a.nmt, (512 / bps) / Cout)); tpg >= 1; --tpg) {
+            const int ng = (a.nmt + tpg - 1) / tpg;
+            const int t2 = (a.nmt + ng - 1) / ng;
+            const int slot = ((Cout + 128 * t2) * a.KS * 2 + 1023) / 1024 * 1024;
+            const int slots = std::min(kTMaxSlots, budget / slot);
+            if (slots < 3) continue;
+            int kp = std::min(a.KS / 16, std::max(1, kTIssuers / t2));
+            while (kp > 1 && t2 * kp * Cout > 512 / bps) --kp;
+            a.tpg = t2;
+            a.kp = kp;
+            a.slots = slots;
+            a.slot_bytes = slot;
+            a.per_sm = bps;
+            break;
+        }
+    }
+    if (!a.per_sm) return false;
+    a.ncols = 32;
+    while (a.ncols < a.tpg * a.kp * Cout) a.ncols <<= 1;
+    a.ngroups = (a.nmt + a.tpg - 1) / a.tpg;
+    a.nsplit = std::max(1, a.per_sm * sms / a.ngroups);      // at most one wave
+    a.spb = (a.nstage + a.nsplit - 1) / a.nsplit;
+    a.nsplit = (a.nstage + a.spb - 1) / a.spb;
+    *pl = a;
+    return true;
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 tma_encoder()
 {

@@ -123,6 +123,13 @@ cudaError_t launch_ramlak(const float *in, float *out, int64_t rows, int nu, dou
 cudaError_t launch_conv3d_tc(const void *X, const void *Wt, const float *bias, void *Y, int out_f32, int D, int H,
                              int W, int Cin, int Cout, int taps, int relu, int *err, cudaStream_t s);
 
+// conv3d_wgrad.cu: plan of the TMA-fed weight gradient (host only; false for shapes it
+// cannot take)
+struct WgradPlan {
+    int Mtot, nmt, tpg, kp, KS, BX, nstage, cwA, cwB, slots, slot_bytes, per_sm, ncols, ngroups, nsplit, spb;
+};
+bool plan_wgrad_tma(int D, int H, int W, int Cin, int Cout, int taps, int sms, WgradPlan *pl);
+
 // conv3d_wgrad.cu: the driver's tensor-map encoder (cuTensorMapEncodeTiled, through the
 // runtime's driver entry point); NULL when the driver does not provide it
 PFN_cuTensorMapEncodeTiled_v12000 tma_encoder();

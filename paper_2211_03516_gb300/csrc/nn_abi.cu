@@ -36,6 +36,32 @@ vamrt_status vamrt_conv3d_wgrad_bf16(const void *x, const void *dy, float *dw, i
                                                      (cudaStream_t)stream));
 }
 
+vamrt_status vamrt_conv3d_halo_plan(int32_t d, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                    int32_t sms, int32_t *out)
+{
+    if (!out || sms < 1 || d < 1 || h < 1 || wd < 1) return einval("NULL out, sms < 1 or empty volume");
+    vamrt::ConvHaloPlan pl;
+    for (int i = 0; i < 18; ++i) out[i] = 0;
+    if (!vamrt::plan_conv3d_halo(d, h, wd, cin, cout, taps, sms, &pl)) return VAMRT_OK;
+    const int32_t v[18] = {1, pl.TZ, pl.TY, pl.Nt, pl.T, pl.WP, pl.PT, pl.NX, pl.rowtile, pl.mg, pl.adv,
+                           pl.a_bytes, pl.box_bytes, pl.stage_bytes, pl.ncols, pl.ry, pl.nslice, pl.nitems};
+    for (int i = 0; i < 18; ++i) out[i] = v[i];
+    return VAMRT_OK;
+}
+
+vamrt_status vamrt_conv3d_wgrad_plan(int32_t d, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                     int32_t sms, int32_t *out)
+{
+    if (!out || sms < 1 || d < 1 || h < 1 || wd < 1) return einval("NULL out, sms < 1 or empty volume");
+    vamrt::WgradPlan pl;
+    for (int i = 0; i < 17; ++i) out[i] = 0;
+    if (!vamrt::plan_wgrad_tma(d, h, wd, cin, cout, taps, sms, &pl)) return VAMRT_OK;
+    const int32_t v[17] = {1, pl.Mtot, pl.nmt, pl.tpg, pl.kp, pl.KS, pl.BX, pl.nstage, pl.cwA, pl.cwB,
+                           pl.slots, pl.slot_bytes, pl.per_sm, pl.ncols, pl.ngroups, pl.nsplit, pl.spb};
+    for (int i = 0; i < 17; ++i) out[i] = v[i];
+    return VAMRT_OK;
+}
+
 vamrt_status vamrt_nn_resample(int32_t op, const void *in, void *out, int32_t d, int32_t h, int32_t w, int32_t c,
                                void *stream)
 {
