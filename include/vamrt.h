@@ -35,7 +35,7 @@ extern "C" {
 typedef enum {
     VAMRT_OK = 0,
     VAMRT_EINVAL = 1,          /* an argument is out of range, NULL or inconsistent */
-    VAMRT_EUNSUPPORTED = 2,    /* a valid request this build does not implement */
+    VAMRT_EUNSUPPORTED = 2,    /* a valid request this library does not implement */
     VAMRT_ECUDA = 3,           /* a CUDA runtime call failed (message in vamrt_last_error) */
     VAMRT_ENOMEM = 4,          /* device allocation failed */
     VAMRT_NOT_CONVERGED = 5,   /* the optimiser hit its iteration cap above tolerance */
