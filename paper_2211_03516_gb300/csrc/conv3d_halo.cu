@@ -457,7 +457,8 @@ bool plan_conv3d_halo(int D, int H, int W, int Cin, int Cout, int taps, int sms,
                 cost = (cost > epi ? cost : epi) + 500.0;
                 const int64_t nreg = (int64_t)((D + TZ - 1) / TZ) * ((H + TY - 1) / TY) * (Cout / Nt);
                 const double total = (double)((nreg + sms - 1) / sms) * cost;
-                if (!found || total < best) {
+                // ties go to the plan with more tiles: more issuers with a chain in flight
+                if (!found || total < best || (total == best && T > pl->T)) {
                     found = true;
                     best = total;
                     int ncols = 32;
