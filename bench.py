@@ -1,5 +1,7 @@
 """Benchmark: ray-voxel samples/s of the projection (A^T) + dose (A) operators inside the
-plain FP32 projection optimiser, on the 256^3 finite-etendue workload.
+plain FP32 projection optimiser, on the large-print workload (768 x 768 x 1024 voxels of
+0.05 mm, 1000 angles, 1024^2 pixels, f/2.8 with 4 rays per pixel, pupil 100 mm, vial
+19 / 1.5 mm); the time-to-target comparison runs on its own, smaller workload.
 
 One step = one optimiser iteration over the whole volume: g = max(0, A^T m),
 d = A g, normalise, error, model update (all in the CUDA library, called through the
@@ -31,7 +33,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "ray-voxel samples/s fwd+adjoint; time-to-target dose error vs plain, 1 GB300"
 UNIT = "samples/s"
-WORKLOAD = "mid_256cube_360ang_16rays"
+WORKLOAD = "large_768x768x1024_1000ang_4rays"
+TTT_WORKLOAD = "mid_256cube_360ang_16rays"
 BYTES_PER_SAMPLE = 32          # 8 trilinear corners x 4 B (FP32 gathers / reductions)
 
 
@@ -112,18 +115,26 @@ def reduce_max(value: float, dist, device) -> float:
 
 
 def cpu_threads() -> int:
-    return 1   # the oracle is single-threaded
+    """Host cores the oracle sample runs on: one thread per core (the oracle's C calls
+    release the GIL, so the threads run in parallel)."""
+    return os.cpu_count() or 1
 
 
-def oracle_sample(w, pupil, target, rows, angle=0):
-    """Oracle A^T and A over pixel rows `rows` of one angle: returns (samples, seconds)."""
+def oracle_sample(w, pupil, target, rows, angle=0, threads=None):
+    """Oracle A^T then A over pixel rows `rows` of one angle, split over host threads:
+    each pixel's projection (FP64 oracle), clamped at 0 as the optimiser does, then the dose
+    of those pixels (sparse, FP64).  Returns (samples, wall seconds, threads)."""
+    import concurrent.futures as cf
+
     from oracle import vam_oracle as O
-    pix = [(angle, v, u) for v in rows for u in range(w.nu)]
-    # samples the chosen pixels visit: per traced ray, the midpoints whose footprint reaches the grid
+    threads = threads or cpu_threads()
+    M = w.rays_per_pixel
+    # samples the chosen pixels visit (counted outside the timed region): per traced ray,
+    # the midpoints whose footprint reaches the grid
     n = 0
     for v in rows:
         for u in range(w.nu):
-            for a in range(pupil.shape[0]):
+            for a in range(M):
                 r = O.trace(w, pupil, u, v, a)
                 if r["status"] != 2:
                     continue
@@ -131,14 +142,23 @@ def oracle_sample(w, pupil, target, rows, angle=0):
                 j = np.arange(r["k"])
                 qz = (r["e"][2] + (j + 0.5) * dl * r["d2"][2]) / w.voxel_mm + 0.5 * (w.nz - 1)
                 n += int(np.count_nonzero((qz > -1) & (qz < w.nz)))
-    g = np.zeros(w.proj_shape)
+    vol = target if target.dtype == np.float64 else np.ascontiguousarray(target, dtype=np.float64)
+    chunks = [[(angle, v, u) for u in range(w.nu)] for v in rows]
+
+    def work(pix):
+        y = O.adjoint_pixels(w, vol, pupil, pix)
+        O.forward_pixels(w, pupil, pix, np.maximum(y, 0.0))
+
     t0 = time.perf_counter()
-    y = O.adjoint_pixels(w, target, pupil, pix)
-    for (k, v, u), val in zip(pix, y):
-        g[k, v, u] = max(val, 0.0)
-    O.forward(w, g, pupil)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(work, chunks))
     dt = time.perf_counter() - t0
-    return 2 * n, dt
+    return 2 * n, dt, threads
+
+
+def sample_rows(w, count):
+    mid = w.nv // 2
+    return list(range(mid - count // 2, mid - count // 2 + count))
 
 
 def run_reference(args, rank, world):
@@ -147,25 +167,24 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     pupil = I.workload_pupil(w)
-    target = I.make_target(w)
-    mid = w.nv // 2
-    rows = list(range(mid - args.ref_rows // 2, mid - args.ref_rows // 2 + args.ref_rows))
+    target = I.make_target(w).astype(np.float64)
+    rows = sample_rows(w, args.ref_rows)
     for _ in range(args.warmup):
         oracle_sample(w, pupil, target, rows[:1])
-    tot_n, tot_t = 0, 0.0
+    tot_n, tot_t, threads = 0, 0.0, cpu_threads()
     for s in range(args.steps):
-        n, dt = oracle_sample(w, pupil, target, rows, angle=(s * 37) % w.n_angles)
+        n, dt, threads = oracle_sample(w, pupil, target, rows, angle=(s * 37) % w.n_angles)
         tot_n += n
         tot_t += dt
     value = tot_n / tot_t
-    sample = (f"{args.ref_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of one angle per step, "
-              f"projection then dose, FP64 oracle")
+    sample = (f"{args.ref_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of one angle per step "
+              f"(of {w.nv} rows x {w.n_angles} angles), projection then dose, FP64 oracle on {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "samples_per_step": tot_n // args.steps},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -436,10 +455,25 @@ def run_gpu(args, rank, world):
     # shared memory, so the roofline is shared-memory bandwidth, measured here; the HBM
     # fraction of the compulsory traffic is reported beside it.
     smem_bps = vamrt.vamrt_measure_smem_bandwidth()
+    l2_read_bps, l2_red_ops = vamrt.vamrt_measure_l2_rates()
     hbm, peak_kind = peaks()
+    # The dose kernel skips the rays of pixels whose value is zero (their contributions are
+    # exactly zero): its algorithmic samples are those of the nonzero pixels of the
+    # projections it was given (the last iteration's g, the same support every step here).
+    _, _, j2 = P.ray_table()
+    per_pixel = torch.from_numpy((j2[:, 1] - j2[:, 0]).astype(np.int64).reshape(w.rays_per_pixel, w.nv, w.nu)
+                                 .sum(0)).to(dev, torch.float64)
+    fwd_spp = sum(float(((proj[k0:k0 + 64] != 0).to(torch.float64) * per_pixel).sum())
+                  for k0 in range(0, w.n_angles, 64))
+    adj_ms_step, fwd_ms_step = adj_ms / args.steps, fwd_ms / args.steps
+    kern = {"adjoint": {"samples": spp, "ms": adj_ms_step},
+            "forward": {"samples": fwd_spp, "ms": fwd_ms_step}}
+    for kk in kern.values():
+        kk["achieved_GBps"] = kk["samples"] * BYTES_PER_SAMPLE / (kk["ms"] / 1e3) / 1e9
+        kk["frac"] = kk["achieved_GBps"] * 1e9 / smem_bps
     dom = "forward" if fwd_ms >= adj_ms else "adjoint"
-    dom_ms = (fwd_ms if dom == "forward" else adj_ms) / args.steps
-    achieved = spp * BYTES_PER_SAMPLE / (dom_ms / 1e3) / 1e9
+    dom_ms = kern[dom]["ms"]
+    achieved = kern[dom]["achieved_GBps"]
     n_rays = P.info()["n_rays"]
     vol_b, proj_b = 4 * math.prod(w.vol_shape), 4 * math.prod(w.proj_shape)
     # compulsory DRAM bytes of one launch: volume in + projections out (adjoint) or
@@ -453,10 +487,15 @@ def run_gpu(args, rank, world):
         except Exception:
             traffic = None
 
-    # ---- time to target: plain FP32 optimiser vs the BF16-storage optimiser ----
+    # ---- time to target, on its own (smaller) workload: plain FP32 optimiser vs variants ----
     ttt = None
     if args.ttt_iters > 0:
-        ttt = time_to_target(P, target, w, args.ttt_iters, beta=args.ttt_beta, mu=args.ttt_mu)
+        wt = I.WORKLOADS[args.ttt_workload]
+        Pt = P if wt.name == w.name else vamrt.Projector.from_workload(wt, I.workload_pupil(wt))
+        tt = target if wt.name == w.name else torch.from_numpy(I.make_target(wt)).to(dev)
+        ttt = {"workload": wt.name}
+        ttt.update(time_to_target(Pt, tt, wt, args.ttt_iters, beta=args.ttt_beta, mu=args.ttt_mu))
+        del Pt, tt
         if not args.no_fins:
             from paper_2211_03516_gb300 import fins as FN
             ttt["fins"] = [FN.fins_experiment(n, beta=args.ttt_beta, mu=args.ttt_mu) for n in (9, 18)]
@@ -468,10 +507,11 @@ def run_gpu(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, dt = oracle_sample(w, pupil, target_np, list(range(w.nv // 2, w.nv // 2 + args.cpu_rows)))
-        cpu = {"value": n / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{args.cpu_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of angle 0, "
-                         f"projection then dose ({n} samples, {dt:.1f} s)"}
+        n, dt, threads = oracle_sample(w, pupil, target_np, sample_rows(w, args.cpu_rows))
+        cpu = {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of angle 0 "
+                         f"(of {w.nv} rows x {w.n_angles} angles), projection then dose, FP64 oracle on "
+                         f"{threads} threads ({n} samples, {dt:.1f} s)"}
 
     if dist:
         dist.barrier()
@@ -486,7 +526,8 @@ def run_gpu(args, rank, world):
                    "pixels": [w.nv, w.nu], "rays_per_pixel": w.rays_per_pixel,
                    "step": "one optimiser iteration: projection (A^T) + clamp + dose (A) + normalise/update",
                    "samples_per_pass": spp, "units_per_step": units_per_step,
-                   "l2": "inputs larger than L2 (model, target, projections, dose, scratch: 0.36 GB)",
+                   "l2": f"inputs larger than L2 (model, target, projections, dose, scratch: "
+                         f"{(4 * math.prod(w.vol_shape) + math.prod(w.proj_shape)) * 4 / 1e9:.2f} GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "setup_s": round(setup_s, 3)},
         "phase_ms_per_step": {"adjoint": adj_ms / args.steps, "forward": fwd_ms / args.steps,
@@ -498,6 +539,9 @@ def run_gpu(args, rank, world):
                      "frac": achieved * 1e9 / smem_bps, "traffic": traffic,
                      "peak_kind": "measured in this run (vamrt_measure_smem_bandwidth)",
                      "bytes_per_sample": BYTES_PER_SAMPLE,
+                     "l2_measured": {"read_GBps": l2_read_bps / 1e9, "red_v4_ops_per_s": l2_red_ops},
+                     "per_kernel": kern,
+                     "forward_sample_fraction": fwd_spp / spp,
                      "hbm": {"compulsory_bytes": compulsory, "achieved": compulsory / (dom_ms / 1e3) / 1e9,
                              "peak": hbm, "frac": compulsory / (dom_ms / 1e3) / 1e9 / hbm,
                              "peak_kind": peak_kind}},
@@ -519,8 +563,10 @@ def main():
     ap.add_argument("--impl", default="vamrt", choices=["vamrt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--angles", type=int, default=0, help="override the angle count (small profiling cases)")
-    ap.add_argument("--cpu-rows", type=int, default=48)
-    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--cpu-rows", type=int, default=128)
+    ap.add_argument("--ref-rows", type=int, default=32)
+    ap.add_argument("--ttt-workload", default=TTT_WORKLOAD,
+                    help="workload of the time-to-target comparison (its own projector)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttt-beta", type=float, default=4.0,
                     help="model step of the over-relaxed optimiser variant in the time-to-target comparison")

@@ -64,8 +64,25 @@ typedef enum {
  *               Telecentric: the ray crosses the image point with direction proportional
  *               to (-xi_a t, 1, -eta_a t), t = 1/(2 f_number).
  *   f_number    INFINITY = zero etendue (all rays of a pixel are its chief ray).
- *   pupil_xy    HOST array of rays_per_pixel points (xi, eta) in the unit disk, copied
- *               during vamrt_make_projector.  NULL means one chief ray (0, 0).
+ *   aperture    how the rays_per_pixel stop points (xi, eta) in the unit disk are chosen
+ *               (Sec. 2.1: a pixel's rays leave points of the aperture stop, the chief ray
+ *               its centre; the paper fills the stop hexagonally):
+ *                 VAMRT_APERTURE_LIST        the HOST array pupil_xy (copied; NULL = one chief ray),
+ *                 VAMRT_APERTURE_CHIEF       one ray, (0, 0),
+ *                 VAMRT_APERTURE_STRATIFIED  rays_per_pixel = n^2: ray a = i n + k takes the point
+ *                                            (2 (i + J0)/n - 1, 2 (k + J1)/n - 1) of stratum (i, k)
+ *                                            of [-1,1]^2, mapped to the disk by Shirley and
+ *                                            Chiu's concentric map,
+ *                 VAMRT_APERTURE_SUNFLOWER   r = sqrt((a + 1/2)/M), azimuth a g + 2 pi J,
+ *                                            g = pi (3 - sqrt 5) the golden angle, J = J0 of a = 0,
+ *                 VAMRT_APERTURE_HEX         13 rays: the points of a hexagonal lattice of spacing
+ *                                            1/2 inside the disk (centre; 6 at r = 1/2, azimuths
+ *                                            0, 60, .. 300 degrees; 6 at r = sqrt(3)/2, 30, 90, ..
+ *                                            330 degrees).
+ *               Jitter numbers Jc (c = 0, 1) of ray a of pixel (u, v): the top 53 bits of
+ *               splitmix64(seed ^ (u + 2^20 v + 2^40 a + 2^56 c)) times 2^-53, with u = v = 0
+ *               unless aperture_flags has VAMRT_JITTER_PER_PIXEL (splitmix64: the Weyl step
+ *               0x9E3779B97F4A7C15 then the mix of Steele, Lea and Flood / Vigna).
  *   vial        inner radius r_inner_mm, glass wall wall_mm, refractive indices outside,
  *               glass, resin; Fresnel losses (unpolarised) at the outer and inner surface;
  *               tracing stops at the inner wall on the far side (Sec. 2.1).
@@ -88,6 +105,13 @@ typedef enum {
  *               light.  pupil_mm and f_number are then ignored.
  * The grid must enclose the resin cylinder: r_inner_mm / voxel_mm <= (min(nx,ny)+1)/2 - 0.01.
  */
+#define VAMRT_APERTURE_LIST 0
+#define VAMRT_APERTURE_CHIEF 1
+#define VAMRT_APERTURE_STRATIFIED 2
+#define VAMRT_APERTURE_SUNFLOWER 3
+#define VAMRT_APERTURE_HEX 4
+#define VAMRT_JITTER_PER_PIXEL 1u  /* aperture_flags: jitter drawn per pixel, not shared by all */
+
 typedef struct {
     double y_mm;               /* vertex on the optical axis (the y axis through x = z = 0) */
     double radius_mm;          /* radius of curvature, centre at y_mm + radius_mm; INFINITY = plane */
@@ -116,6 +140,9 @@ typedef struct {
     double object_y_mm;              /* pixel array plane, before the first surface */
     double magnification;            /* paraxial image / object height (nonzero) */
     double aim_mm;                   /* launch aim distance (> 0) */
+    int32_t aperture;                /* VAMRT_APERTURE_* (0 = LIST: pupil_xy) */
+    uint32_t aperture_flags;         /* VAMRT_JITTER_PER_PIXEL */
+    uint64_t seed;                   /* jitter seed */
 } vamrt_geometry;
 
 typedef struct vamrt_projector vamrt_projector;   /* opaque */
@@ -184,8 +211,12 @@ vamrt_status vamrt_forward_dose(vamrt_projector *p, const void *proj, vamrt_dtyp
  *     loads the library holds the 16 MiB) and is shared by all calls and projectors: each
  *     call first clears the part it uses, and calls that overlap on the GPU (other streams,
  *     other threads) race on it.  Serialise them.
- *   - The first call on a device looks up the array's device address (one runtime call,
- *     no allocation); make that first call before any CUDA stream capture.
+ *   - The library's device code loads lazily: the array is created on a device, and its
+ *     device address looked up, when vamrt_make_projector runs there (that call allocates
+ *     anyway), so the projector's own device already holds it and this call only reads
+ *     the cached address.  After a device reset (a new context) the first call looks the
+ *     address up again, which loads the array anew (16 MiB): make that call before any
+ *     CUDA stream capture, or make a new projector first.
  *   - The current device must be the projector's device.
  * Errors: EINVAL (NULL, dtype, flags, grid too large, wrong device), ECUDA.
  */
@@ -195,12 +226,19 @@ vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, const void *pro
 /*
  * Projection optimisation (Sec. 2.7).  The paper runs the object-space model
  * optimisation of Rackson et al. with both operators replaced by the ray-traced ones
- * and stops once the absolute relative dose error is below 0.5 %.  Iteration, per the
- * reading this library implements:
- *   g = max(0, A^T m);  d = A g;  dn = d / max(d);
- *   E = sum |dn - f| / sum f;  m <- max(0, m + beta (f - dn) + mu (m - m_prev));
- *   stop once E < tol,
- * with beta = 1, mu = 0 the plain update (params.step, 0 also meaning 1; params.momentum).
+ * and stops once the absolute relative error between target and simulated dose is below
+ * 0.5 %.  Iteration, per the reading this library implements:
+ *   g = max(0, A^T m);  d = A g;  dn = d / max_resin(d);
+ *   E = sum |dn - f| / sum f;  V = voxel error rate of dn (vamrt_voxel_error_rate);
+ *   m <- max(0, m + beta (f - dn) + mu (m - m_prev));
+ *   stop once V < tol (params.stop = VAMRT_STOP_VER, the default) or E < tol
+ *   (VAMRT_STOP_ERROR),
+ * max_resin the maximum over the resin voxels (centres within r_inner_mm of the axis).
+ * The paper's "absolute relative error" is read as V: the target against the dose as it
+ * prints (thresholded), relative to the resin volume.  E, the dose's L1 error, cannot
+ * fall to 0.5 % for a binary target (the dose is never zero in the void along rays that
+ * cross the part) and is reported beside it.
+ * beta = 1, mu = 0 is the plain update (params.step, 0 also meaning 1; params.momentum).
  * beta > 1 over-relaxes the model update and mu > 0 adds heavy-ball momentum -- neither is
  * in the paper; beta = 4, mu = 0.5 reaches the plain loop's final voxel error rate in 10 of
  * 30 iterations on the 256^3 test workload (13 without momentum).  With mu > 0 the
@@ -211,7 +249,8 @@ vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, const void *pro
  * (copy the target there for OSMO's start), out = the updated model.  proj: device
  * [n_angles][nv][nu] in proj_dtype, out = g of the last iteration.  dose: device
  * [nz][ny][nx] in dose_dtype, out = dn of the last iteration.
- * Synchronises `stream` once every check_every iterations to read E.
+ * Synchronises `stream` once every check_every iterations to read E and V (V is computed
+ * on those iterations only).
  */
 typedef struct {
     int32_t max_iter;          /* 1 .. 4096 */
@@ -224,7 +263,11 @@ typedef struct {
     double step;               /* object mode: beta in [0, 64] (0 = 1); projection mode: alpha in (0, 1] */
     double momentum;           /* object mode: mu in [0, 1) (0 = none) */
     float *prev_model;         /* device f32 [nz][ny][nx], required when momentum > 0; see above */
+    int32_t stop;              /* VAMRT_STOP_VER (0) or VAMRT_STOP_ERROR */
 } vamrt_opt_params;
+
+#define VAMRT_STOP_VER 0
+#define VAMRT_STOP_ERROR 1
 
 /* Optimiser modes.  VAMRT_OPT_OBJECT iterates on the model m (model in = m0).
  * VAMRT_OPT_PROJECTIONS iterates on the projections themselves, starting from proj (in =
@@ -242,6 +285,8 @@ typedef struct {
     double adjoint_ms;         /* with timing: summed device time of the projection kernels */
     double forward_ms;         /* with timing: summed device time of the dose kernels */
     double update_ms;          /* with timing: summed device time of normalise/update/error */
+    double final_ver;          /* V at the last check */
+    double *ver_history;       /* optional HOST array of max_iter entries: V at checked iterations, NaN elsewhere */
 } vamrt_opt_report;
 
 vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *model, void *proj,
@@ -265,7 +310,8 @@ vamrt_status vamrt_threshold_loss(vamrt_projector *p, const void *dose, vamrt_dt
 /*
  * Voxel error rate (VER) of a dose against a binary target: the fraction of resin voxels
  * (centres within r_inner_mm of the axis) whose printed state differs from the target at
- * the best of the 1023 thresholds tau_i = (i/1024) max(dose), i = 1..1023 -- how well the
+ * the best of the 1023 thresholds tau_i = (i/1024) max(dose), i = 1..1023, max over the
+ * resin voxels -- how well the
  * dose prints the part whatever its scale (the optimiser's goal, Sec. 2.7).  A voxel is
  * above tau_i iff min(floor(dose * (1024 / max)), 1023) >= i, evaluated in FP32.
  * dose: device [nz][ny][nx] in dose_dtype (>= 0); target: device f32.  Writes the rate
@@ -416,11 +462,21 @@ vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4
 
 /*
  * Measured shared-memory read bandwidth of the current device in bytes/s (conflict-free
- * 32-bit loads on every SM).  The operators stage their per-sample corner words in shared
+ * 32-bit volatile loads on every SM, none merged or dropped).  The operators stage their per-sample corner words in shared
  * memory, so this is the denominator of their roofline.  Synchronises `stream`; allocates
  * a small temporary device buffer.  Errors: EINVAL (NULL), ENOMEM, ECUDA.
  */
 vamrt_status vamrt_measure_smem_bandwidth(double *bytes_per_second, void *stream);
+
+/*
+ * Measured L2 rates of the current device: *read_bytes_per_second for 16-byte loads that
+ * bypass L1 over a 32 MiB buffer resident in L2, and *red_ops_per_second for 16-byte
+ * vector reductions (red.global.add.v4.f32, the dose flush's instruction) to distinct
+ * addresses of that buffer.  The operators stage volume boxes from L2 and flush dose
+ * boxes into it, so these bound their L2 traffic.  Synchronises `stream`; allocates a
+ * temporary 32 MiB device buffer.  Errors: EINVAL (NULL), ENOMEM, ECUDA.
+ */
+vamrt_status vamrt_measure_l2_rates(double *read_bytes_per_second, double *red_ops_per_second, void *stream);
 
 /* Number of kernels this library has launched in the process (all devices). */
 uint64_t vamrt_launch_count(void);

@@ -4,15 +4,21 @@ Sec. 2.7 runs the object-space model optimisation (OSMO) of Rackson et al. with 
 Radon transform and its inverse replaced by the ray-traced operators, and stops when the
 absolute relative error between target and simulated dose falls below 0.5 %.  OSMO's
 own equations are in that reference, not in the paper, so this file follows a stated
-reading (parity unpinned beyond its properties):
+reading:
 
   m^0 = f_T
   g^k = max(0, P m^k)                 P: projection (the adjoint operator)
   d^k = A g^k                         A: dose operator
-  dn^k = d^k / max(d^k)               max over the grid
-  E^k = sum |dn^k - f_T| / sum f_T    "absolute relative error"
+  dn^k = d^k / max_resin(d^k)         maximum over the resin voxels
+  E^k = sum |dn^k - f_T| / sum f_T    the dose's L1 error relative to the target
+  V^k = voxel error rate of dn^k      resin voxels misprinted at the best threshold
   m^{k+1} = max(0, m^k + (f_T - dn^k))
-  stop after the update once E^k < tol, or after n_iter iterations.
+  stop after the update once V^k < tol, or after n_iter iterations.
+
+"Absolute relative error" is read as V: the absolute mismatch between the target and
+the dose as printed (thresholded), relative to the resin volume.  E cannot fall to
+0.5 % for a binary target: a non-negative dose is never zero in the void along rays
+that cross the part.
 
 The thresholded dose loss (differentiable path; not in the paper):
   L(D) = mean_{v in P} relu(d_h - D_v)^2 + mean_{v in Q} relu(D_v - d_l)^2
@@ -21,30 +27,39 @@ with P = {f_T = 1}, Q = {f_T = 0}, and its gradient dL/dD.
 import numpy as np
 
 
-def osmo(target, project, dose, n_iter, tol=0.005, beta=1.0, mu=0.0, m0=None, m_prev=None):
-    """Returns (g, dn, m, errors) after the iterations; project/dose are FP64 callables.
-    beta scales the model update and mu adds heavy-ball momentum,
+def _resin(resin, shape):
+    return np.ones(shape, dtype=bool) if resin is None else np.asarray(resin, dtype=bool)
+
+
+def osmo(target, project, dose, n_iter, tol=0.005, beta=1.0, mu=0.0, m0=None, m_prev=None, resin=None,
+         stop="ver"):
+    """Returns (g, dn, m, errors E, voxel error rates V) after the iterations; project and
+    dose are FP64 callables; resin is a boolean mask (default: every voxel).  beta scales
+    the model update and mu adds heavy-ball momentum,
     m <- max(0, m + beta (f - dn) + mu (m - m_prev)); beta = 1, mu = 0 is the reading
-    above, the others variants not in the paper.  m0 defaults to f, m_prev to m0 (at rest)."""
+    above, the others variants not in the paper.  m0 defaults to f, m_prev to m0 (at
+    rest).  stop: "ver" (V < tol, the reading of Sec. 2.7) or "error" (E < tol)."""
     f = np.asarray(target, dtype=np.float64)
+    rmask = _resin(resin, f.shape)
     fsum = f.sum()
     m = f.copy() if m0 is None else np.array(m0, dtype=np.float64)
     prev = m.copy() if m_prev is None else np.array(m_prev, dtype=np.float64)
-    errors = []
+    errors, vers = [], []
     g = dn = None
     for _ in range(n_iter):
         g = np.maximum(0.0, project(m))
         d = dose(g)
-        dmax = d.max()
+        dmax = d[rmask].max()
         if not dmax > 0.0:
-            raise FloatingPointError("dose is zero everywhere")
+            raise FloatingPointError("dose is zero everywhere in the resin")
         dn = d / dmax
         err = np.abs(dn - f).sum() / fsum
         errors.append(err)
+        vers.append(voxel_error_rate(dn, f, rmask)[0])
         m, prev = np.maximum(0.0, m + beta * (f - dn) + mu * (m - prev)), m
-        if err < tol:
+        if (vers[-1] if stop == "ver" else err) < tol:
             break
-    return g, dn, m, np.array(errors)
+    return g, dn, m, np.array(errors), np.array(vers)
 
 
 def threshold_loss(dose, target, d_l, d_h):
@@ -80,18 +95,19 @@ def voxel_error_rate(dose, target, resin_mask):
     return best / x.size, best_i
 
 
-def osmo_projections(target, g0, project, dose, n_iter, alpha=1.0):
+def osmo_projections(target, g0, project, dose, n_iter, alpha=1.0, resin=None):
     """Projection-space iteration from g0 (reading; the learned warm start's continuation):
-    d = A g; dn = d / max(d); E = sum|dn - f| / sum f; g <- max(0, g + P(alpha (f - dn))).
+    d = A g; dn = d / max_resin(d); E = sum|dn - f| / sum f; g <- max(0, g + P(alpha (f - dn))).
     Without the model clamp this is the update OSMO makes to g = P m."""
     f = np.asarray(target, dtype=np.float64)
+    rmask = _resin(resin, f.shape)
     fsum = f.sum()
     g = np.asarray(g0, dtype=np.float64).copy()
     errors = []
     dn = None
     for _ in range(n_iter):
         d = dose(g)
-        dn = d / d.max()
+        dn = d / d[rmask].max()
         errors.append(np.abs(dn - f).sum() / fsum)
         g = np.maximum(0.0, g + project(alpha * (f - dn)))
     return g, dn, np.array(errors)

@@ -31,6 +31,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#define ORC_PI 3.14159265358979323846
+
 typedef struct {
     int32_t nx, ny, nz;
     double h;               /* voxel pitch, mm */
@@ -58,6 +60,15 @@ typedef struct {
     const double *surf;     /* n_surf x 5: vertex y, radius (INFINITY = plane; centre at y + radius),
                                index after, clear semi-aperture, stop flag */
     double obj_y, mag, aim;
+    /* Aperture-stop samples generated here instead of read from pupil_xy (Sec. 2.1: rays
+     * leave points of the stop; the paper fills it hexagonally).  0 = the list pupil_xy;
+     * 1 = chief ray only; 2 = n x n stratified jitter (m = n^2) mapped to the disk by the
+     * concentric map; 3 = golden-angle sunflower; 4 = hexagonal filling, 13 rays.
+     * per_pixel: the jitter draws depend on the pixel (u, v), else they are shared by every
+     * pixel.  Jitter numbers come from splitmix64 of seed ^ key(u, v, a, c). */
+    int32_t aperture;
+    int32_t per_pixel;
+    uint64_t seed;
 } orc_geom;
 
 typedef struct {
@@ -170,6 +181,79 @@ int orc_lens_train(const orc_geom *g, double o[3], double d[3])
     return 1;
 }
 
+/* splitmix64 (Steele, Lea and Flood 2014; Vigna's public-domain form): one step of the
+ * generator from state x, i.e. the Weyl increment followed by the variant-13 finaliser. */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64(uint64_t x) { return splitmix64(x); }
+
+/* Jitter number in [0, 1) for pixel (u, v), aperture sample a and component c (0 or 1):
+ * the top 53 bits of splitmix64(seed ^ key), key = u + 2^20 v + 2^40 a + 2^56 c. */
+double orc_jitter(uint64_t seed, int32_t u, int32_t v, int32_t a, int32_t c)
+{
+    uint64_t key = (uint64_t)(uint32_t)u | ((uint64_t)(uint32_t)v << 20) | ((uint64_t)(uint32_t)a << 40) |
+                   ((uint64_t)(uint32_t)c << 56);
+    return (double)(splitmix64(seed ^ key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Shirley and Chiu's concentric map of the square [-1,1]^2 onto the unit disk: squares
+ * centred on the origin go to circles, the four triangular sectors between the diagonals
+ * to the four quarter disks, preserving area fractions. */
+static void concentric(double p, double q, double out[2])
+{
+    double r, phi;
+    if (p == 0.0 && q == 0.0) { out[0] = 0.0; out[1] = 0.0; return; }
+    if (fabs(p) > fabs(q)) { r = p; phi = (ORC_PI / 4.0) * (q / p); }
+    else { r = q; phi = ORC_PI / 2.0 - (ORC_PI / 4.0) * (p / q); }
+    out[0] = r * cos(phi);
+    out[1] = r * sin(phi);
+}
+
+/* Aperture-stop point (xi, eta) in the unit disk of aperture sample a of pixel (u, v). */
+void orc_aperture_point(const orc_geom *g, int32_t u, int32_t v, int32_t a, double out[2])
+{
+    int32_t pu = g->per_pixel ? u : 0, pv = g->per_pixel ? v : 0;
+    out[0] = 0.0; out[1] = 0.0;
+    if (g->aperture == 0) { out[0] = g->pupil_xy[2 * a]; out[1] = g->pupil_xy[2 * a + 1]; return; }
+    if (g->aperture == 1) return;                              /* the chief ray: the stop's centre */
+    if (g->aperture == 2) {
+        /* n x n strata of [-1,1]^2, one jittered point in stratum (i, k), a = i n + k */
+        int32_t n = (int32_t)floor(sqrt((double)g->m) + 0.5);
+        int32_t i = a / n, k = a % n;
+        double p = 2.0 * (i + orc_jitter(g->seed, pu, pv, a, 0)) / n - 1.0;
+        double q = 2.0 * (k + orc_jitter(g->seed, pu, pv, a, 1)) / n - 1.0;
+        concentric(p, q, out);
+        return;
+    }
+    if (g->aperture == 3) {
+        /* sunflower: radius sqrt((a + 1/2)/m), azimuth a times the golden angle, the whole
+         * pattern turned by 2 pi times one jitter number of the pixel */
+        double golden = ORC_PI * (3.0 - sqrt(5.0));
+        double r = sqrt((a + 0.5) / g->m);
+        double phi = a * golden + 2.0 * ORC_PI * orc_jitter(g->seed, pu, pv, 0, 0);
+        out[0] = r * cos(phi);
+        out[1] = r * sin(phi);
+        return;
+    }
+    /* hexagonal filling of the stop (Sec. 2.1) read as the points of a hexagonal lattice of
+     * spacing 1/2 inside the unit disk: the centre, 6 at distance 1/2 (azimuths 0, 60, ...,
+     * 300 degrees) and 6 at distance sqrt(3)/2 (30, 90, ..., 330 degrees) */
+    if (a == 0) return;
+    if (a <= 6) {
+        double t = (a - 1) * ORC_PI / 3.0;
+        out[0] = 0.5 * cos(t); out[1] = 0.5 * sin(t);
+        return;
+    }
+    double t = ORC_PI / 6.0 + (a - 7) * ORC_PI / 3.0, r = sqrt(3.0) / 2.0;
+    out[0] = r * cos(t); out[1] = r * sin(t);
+}
+
 /* Trace one ray (pixel u, v, aperture sample a) in the vial frame at theta = 0. */
 int orc_trace(const orc_geom *g, int32_t u, int32_t v, int32_t a, orc_ray *ray)
 {
@@ -177,7 +261,9 @@ int orc_trace(const orc_geom *g, int32_t u, int32_t v, int32_t a, orc_ray *ray)
     double r_out = g->r_in + g->wall;
     double qx = (u - 0.5 * (g->nu - 1)) * g->pu;   /* image point Q = (qx, 0, qz) */
     double qz = (v - 0.5 * (g->nv - 1)) * g->pv;
-    double xi = g->pupil_xy[2 * a], eta = g->pupil_xy[2 * a + 1];
+    double stop[2];
+    orc_aperture_point(g, u, v, a, stop);
+    double xi = stop[0], eta = stop[1];
     double *o = ray->origin, *d = ray->d0;
     if (g->n_surf > 0) {
         double rs = 0.0;
@@ -322,6 +408,32 @@ void orc_forward(const orc_geom *g, const double *proj, double *dose)
                 }
             }
     }
+}
+
+/* Dose contributions of one projection pixel (k, v, u) of intensity `intensity` (Sec. 2.5,
+ * the same terms orc_forward adds for that pixel), listed instead of summed into a dense
+ * volume: entry i adds val[i] to voxel idx[i].  Writes at most cap entries; returns the
+ * number of contributions (more than cap means the lists were cut short). */
+int64_t orc_forward_pixel(const orc_geom *g, int32_t k, int32_t v, int32_t u, double intensity, int64_t *idx,
+                          double *val, int64_t cap)
+{
+    double ct = cos(g->angles[k]), st = sin(g->angles[k]);
+    int64_t n = 0;
+    for (int32_t a = 0; a < g->m; ++a) {
+        orc_ray ray;
+        if (orc_trace(g, u, v, a, &ray) != 2) continue;
+        for (int32_t j = 0; j < ray.k; ++j) {
+            double q[3], fac;
+            sample(g, &ray, j, ct, st, q, &fac);
+            corners8 c;
+            trilinear(g, q, &c);
+            for (int i = 0; i < c.n; ++i) {
+                if (n < cap) { idx[n] = c.idx[i]; val[n] = intensity * fac * c.w[i]; }
+                n++;
+            }
+        }
+    }
+    return n;
 }
 
 /* Samples per pass whose trilinear footprint reaches the grid (-1 < q_z < nz); the

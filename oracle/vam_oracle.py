@@ -46,6 +46,7 @@ class OrcGeom(ctypes.Structure):
         ("unattenuated", ctypes.c_int32),
         ("n_surf", ctypes.c_int32), ("surf", _dp),
         ("obj_y", ctypes.c_double), ("mag", ctypes.c_double), ("aim", ctypes.c_double),
+        ("aperture", ctypes.c_int32), ("per_pixel", ctypes.c_int32), ("seed", ctypes.c_uint64),
     ]
 
 
@@ -92,19 +93,46 @@ def lib():
         L.orc_lens_train.argtypes = [ctypes.POINTER(OrcGeom), _dp, _dp]
         L.orc_lens_train.restype = ctypes.c_int
         L.orc_sizeof_ray.restype = ctypes.c_int32
+        L.orc_forward_pixel.argtypes = [ctypes.POINTER(OrcGeom), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+        L.orc_forward_pixel.restype = ctypes.c_int64
+        L.orc_splitmix64.argtypes = [ctypes.c_uint64]
+        L.orc_splitmix64.restype = ctypes.c_uint64
+        L.orc_jitter.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.orc_jitter.restype = ctypes.c_double
+        L.orc_aperture_point.argtypes = [ctypes.POINTER(OrcGeom), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp]
+        L.orc_aperture_point.restype = None
         assert L.orc_sizeof_geom() == ctypes.sizeof(OrcGeom)
         assert L.orc_sizeof_ray() == ctypes.sizeof(OrcRay)
         _lib = L
     return _lib
 
 
-class _Geom:
-    """Keeps the numpy arrays the C struct points to alive."""
+# aperture pattern names -> the oracle's own codes (see orc_geom.aperture)
+_APERTURE = {"chief": 1, "stratified": 2, "sunflower": 3, "hex13": 4}
 
-    def __init__(self, w, pupil_xy, angles, unattenuated=False):
-        self.pupil_xy = np.ascontiguousarray(pupil_xy, dtype=np.float64).reshape(-1, 2)
+
+class _Geom:
+    """Keeps the numpy arrays the C struct points to alive.  `pupil` is either an explicit
+    (m, 2) list of stop points or a named pattern (an object with pattern, n_rays, seed and
+    per_pixel attributes) that the oracle generates itself."""
+
+    def __init__(self, w, pupil, angles, unattenuated=False):
+        named = hasattr(pupil, "pattern")
+        if named:
+            m = int(pupil.n_rays)
+            if pupil.pattern == "stratified":
+                n = int(round(m ** 0.5))
+                assert n * n == m, "stratified needs a square ray count"
+            self.pupil_xy = np.zeros((m, 2))
+        else:
+            self.pupil_xy = np.ascontiguousarray(pupil, dtype=np.float64).reshape(-1, 2)
         self.angles = np.ascontiguousarray(angles, dtype=np.float64).ravel()
         g = OrcGeom()
+        if named:
+            g.aperture = _APERTURE[pupil.pattern]
+            g.per_pixel = 1 if pupil.per_pixel else 0
+            g.seed = int(pupil.seed) & 0xFFFFFFFFFFFFFFFF
         g.nx, g.ny, g.nz, g.h = w.nx, w.ny, w.nz, w.voxel_mm
         g.nu, g.nv, g.pu, g.pv = w.nu, w.nv, w.pixel_u_mm, w.pixel_v_mm
         g.pupil, g.fnum = w.pupil_mm, w.f_number
@@ -182,6 +210,35 @@ def forward(w, proj, pupil_xy, angles=None) -> np.ndarray:
     return out
 
 
+def forward_pixels(w, pupil, pixels, values, angles=None):
+    """Sec. 2.5 dose of projections that are zero except at the listed (k, v, u) pixels
+    (intensities `values`), as a sparse volume: (sorted flat voxel indices, dose there).
+    Each pixel's contributions come from the same per-sample terms as forward(); the sums
+    over pixels and samples are formed in FP64."""
+    G = geom(w, pupil, angles)
+    L = lib()
+    idx_parts, val_parts = [], []
+    cap = 1 << 16
+    for (k, v, u), val in zip(pixels, values):
+        while True:
+            idx = np.empty(cap, np.int64)
+            vv = np.empty(cap, np.float64)
+            n = L.orc_forward_pixel(G.ref, int(k), int(v), int(u), float(val), idx.ctypes.data, vv.ctypes.data, cap)
+            if n <= cap:
+                break
+            cap = int(n)
+        idx_parts.append(idx[:n])
+        val_parts.append(vv[:n])
+    if not idx_parts:
+        return np.zeros(0, np.int64), np.zeros(0)
+    idx = np.concatenate(idx_parts)
+    vals = np.concatenate(val_parts)
+    uniq, inv = np.unique(idx, return_inverse=True)
+    dose = np.zeros(uniq.size)
+    np.add.at(dose, inv, vals)
+    return uniq, dose
+
+
 def lens_trace(w, origin, direction):
     """The oracle's lens-train stage alone: (ok, point on the last surface, direction
     behind it) for a ray (origin, unit direction) starting before the first surface."""
@@ -190,6 +247,24 @@ def lens_trace(w, origin, direction):
     d = np.array(direction, dtype=np.float64)
     ok = lib().orc_lens_train(G.ref, o.ctypes.data_as(_dp), d.ctypes.data_as(_dp))
     return bool(ok), o, d
+
+
+def aperture_points(w, pupil, u, v) -> np.ndarray:
+    """Sec. 2.1 stop sampling: the (m, 2) stop points (xi, eta) of pixel (u, v)."""
+    G = geom(w, pupil, np.zeros(1))
+    out = np.zeros((G.g.m, 2))
+    for a in range(G.g.m):
+        lib().orc_aperture_point(G.ref, u, v, a, out[a].ctypes.data_as(_dp))
+    return out
+
+
+def jitter(seed, u, v, a, c) -> float:
+    """The jitter number in [0, 1) of pixel (u, v), aperture sample a, component c."""
+    return float(lib().orc_jitter(int(seed) & 0xFFFFFFFFFFFFFFFF, u, v, a, c))
+
+
+def splitmix64(x) -> int:
+    return int(lib().orc_splitmix64(int(x) & 0xFFFFFFFFFFFFFFFF))
 
 
 def sample_count(w, pupil_xy, angles=None) -> int:

@@ -46,7 +46,11 @@ struct OpParams {
 
 // Per-ray constants of the FP64 tracer.
 struct TraceParams {
-    const double *pupil_xy;   // device, M pairs
+    const double *pupil_xy;   // device, M pairs (aperture = VAMRT_APERTURE_LIST)
+    int aperture;             // VAMRT_APERTURE_*
+    int per_pixel;            // jitter drawn per pixel
+    unsigned long long seed;
+    int strat_n;              // strata per side (stratified aperture)
     int nu, nv, M, nz;
     double pu, pv;
     double pupil_mm, f_number;
@@ -77,7 +81,7 @@ struct vamrt_projector {
     double *red;               // kRedBlocks partials + scalars
     double *hist;              // kMaxHistory errors
     float *dmax;               // one float, max of the dose
-    double *host_err;          // pinned, one double
+    double *host_err;          // pinned, 4 doubles: the optimiser's E and VER counts
     vamrt::OpParams op;
 };
 
@@ -91,6 +95,10 @@ void set_error(const char *msg);
 // raytable.cu
 cudaError_t launch_raytable(const TraceParams &T, float4 *A, float4 *B, int2 *J,
                             unsigned long long *counters, cudaStream_t s);
+
+// static_dose.cu: device address of the allocation-free dose entry point's static
+// accumulator on the current device `dev` (loads its module on first use)
+cudaError_t static_acc_address(int dev, float **out);
 
 // operators.cu
 cudaError_t operators_init();

@@ -1,6 +1,7 @@
 // Elementwise and reduction kernels of the projection optimiser (Sec. 2.7).
 //
-// Per iteration, after the two operators: the dose maximum (order-free, so exact), then
+// Per iteration, after the two operators: the dose maximum over the resin (order-free, so
+// exact), then
 // one fused pass that normalises the dose, writes it out, updates the model and emits
 // per-block FP64 partial sums of |dn - f|; a single block adds the partials in a fixed
 // order, so the error E is deterministic.
@@ -51,8 +52,10 @@ __global__ void finish_sum_kernel(const double *__restrict__ partials, int n, co
     if (threadIdx.x == 0) *out = divisor ? s / *divisor : s;
 }
 
-__global__ void interior_max_kernel(const float *__restrict__ acc, int nx, int ny, int nz, int px, int py,
-                                    float *__restrict__ out)
+// Maximum of the dose over the resin voxels (centres within r_inner of the axis, decided
+// in FP64 without fused multiply-adds).
+__global__ void resin_max_kernel(const float *__restrict__ acc, int nx, int ny, int nz, int px, int py, double h,
+                                 double r2, float *__restrict__ out)
 {
     const int64_t total = (int64_t)nx * ny * nz;
     float m = 0.f;
@@ -60,6 +63,8 @@ __global__ void interior_max_kernel(const float *__restrict__ acc, int nx, int n
         const int x = (int)(i % nx);
         const int y = (int)((i / nx) % ny);
         const int z = (int)(i / ((int64_t)nx * ny));
+        const double cx = (x - 0.5 * (nx - 1)) * h, cy = (y - 0.5 * (ny - 1)) * h;
+        if (__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)) > r2) continue;
         m = fmaxf(m, acc[((int64_t)(z + 1) * py + (y + 1)) * px + (x + 1)]);
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -133,7 +138,8 @@ cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, floa
     int gm = (int)((n + kRedThreads - 1) / kRedThreads);
     if (gm > p->num_sms * 8) gm = p->num_sms * 8;
     const int px = p->op.px, py = p->op.py;
-    interior_max_kernel<<<gm, kRedThreads, 0, s>>>(p->scratch, nx, ny, nz, px, py, p->dmax);
+    resin_max_kernel<<<gm, kRedThreads, 0, s>>>(p->scratch, nx, ny, nz, px, py, p->g.voxel_mm,
+                                                p->g.r_inner_mm * p->g.r_inner_mm, p->dmax);
     const int G = red_grid(n);
     if (dose_dt == VAMRT_F32)
         osmo_update_kernel<float><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,

@@ -104,6 +104,92 @@ __device__ bool through_lenses(const double *sv, int n_surf, double n0, d3 &o, d
     return true;
 }
 
+// ---------------------------------------------------------------------------------
+// aperture-stop samples (Sec. 2.1: a pixel's rays leave points of the stop)
+// ---------------------------------------------------------------------------------
+
+// splitmix64 as published (Steele, Lea and Flood; Vigna's form): Weyl step, then mix.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long state)
+{
+    unsigned long long z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// uniform in [0, 1): 53 high bits of the hash of (pixel, ray, component)
+__device__ double jitter01(unsigned long long seed, int u, int v, int a, int c)
+{
+    const unsigned long long key = (unsigned long long)(unsigned)u | ((unsigned long long)(unsigned)v << 20) |
+                                   ((unsigned long long)(unsigned)a << 40) | ((unsigned long long)(unsigned)c << 56);
+    return (double)(mix64(seed ^ key) >> 11) * 0x1.0p-53;
+}
+
+// Shirley-Chiu concentric square-to-disk map of (s, t) in [-1,1]^2
+__device__ void square_to_disk(double s, double t, double &x, double &y)
+{
+    const double quarter = 0.78539816339744830962;   // pi / 4
+    double rad = 0.0, ang = 0.0;
+    if (s != 0.0 || t != 0.0) {
+        if (fabs(s) > fabs(t)) {
+            rad = s;
+            ang = quarter * (t / s);
+        } else {
+            rad = t;
+            ang = 2.0 * quarter - quarter * (s / t);
+        }
+    }
+    double sn, cs;
+    sincos(ang, &sn, &cs);
+    x = rad * cs;
+    y = rad * sn;
+}
+
+__device__ void stop_point(const TraceParams &P, int u, int v, int a, double &xi, double &et)
+{
+    const int ju = P.per_pixel ? u : 0, jv = P.per_pixel ? v : 0;
+    xi = 0.0;
+    et = 0.0;
+    switch (P.aperture) {
+    case VAMRT_APERTURE_LIST:
+        xi = P.pupil_xy[2 * a];
+        et = P.pupil_xy[2 * a + 1];
+        break;
+    case VAMRT_APERTURE_STRATIFIED: {
+        const int n = P.strat_n, i = a / n, k = a - (a / n) * n;
+        const double s = 2.0 * ((double)i + jitter01(P.seed, ju, jv, a, 0)) / n - 1.0;
+        const double t = 2.0 * ((double)k + jitter01(P.seed, ju, jv, a, 1)) / n - 1.0;
+        square_to_disk(s, t, xi, et);
+        break;
+    }
+    case VAMRT_APERTURE_SUNFLOWER: {
+        const double pi = 3.14159265358979323846;
+        const double golden = pi * (3.0 - sqrt(5.0));
+        const double r = sqrt(((double)a + 0.5) / P.M);
+        const double ang = (double)a * golden + 2.0 * pi * jitter01(P.seed, ju, jv, 0, 0);
+        xi = r * cos(ang);
+        et = r * sin(ang);
+        break;
+    }
+    case VAMRT_APERTURE_HEX: {
+        // hexagonal lattice of spacing 1/2 inside the unit disk: centre, inner ring of 6 at
+        // 1/2, outer ring of 6 at sqrt(3)/2 turned by 30 degrees
+        const double pi = 3.14159265358979323846;
+        if (a >= 1 && a <= 6) {
+            xi = 0.5 * cos((a - 1) * (pi / 3.0));
+            et = 0.5 * sin((a - 1) * (pi / 3.0));
+        } else if (a >= 7) {
+            const double ang = pi / 6.0 + (a - 7) * (pi / 3.0);
+            xi = 0.5 * sqrt(3.0) * cos(ang);
+            et = 0.5 * sqrt(3.0) * sin(ang);
+        }
+        break;
+    }
+    default:   // VAMRT_APERTURE_CHIEF
+        break;
+    }
+}
+
 __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *__restrict__ B,
                                 int2 *__restrict__ J, unsigned long long *__restrict__ counters)
 {
@@ -120,7 +206,8 @@ __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *_
 
     // image point of the pixel in the best-focus plane y = 0
     const d3 Q = {(u - 0.5 * (P.nu - 1)) * P.pu, 0.0, (v - 0.5 * (P.nv - 1)) * P.pv};
-    const double xi = P.pupil_xy[2 * a], et = P.pupil_xy[2 * a + 1];
+    double xi, et;
+    stop_point(P, u, v, a, xi, et);
     d3 o, d;
     if (P.n_surf > 0) {
         // pixel in the object plane, launched telecentric in object space towards the stop

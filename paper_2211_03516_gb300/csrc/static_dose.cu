@@ -9,6 +9,8 @@
 // no cudaFree, no library routine that allocates.
 #include <stdio.h>
 
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -23,25 +25,58 @@ static __device__ __align__(256) float g_static_acc[kStaticAccFloats];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the context the address was looked up in, and the address.
+void *g_acc_ctx[kMaxDevices] = {};
 float *g_acc_addr[kMaxDevices] = {};
 
-// Device address of g_static_acc on the current device.  In host code the array's name
-// is only a host-side stand-in, so the address must come from the runtime, once per
-// device, with that device current.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+// The driver's cuCtxGetCurrent, through the runtime's entry-point query (the library links
+// the static runtime only).  NULL when the driver does not provide it.
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+    });
+    return fn;
+}
+
+}  // namespace
+
+namespace vamrt {
+
+// Device address of g_static_acc on the current device (dev).  In host code the array's
+// name is only a host-side stand-in, so the address must come from the runtime, with the
+// device current.  Looking it up also loads the array's module (the library's modules load
+// lazily), which is what allocates the array on the device; vamrt_make_projector calls
+// this so that the allocation happens there and not in vamrt_forward_dose_static.  The
+// address is cached per device together with the context it was found in, and looked up
+// again when the current context differs (after a device reset).
 cudaError_t static_acc_address(int dev, float **out)
 {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get) get(&ctx);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_acc_addr[dev]) {
+    if (!g_acc_addr[dev] || g_acc_ctx[dev] != (void *)ctx) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_acc);
         if (e != cudaSuccess) return e;
         g_acc_addr[dev] = (float *)ptr;
+        g_acc_ctx[dev] = (void *)ctx;
     }
     *out = g_acc_addr[dev];
     return cudaSuccess;
 }
 
-}  // namespace
+}  // namespace vamrt
 
 extern "C" vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, const void *proj,
                                                   vamrt_dtype proj_dtype, void *dose, vamrt_dtype dose_dtype,
@@ -83,7 +118,7 @@ extern "C" vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, cons
         return VAMRT_EINVAL;
     }
     float *acc = nullptr;
-    cudaError_t e = static_acc_address(dev, &acc);
+    cudaError_t e = vamrt::static_acc_address(dev, &acc);
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's sums: clear the part this grid uses
     if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(float) * p->pad_elems, s);

@@ -54,9 +54,30 @@ vamrt_status validate(const vamrt_geometry *g)
     if (!(g->pupil_mm > 0.0) || isnan(g->pupil_mm)) return fail(VAMRT_EINVAL, "pupil_mm must be > 0 or INFINITY");
     if (!(g->f_number > 0.0) || isnan(g->f_number)) return fail(VAMRT_EINVAL, "f_number must be > 0 or INFINITY");
     if (g->rays_per_pixel < 1 || g->rays_per_pixel > 4096) return fail(VAMRT_EINVAL, "rays_per_pixel must be 1..4096");
-    if (!g->pupil_xy && g->rays_per_pixel != 1)
-        return fail(VAMRT_EINVAL, "pupil_xy may be NULL only with one ray per pixel");
-    if (g->pupil_xy)
+    if (g->aperture_flags & ~VAMRT_JITTER_PER_PIXEL) return fail(VAMRT_EINVAL, "unknown aperture_flags");
+    switch (g->aperture) {
+    case VAMRT_APERTURE_LIST:
+        if (!g->pupil_xy && g->rays_per_pixel != 1)
+            return fail(VAMRT_EINVAL, "pupil_xy may be NULL only with one ray per pixel");
+        break;
+    case VAMRT_APERTURE_CHIEF:
+        if (g->rays_per_pixel != 1) return fail(VAMRT_EINVAL, "the chief-ray aperture has one ray per pixel");
+        break;
+    case VAMRT_APERTURE_STRATIFIED: {
+        const int n = (int)lround(sqrt((double)g->rays_per_pixel));
+        if (n * n != g->rays_per_pixel) return fail(VAMRT_EINVAL, "stratified aperture needs n^2 rays per pixel");
+        break;
+    }
+    case VAMRT_APERTURE_SUNFLOWER:
+        break;
+    case VAMRT_APERTURE_HEX:
+        if (g->rays_per_pixel != 13) return fail(VAMRT_EINVAL, "the hexagonal aperture has 13 rays per pixel");
+        break;
+    default:
+        return fail(VAMRT_EINVAL, "unknown aperture pattern %d", g->aperture);
+    }
+    if (g->nu >= (1 << 20) || g->nv >= (1 << 20)) return fail(VAMRT_EINVAL, "nu and nv must be below 2^20");
+    if (g->aperture == VAMRT_APERTURE_LIST && g->pupil_xy)
         for (int a = 0; a < g->rays_per_pixel; ++a) {
             const double x = g->pupil_xy[2 * a], y = g->pupil_xy[2 * a + 1];
             if (!isfinite(x) || !isfinite(y) || x * x + y * y > 1.0 + 1e-12)
@@ -185,7 +206,7 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     if (!p) return fail(VAMRT_ENOMEM, "host allocation failed");
     Guard guard{p};
     p->g = *geom;
-    p->g.pupil_xy = nullptr;
+    p->g.pupil_xy = nullptr;          // host arrays, used only while tracing below
     p->g.angles_rad = nullptr;
     p->g.surfaces = nullptr;          // host array, used only while tracing below
     if (p->g.step_vox == 0.0) p->g.step_vox = 0.5;
@@ -194,6 +215,12 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
 
     CK(cudaGetDevice(&p->device), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device), "cudaDeviceGetAttribute");
+    {
+        // load the allocation-free dose entry point's static accumulator here, where
+        // allocating is expected, so that vamrt_forward_dose_static never allocates
+        float *static_acc = nullptr;
+        CK(vamrt::static_acc_address(p->device, &static_acc), "static accumulator");
+    }
     p->n_rays = (int64_t)g.nu * g.nv * M;
     const int px = ((g.nx + 2 + 3) / 4) * 4;   // rows padded to 16-byte groups
     p->pad_elems = (int64_t)px * (g.ny + 2) * (g.nz + 2);
@@ -206,7 +233,7 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     CK(cudaMalloc(&p->red, sizeof(double) * (vamrt::kRedBlocks + 8)), "cudaMalloc(reduction)");
     CK(cudaMalloc(&p->hist, sizeof(double) * vamrt::kMaxHistory), "cudaMalloc(history)");
     CK(cudaMalloc(&p->dmax, sizeof(float) * 4), "cudaMalloc(dmax)");
-    CK(cudaMallocHost(&p->host_err, sizeof(double)), "cudaMallocHost");
+    CK(cudaMallocHost(&p->host_err, 4 * sizeof(double)), "cudaMallocHost");   // E and the 3 VER counts
     p->device_bytes = (sizeof(float4) * 2 + sizeof(int2)) * (uint64_t)p->n_rays + sizeof(double2) * g.n_angles +
                       sizeof(float) * (uint64_t)p->pad_elems;
 
@@ -240,14 +267,19 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     double *d_pupil = (double *)tmp;
     double *d_surf = d_pupil + 2 * M;
     unsigned long long *d_cnt = (unsigned long long *)((char *)tmp + pupil_bytes + surf_bytes);
-    double chief[2] = {0.0, 0.0};
-    e = cudaMemcpyAsync(d_pupil, geom->pupil_xy ? geom->pupil_xy : chief, pupil_bytes, cudaMemcpyHostToDevice, s);
+    const bool listed = geom->aperture == VAMRT_APERTURE_LIST && geom->pupil_xy;
+    e = listed ? cudaMemcpyAsync(d_pupil, geom->pupil_xy, pupil_bytes, cudaMemcpyHostToDevice, s)
+               : cudaMemsetAsync(d_pupil, 0, pupil_bytes, s);
     if (e == cudaSuccess && n_surf > 0)
         e = cudaMemcpyAsync(d_surf, hsurf.data(), surf_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s);
 
     vamrt::TraceParams T;
     T.pupil_xy = d_pupil;
+    T.aperture = geom->aperture;
+    T.per_pixel = (geom->aperture_flags & VAMRT_JITTER_PER_PIXEL) ? 1 : 0;
+    T.seed = geom->seed;
+    T.strat_n = (int)lround(sqrt((double)M));
     T.nu = g.nu; T.nv = g.nv; T.M = M; T.nz = g.nz;
     T.pu = g.pixel_u_mm; T.pv = g.pixel_v_mm;
     T.pupil_mm = g.pupil_mm; T.f_number = g.f_number;
@@ -353,6 +385,8 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         return fail(VAMRT_EINVAL, "momentum must be in [0, 1)");
     if (params->momentum != 0.0 && (params->mode != VAMRT_OPT_OBJECT || !params->prev_model))
         return fail(VAMRT_EINVAL, "momentum needs object mode and a prev_model buffer");
+    if (params->stop != VAMRT_STOP_VER && params->stop != VAMRT_STOP_ERROR)
+        return fail(VAMRT_EINVAL, "unknown stop criterion %d", params->stop);
     cudaStream_t s = (cudaStream_t)stream;
     double *fsum = p->red + vamrt::kRedBlocks;
     // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration
@@ -366,8 +400,15 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]), "cudaEventCreate");
     CK(vamrt::launch_sum(p, target, fsum, s), "target sum");
     int it = 0;
-    double err = NAN;
+    double err = NAN, ver = NAN;
     bool converged = false;
+    std::vector<double> vers((size_t)params->max_iter, NAN);
+    long long *ver3 = reinterpret_cast<long long *>(p->red + vamrt::kRedBlocks + 5);
+    struct Checked {
+        double err;
+        long long ver3[3];
+    };
+    Checked *host_chk = reinterpret_cast<Checked *>(p->host_err);
     const bool proj_space = params->mode == VAMRT_OPT_PROJECTIONS;
     for (; it < params->max_iter;) {
         if (params->timing) CK(cudaEventRecord(ev[0], s), "cudaEventRecord");
@@ -401,14 +442,19 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         }
         ++it;
         if (it % params->check_every == 0 || it == params->max_iter) {
-            CK(cudaMemcpyAsync(p->host_err, p->hist + it - 1, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+            // the voxel error rate of this iteration's normalised dose, then E and V together
+            CK(vamrt::launch_ver(p, dose, params->dose_dtype, target, ver3, s), "voxel error rate kernels");
+            CK(cudaMemcpyAsync(&host_chk->err, p->hist + it - 1, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaMemcpyAsync(host_chk->ver3, ver3, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy");
             CK(cudaStreamSynchronize(s), "sync");
-            err = *p->host_err;
+            err = host_chk->err;
+            ver = host_chk->ver3[2] > 0 ? (double)host_chk->ver3[0] / (double)host_chk->ver3[2] : 0.0;
+            vers[it - 1] = ver;
             if (!isfinite(err)) {
-                if (report) { report->iterations = it; report->final_error = err; }
+                if (report) { report->iterations = it; report->final_error = err; report->final_ver = ver; }
                 return fail(VAMRT_NUMERIC, "dose error is not finite at iteration %d (zero or NaN dose)", it);
             }
-            if (err < params->tol) { converged = true; break; }
+            if ((params->stop == VAMRT_STOP_VER ? ver : err) < params->tol) { converged = true; break; }
         }
     }
     if (report) {
@@ -417,6 +463,9 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         report->adjoint_ms = t_adj;
         report->forward_ms = t_fwd;
         report->update_ms = t_upd;
+        report->final_ver = ver;
+        if (report->ver_history)
+            for (int i = 0; i < it; ++i) report->ver_history[i] = vers[(size_t)i];
         if (report->error_history) {
             CK(cudaMemcpyAsync(report->error_history, p->hist, sizeof(double) * it, cudaMemcpyDeviceToHost, s), "copy");
             CK(cudaStreamSynchronize(s), "sync");

@@ -1,6 +1,6 @@
 // Voxel error rate of a dose against a binary target: the fraction of resin voxels whose
 // printed state (dose above a threshold) differs from the target, at the best of 1023
-// thresholds tau_i = (i / 1024) max(dose), i = 1..1023.  It measures how well a dose
+// thresholds tau_i = (i / 1024) max(dose), i = 1..1023, the maximum taken over the resin.  It measures how well a dose
 // prints the part independently of the dose's scale, the quantity the optimiser's
 // stopping rule is after (Sec. 2.7).
 //
@@ -21,12 +21,19 @@ constexpr int kVerThreads = 256;
 __device__ __forceinline__ float ldd(const float *p) { return *p; }
 __device__ __forceinline__ float ldd(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
+// maximum over the resin voxels (the same FP64 test as the histogram below)
 template <typename DT>
-__global__ void dose_max_kernel(const DT *__restrict__ dose, int64_t n, float *__restrict__ out)
+__global__ void dose_max_kernel(const DT *__restrict__ dose, int nx, int ny, int nz, double h, double r2,
+                                float *__restrict__ out)
 {
+    const int64_t n = (int64_t)nx * ny * nz;
     float m = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny);
+        const double cx = (x - 0.5 * (nx - 1)) * h, cy = (y - 0.5 * (ny - 1)) * h;
+        if (__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)) > r2) continue;
         m = fmaxf(m, ldd(dose + i));
+    }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));   // m >= 0
 }
@@ -96,11 +103,13 @@ cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype d
     if (g > (unsigned)p->num_sms * 8u) g = (unsigned)p->num_sms * 8u;
     const double r2 = p->g.r_inner_mm * p->g.r_inner_mm;
     if (dt == VAMRT_F32) {
-        dose_max_kernel<float><<<g, kVerThreads, 0, s>>>((const float *)dose, n, p->dmax);
+        dose_max_kernel<float><<<g, kVerThreads, 0, s>>>((const float *)dose, nx, ny, nz, p->g.voxel_mm, r2,
+                                                          p->dmax);
         ver_hist_kernel<float><<<g, kVerThreads, 0, s>>>((const float *)dose, target, nx, ny, nz, p->g.voxel_mm, r2,
                                                           p->dmax, hist);
     } else {
-        dose_max_kernel<__nv_bfloat16><<<g, kVerThreads, 0, s>>>((const __nv_bfloat16 *)dose, n, p->dmax);
+        dose_max_kernel<__nv_bfloat16><<<g, kVerThreads, 0, s>>>((const __nv_bfloat16 *)dose, nx, ny, nz,
+                                                                  p->g.voxel_mm, r2, p->dmax);
         ver_hist_kernel<__nv_bfloat16><<<g, kVerThreads, 0, s>>>((const __nv_bfloat16 *)dose, target, nx, ny, nz,
                                                                   p->g.voxel_mm, r2, p->dmax, hist);
     }

@@ -113,7 +113,7 @@ class Workload:
     n_angles: int
     pupil_mm: float
     f_number: float
-    pupil_pattern: str  # chief | stratified4x4 | sunflower | hex13 | stratified<n>x<n>
+    pupil_pattern: str  # chief | stratified<n>x<n> | sunflower | hex13
     rays_per_pixel: int
     r_inner_mm: float
     wall_mm: float
@@ -126,6 +126,7 @@ class Workload:
     seed: int = 0
     osmo_iters: int = 10
     lens: Optional[LensTrain] = None   # a lens train replacing the ideal pupil model
+    jitter_per_pixel: Optional[bool] = None   # None: per pixel for stratified, shared otherwise
 
     def scaled(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -180,75 +181,61 @@ MID = WORKLOADS["mid_256cube_360ang_16rays"]
 
 
 # ----------------------------------------------------------------------------------
-# aperture-stop sample patterns (points in the unit disk, one set shared by all pixels)
+# aperture-stop sampling: which pattern a projector uses (the points themselves are
+# generated inside the CUDA library and, independently, inside the oracle)
 # ----------------------------------------------------------------------------------
-def _concentric_disk(a: np.ndarray, b: np.ndarray):
-    """Shirley-Chiu concentric map of [-1,1]^2 onto the unit disk."""
-    x = np.zeros_like(a)
-    y = np.zeros_like(a)
-    for i in range(a.size):
-        p, q = a.flat[i], b.flat[i]
-        if p == 0.0 and q == 0.0:
-            r, phi = 0.0, 0.0
-        elif abs(p) > abs(q):
-            r, phi = p, (math.pi / 4.0) * (q / p)
-        else:
-            r, phi = q, (math.pi / 2.0) - (math.pi / 4.0) * (p / q)
-        x.flat[i] = r * math.cos(phi)
-        y.flat[i] = r * math.sin(phi)
-    return x, y
+@dataclass(frozen=True)
+class Aperture:
+    """The aperture-stop samples of a projector, by name (Sec. 2.1: rays leave points of
+    the stop).  pattern: "chief" (one ray, the stop's centre), "stratified" (n x n
+    jittered strata, n_rays = n^2), "sunflower" (golden-angle spiral) or "hex13" (the
+    paper's hexagonal filling, 13 rays).  seed and per_pixel select the jitter draws.
+    Holds no sample positions: both the library and the oracle generate them."""
+
+    pattern: str
+    n_rays: int
+    seed: int = 0
+    per_pixel: bool = False
+
+
+def workload_pupil(w: Workload) -> Aperture:
+    """The workload's aperture pattern.  Stratified jitter is drawn per pixel (the 4 x 4
+    'stratified jitter' of the 256^3 workload); the sunflower's turn is shared by every
+    pixel, so that ray a of neighbouring pixels leaves nearly the same stop point (set
+    jitter_per_pixel to draw it per pixel)."""
+    pat = w.pupil_pattern
+    kind = "stratified" if pat.startswith("stratified") else pat
+    if kind not in ("chief", "stratified", "sunflower", "hex13"):
+        raise ValueError(f"unknown pupil pattern {pat!r}")
+    if kind == "stratified":
+        n = int(pat[len("stratified"):].split("x")[0])
+        if n * n != w.rays_per_pixel:
+            raise ValueError(f"{pat} needs {n * n} rays, got {w.rays_per_pixel}")
+    if kind == "chief" and w.rays_per_pixel != 1:
+        raise ValueError("chief pattern has exactly one ray")
+    if kind == "hex13" and w.rays_per_pixel != 13:
+        raise ValueError("hex13 has 13 rays")
+    per_pixel = (kind == "stratified") if w.jitter_per_pixel is None else bool(w.jitter_per_pixel)
+    return Aperture(kind, w.rays_per_pixel, w.seed, per_pixel)
 
 
 def pupil_samples(pattern: str, m: int, seed: int = 0) -> np.ndarray:
-    """(m, 2) float64 array of aperture-stop positions (xi, eta) in the unit disk.
-
-    chief          : the single point (0, 0), a zero-etendue pixel.
-    stratified<n>x<n>: one jittered point per cell of an n x n grid on [-1,1]^2, mapped
-                     to the disk by the concentric map.
-    sunflower      : golden-angle spiral r = sqrt((a+1/2)/m), phase jittered by one
-                     seeded rotation.
-    hex13          : hexagonal filling (Sec. 2.1): centre, 6 points at r=1/2, 6 at
-                     r=sqrt(3)/2 (a hex lattice of spacing 1/2 clipped to the disk).
-    """
-    rng = np.random.default_rng(seed)
+    """An explicit (m, 2) float64 list of stop points (xi, eta), passed to a projector in
+    place of a named pattern: "chief" = the single point (0, 0); "disk" = m seeded points
+    drawn uniformly in the unit disk (rejection from the square)."""
     if pattern == "chief":
         if m != 1:
             raise ValueError("chief pattern has exactly one ray")
         return np.zeros((1, 2))
-    if pattern.startswith("stratified"):
-        n = int(pattern[len("stratified"):].split("x")[0])
-        if n * n != m:
-            raise ValueError(f"{pattern} needs {n*n} rays, got {m}")
-        i, k = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
-        j = rng.random((2, n, n))
-        a = 2.0 * (i + j[0]) / n - 1.0
-        b = 2.0 * (k + j[1]) / n - 1.0
-        x, y = _concentric_disk(a.ravel(), b.ravel())
-        return np.stack([x, y], axis=1)
-    if pattern == "sunflower":
-        golden = math.pi * (3.0 - math.sqrt(5.0))
-        phase = 2.0 * math.pi * rng.random()
-        a = np.arange(m)
-        r = np.sqrt((a + 0.5) / m)
-        phi = a * golden + phase
-        return np.stack([r * np.cos(phi), r * np.sin(phi)], axis=1)
-    if pattern == "hex13":
-        if m != 13:
-            raise ValueError("hex13 has 13 rays")
-        pts = [(0.0, 0.0)]
-        for k in range(6):
-            t = k * math.pi / 3.0
-            pts.append((0.5 * math.cos(t), 0.5 * math.sin(t)))
-        for k in range(6):
-            t = math.pi / 6.0 + k * math.pi / 3.0
-            r = math.sqrt(3.0) / 2.0
-            pts.append((r * math.cos(t), r * math.sin(t)))
+    if pattern == "disk":
+        rng = np.random.default_rng(seed)
+        pts = []
+        while len(pts) < m:
+            x, y = rng.uniform(-1.0, 1.0, size=2)
+            if x * x + y * y <= 1.0:
+                pts.append((x, y))
         return np.array(pts)
-    raise ValueError(f"unknown pupil pattern {pattern!r}")
-
-
-def workload_pupil(w: Workload) -> np.ndarray:
-    return pupil_samples(w.pupil_pattern, w.rays_per_pixel, w.seed)
+    raise ValueError(f"unknown explicit pupil list {pattern!r}")
 
 
 # Fin part (Sec. 3: 1 mm fins at a 2.25 mm period, normal to the vial axis, on a base at
@@ -351,32 +338,75 @@ def _rand_centre(rng, w: Workload, extent: float, reach: float):
     return (rad * math.cos(phi), rad * math.sin(phi), rng.uniform(-zmax, zmax))
 
 
+def _axis(n: int, h: float, i0: int = 0, i1: Optional[int] = None) -> np.ndarray:
+    """Voxel-centre coordinates (i - (n-1)/2) h of indices i0 .. i1-1 (the values
+    voxel_centres gives, computed the same way)."""
+    return (np.arange(i0, n if i1 is None else i1) - (n - 1) / 2.0) * h
+
+
+class _Grid:
+    """Broadcastable voxel-centre coordinates and bounded sub-box evaluation of a primitive:
+    a primitive whose points all lie within `extent` mm of its centre is evaluated only on
+    the index box that covers that ball, with coordinates computed exactly as on the full
+    grid, so the result equals a full-grid evaluation."""
+
+    def __init__(self, w: Workload):
+        self.w = w
+        self.n = (w.nx, w.ny, w.nz)
+        self.h = w.voxel_mm
+        self.X = _axis(w.nx, self.h)[None, None, :]
+        self.Y = _axis(w.ny, self.h)[None, :, None]
+        self.Z = _axis(w.nz, self.h)[:, None, None]
+
+    def _range(self, ax: int, c: float, extent: float):
+        n = self.n[ax]
+        lo = int(math.floor((c - extent) / self.h + (n - 1) / 2.0)) - 1
+        hi = int(math.ceil((c + extent) / self.h + (n - 1) / 2.0)) + 2
+        return max(lo, 0), min(hi, n)
+
+    def apply(self, m: np.ndarray, fn, c, extent: float, union: bool = True):
+        """m |= fn(Z, Y, X) (union) or m &= ~fn(Z, Y, X) inside the primitive's box."""
+        (x0, x1), (y0, y1), (z0, z1) = (self._range(a, c[a], extent) for a in range(3))
+        if x0 >= x1 or y0 >= y1 or z0 >= z1:
+            return
+        h = self.h
+        Z = _axis(self.n[2], h, z0, z1)[:, None, None]
+        Y = _axis(self.n[1], h, y0, y1)[None, :, None]
+        X = _axis(self.n[0], h, x0, x1)[None, None, :]
+        p = fn(Z, Y, X)
+        if union:
+            m[z0:z1, y0:y1, x0:x1] |= p
+        else:
+            m[z0:z1, y0:y1, x0:x1] &= ~p
+
+
 def make_target(w: Workload, kind: Optional[str] = None, seed: Optional[int] = None) -> np.ndarray:
     kind = kind or w.target
     seed = w.seed if seed is None else seed
     rng = np.random.default_rng(seed + 1000)
-    Z, Y, X = voxel_centres(w)
+    G = _Grid(w)
+    Z, Y, X = G.Z, G.Y, G.X          # broadcastable [nz,1,1], [1,ny,1], [1,1,nx]
     reach = reach_radius(w)
+    m = np.zeros(w.vol_shape, dtype=bool)
     if kind == "sphere_cube":
         # sphere r = 4 mm centred (0,0,-1.5) united with a 3 mm cube centred (1,1,3.5)
-        m = _sphere(Z, Y, X, (0.0, 0.0, -1.5), 4.0) | _box(Z, Y, X, (1.0, 1.0, 3.5), (1.5, 1.5, 1.5))
+        m |= _sphere(Z, Y, X, (0.0, 0.0, -1.5), 4.0) | _box(Z, Y, X, (1.0, 1.0, 3.5), (1.5, 1.5, 1.5))
     elif kind == "spheres_tori12":
-        m = np.zeros(X.shape, dtype=bool)
         for k in range(12):
             if k % 2 == 0:
                 r = rng.uniform(1.0, 5.0)
                 c = _rand_centre(rng, w, r, reach)
-                m |= _sphere(Z, Y, X, c, r)
+                G.apply(m, lambda Z, Y, X, c=c, r=r: _sphere(Z, Y, X, c, r), c, r)
             else:
                 R = rng.uniform(1.0, 5.0)
                 r = rng.uniform(0.35, 0.3 * R + 0.35)
                 c = _rand_centre(rng, w, R + r, reach)
-                m |= _torus(Z, Y, X, c, _rand_axis(rng), R, r)
+                ax = _rand_axis(rng)
+                G.apply(m, lambda Z, Y, X, c=c, ax=ax, R=R, r=r: _torus(Z, Y, X, c, ax, R, r), c, R + r)
     elif kind == "strut_lattice":
         cell, beam = 4.0, 0.5
         off = rng.uniform(0.0, cell, size=3)
         keep = 0.75
-        m = np.zeros(X.shape, dtype=bool)
         # beams along x, y and z through the lattice points; each beam family keeps a
         # seeded random subset of the lines
         gx = np.mod(X - off[0] + cell / 2, cell) - cell / 2
@@ -401,36 +431,34 @@ def make_target(w: Workload, kind: Optional[str] = None, seed: Optional[int] = N
     elif kind in ("csg", "csg_shells"):
         n_prim = 40 if kind == "csg_shells" else int(rng.integers(3, 7))
         scale = min(reach, w.nz * w.voxel_mm / 2.0)
-        m = np.zeros(X.shape, dtype=bool)
         for k in range(n_prim):
             t = rng.integers(0, 3)
             if t == 0:
                 r = rng.uniform(0.12, 0.35) * scale
                 c = _rand_centre(rng, w, r, reach)
-                p = _sphere(Z, Y, X, c, r)
+                fn, ext = (lambda Z, Y, X, c=c, r=r: _sphere(Z, Y, X, c, r)), r
             elif t == 1:
                 half = rng.uniform(0.08, 0.3, size=3) * scale
-                c = _rand_centre(rng, w, float(np.linalg.norm(half)), reach)
-                p = _box(Z, Y, X, c, half)
+                ext = float(np.linalg.norm(half))
+                c = _rand_centre(rng, w, ext, reach)
+                fn = lambda Z, Y, X, c=c, half=half: _box(Z, Y, X, c, half)  # noqa: E731
             else:
                 R = rng.uniform(0.15, 0.35) * scale
                 r = rng.uniform(0.25, 0.5) * R
                 c = _rand_centre(rng, w, R + r, reach)
-                p = _torus(Z, Y, X, c, _rand_axis(rng), R, r)
+                ax = _rand_axis(rng)
+                fn, ext = (lambda Z, Y, X, c=c, ax=ax, R=R, r=r: _torus(Z, Y, X, c, ax, R, r)), R + r
             if kind == "csg_shells" and k % 4 == 3 and t == 0:
                 # thin-walled shell of 0.3 mm
-                inner = _sphere(Z, Y, X, c, max(r - 0.3, 0.0))
-                p = p & ~inner
-            if k > 0 and rng.random() < 0.25:
-                m &= ~p  # difference
-            else:
-                m |= p
+                ri = max(r - 0.3, 0.0)
+                fn = lambda Z, Y, X, c=c, r=r, ri=ri: _sphere(Z, Y, X, c, r) & ~_sphere(Z, Y, X, c, ri)  # noqa: E731
+            G.apply(m, fn, c, ext, union=not (k > 0 and rng.random() < 0.25))
         m &= X * X + Y * Y <= reach * reach
     elif kind.startswith("fins"):
         n_fins = int(kind[4:])
         hx = FIN_HALF_MM
         zt = float(fin_bottoms_mm(n_fins)[-1]) + FIN_THICK_MM
-        m = _box(Z, Y, X, (0.0, 0.0, FIN_BASE_MM / 2), (hx, hx, FIN_BASE_MM / 2))           # base
+        m |= _box(Z, Y, X, (0.0, 0.0, FIN_BASE_MM / 2), (hx, hx, FIN_BASE_MM / 2))           # base
         m |= _box(Z, Y, X, (0.0, hx - 0.5, zt / 2), (hx, 0.5, zt / 2))                      # spine
         for zb in fin_bottoms_mm(n_fins):
             m |= _box(Z, Y, X, (0.0, 0.0, zb + FIN_THICK_MM / 2), (hx, hx, FIN_THICK_MM / 2))

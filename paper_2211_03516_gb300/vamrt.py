@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libvamrt.so")
 VAMRT_OK, VAMRT_EINVAL, VAMRT_EUNSUPPORTED, VAMRT_ECUDA, VAMRT_ENOMEM, VAMRT_NOT_CONVERGED, VAMRT_NUMERIC = range(7)
 VAMRT_F32, VAMRT_BF16 = 0, 1
 VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG, VAMRT_UNATTENUATED = 1, 2, 4
+VAMRT_APERTURE = {"list": 0, "chief": 1, "stratified": 2, "sunflower": 3, "hex13": 4}
+VAMRT_JITTER_PER_PIXEL = 1
 
 _DTYPES = {torch.float32: VAMRT_F32, torch.bfloat16: VAMRT_BF16}
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -53,6 +55,7 @@ class Geometry(ctypes.Structure):
         ("step_vox", ctypes.c_double),
         ("n_surfaces", ctypes.c_int32), ("surfaces", ctypes.POINTER(Surface)),
         ("object_y_mm", ctypes.c_double), ("magnification", ctypes.c_double), ("aim_mm", ctypes.c_double),
+        ("aperture", ctypes.c_int32), ("aperture_flags", ctypes.c_uint32), ("seed", ctypes.c_uint64),
     ]
 
 
@@ -65,12 +68,13 @@ class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("check_every", ctypes.c_int32),
                 ("proj_dtype", ctypes.c_int), ("dose_dtype", ctypes.c_int), ("timing", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("step", ctypes.c_double), ("momentum", ctypes.c_double),
-                ("prev_model", ctypes.c_void_p)]
+                ("prev_model", ctypes.c_void_p), ("stop", ctypes.c_int32)]
 
 
 class OptReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("final_error", ctypes.c_double), ("error_history", _dp),
-                ("adjoint_ms", ctypes.c_double), ("forward_ms", ctypes.c_double), ("update_ms", ctypes.c_double)]
+                ("adjoint_ms", ctypes.c_double), ("forward_ms", ctypes.c_double), ("update_ms", ctypes.c_double),
+                ("final_ver", ctypes.c_double), ("ver_history", _dp)]
 
 
 _lib = None
@@ -106,6 +110,8 @@ def lib() -> ctypes.CDLL:
         L.vamrt_export_u8.restype = i32
         L.vamrt_measure_smem_bandwidth.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
         L.vamrt_measure_smem_bandwidth.restype = i32
+        L.vamrt_measure_l2_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+        L.vamrt_measure_l2_rates.restype = i32
         L.vamrt_ramlak_filter.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, u32, vp]
         L.vamrt_ramlak_filter.restype = i32
         L.vamrt_launch_count.argtypes = []
@@ -156,7 +162,7 @@ class GeometrySpec:
     pixel_v_mm: float
     pupil_mm: float
     f_number: float
-    pupil_xy: np.ndarray
+    pupil: object                # a named aperture pattern (inputs.Aperture) or an explicit (m, 2) list
     r_inner_mm: float
     wall_mm: float
     n_outside: float
@@ -169,10 +175,12 @@ class GeometrySpec:
     lens: object = None          # inputs.LensTrain or None (ideal pupil)
 
     @classmethod
-    def from_workload(cls, w, pupil_xy, angles_rad=None) -> "GeometrySpec":
+    def from_workload(cls, w, pupil, angles_rad=None) -> "GeometrySpec":
+        if not hasattr(pupil, "pattern"):
+            pupil = np.asarray(pupil, dtype=np.float64).reshape(-1, 2)
         return cls(nx=w.nx, ny=w.ny, nz=w.nz, voxel_mm=w.voxel_mm, nu=w.nu, nv=w.nv,
                    pixel_u_mm=w.pixel_u_mm, pixel_v_mm=w.pixel_v_mm, pupil_mm=w.pupil_mm,
-                   f_number=w.f_number, pupil_xy=np.asarray(pupil_xy, dtype=np.float64).reshape(-1, 2),
+                   f_number=w.f_number, pupil=pupil,
                    r_inner_mm=w.r_inner_mm, wall_mm=w.wall_mm, n_outside=w.n_outside,
                    n_glass=w.n_glass, n_resin=w.n_resin, mu_per_mm=w.mu_per_mm,
                    n_angles=w.n_angles if angles_rad is None else len(angles_rad),
@@ -185,7 +193,7 @@ def _to_struct(spec: GeometrySpec):
     g = Geometry()
     for name, _ in Geometry._fields_:
         if name in ("pupil_xy", "angles_rad", "rays_per_pixel", "n_surfaces", "surfaces", "object_y_mm",
-                    "magnification", "aim_mm"):
+                    "magnification", "aim_mm", "aperture", "aperture_flags", "seed"):
             continue
         setattr(g, name, getattr(spec, name))
     if spec.lens is not None:
@@ -197,10 +205,18 @@ def _to_struct(spec: GeometrySpec):
         g.object_y_mm = spec.lens.object_y_mm
         g.magnification = spec.lens.magnification
         g.aim_mm = spec.lens.aim_mm
-    pupil = np.ascontiguousarray(spec.pupil_xy, dtype=np.float64).reshape(-1, 2)
-    keep.append(pupil)
-    g.rays_per_pixel = pupil.shape[0]
-    g.pupil_xy = pupil.ctypes.data_as(_dp)
+    if hasattr(spec.pupil, "pattern"):
+        g.aperture = VAMRT_APERTURE[spec.pupil.pattern]
+        g.aperture_flags = VAMRT_JITTER_PER_PIXEL if spec.pupil.per_pixel else 0
+        g.seed = int(spec.pupil.seed) & 0xFFFFFFFFFFFFFFFF
+        g.rays_per_pixel = int(spec.pupil.n_rays)
+        g.pupil_xy = None
+    else:
+        pupil = np.ascontiguousarray(spec.pupil, dtype=np.float64).reshape(-1, 2)
+        keep.append(pupil)
+        g.aperture = VAMRT_APERTURE["list"]
+        g.rays_per_pixel = pupil.shape[0]
+        g.pupil_xy = pupil.ctypes.data_as(_dp)
     if spec.angles_rad is not None:
         ang = np.ascontiguousarray(spec.angles_rad, dtype=np.float64)
         keep.append(ang)
@@ -229,8 +245,8 @@ class Projector:
         self.proj_shape = (spec.n_angles, spec.nv, spec.nu)
 
     @classmethod
-    def from_workload(cls, w, pupil_xy, angles_rad=None, stream=None) -> "Projector":
-        return cls(GeometrySpec.from_workload(w, pupil_xy, angles_rad), stream)
+    def from_workload(cls, w, pupil, angles_rad=None, stream=None) -> "Projector":
+        return cls(GeometrySpec.from_workload(w, pupil, angles_rad), stream)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -323,14 +339,17 @@ class Projector:
 
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,
-                 timing=False, mode="object", step=1.0, momentum=0.0, prev_model=None, stream=None) -> dict:
+                 timing=False, mode="object", step=1.0, momentum=0.0, prev_model=None, stop="ver",
+                 stream=None) -> dict:
         """Projection optimisation (vamrt_optimize).  Returns g, dn, model, errors, converged.
         mode "object": OSMO on the model (model in = m0, default the target), model step
         `step` (1 = the plain update) and heavy-ball `momentum` (0 = none), whose previous
         model lives in prev_model (in: the model before m0 -- a copy of m0 to start at rest,
         made here when prev_model is None; out: updated; pass the same buffer back to keep
         momentum across calls);
-        mode "projections": iterate on proj (in = g0, required), model = workspace."""
+        mode "projections": iterate on proj (in = g0, required), model = workspace.
+        stop: "ver" (the voxel error rate V < tol, the reading of Sec. 2.7's stop) or
+        "error" (the dose's L1 error E < tol); `vers` holds V of the checked iterations."""
         if mode not in ("object", "projections"):
             raise ValueError("mode must be 'object' or 'projections'")
         if mode == "projections" and proj is None:
@@ -351,12 +370,15 @@ class Projector:
         params = OptParams(max_iter=max_iter, tol=tol, check_every=check_every, proj_dtype=_DTYPES[proj.dtype],
                            dose_dtype=_DTYPES[dose.dtype], timing=1 if timing else 0,
                            mode=0 if mode == "object" else 1, step=float(step), momentum=float(momentum),
-                           prev_model=pm)
+                           prev_model=pm, stop={"ver": 0, "error": 1}[stop])
         hist = np.zeros(max_iter, dtype=np.float64)
-        rep = OptReport(iterations=0, final_error=math.nan, error_history=hist.ctypes.data_as(_dp))
+        vhist = np.full(max_iter, np.nan)
+        rep = OptReport(iterations=0, final_error=math.nan, error_history=hist.ctypes.data_as(_dp),
+                        final_ver=math.nan, ver_history=vhist.ctypes.data_as(_dp))
         st = _check(lib().vamrt_optimize(self.handle, tp, mp, pp, dp, ctypes.byref(params), ctypes.byref(rep),
                                          _stream(stream)), "vamrt_optimize", ok=(VAMRT_OK, VAMRT_NOT_CONVERGED))
         return dict(proj=proj, dose=dose, model=model, prev_model=prev_model, errors=hist[:rep.iterations].copy(),
+                    vers=vhist[:rep.iterations].copy(), final_ver=rep.final_ver,
                     iterations=rep.iterations, final_error=rep.final_error, converged=(st == VAMRT_OK),
                     adjoint_ms=rep.adjoint_ms, forward_ms=rep.forward_ms, update_ms=rep.update_ms)
 
@@ -385,6 +407,14 @@ def vamrt_measure_smem_bandwidth(stream=None) -> float:
     out = ctypes.c_double()
     _check(lib().vamrt_measure_smem_bandwidth(ctypes.byref(out), _stream(stream)), "vamrt_measure_smem_bandwidth")
     return float(out.value)
+
+
+def vamrt_measure_l2_rates(stream=None):
+    """(L2 read bandwidth in bytes/s, L2 16-byte vector reductions per s) of the current GPU."""
+    rd, red = ctypes.c_double(), ctypes.c_double()
+    _check(lib().vamrt_measure_l2_rates(ctypes.byref(rd), ctypes.byref(red), _stream(stream)),
+           "vamrt_measure_l2_rates")
+    return float(rd.value), float(red.value)
 
 
 def vamrt_launch_count() -> int:

@@ -110,9 +110,33 @@ def test_make_projector_rejects_bad_lens_train(L, lens, msg):
 def test_make_projector_rejects_pupil_outside_disk(L):
     from paper_2211_03516_gb300 import vamrt
     spec = _spec()
-    spec.pupil_xy = np.array([[0.9, 0.9]])
+    spec.pupil = np.array([[0.9, 0.9]])
     with pytest.raises(vamrt.VamrtError, match="unit disk"):
         vamrt.vamrt_make_projector(spec)
+
+
+@pytest.mark.parametrize("pattern,n,msg", [("stratified", 15, r"n\^2 rays"), ("hex13", 12, "13 rays"),
+                                           ("chief", 2, "one ray")])
+def test_make_projector_rejects_bad_aperture(L, pattern, n, msg):
+    """Named aperture patterns are checked on the host: a stratified pattern needs a square
+    ray count, the hexagonal filling 13 rays, the chief ray one."""
+    from paper_2211_03516_gb300 import inputs as I
+    from paper_2211_03516_gb300 import vamrt
+    spec = _spec()
+    spec.pupil = I.Aperture(pattern, n, seed=1, per_pixel=True)
+    with pytest.raises(vamrt.VamrtError, match=msg):
+        vamrt.vamrt_make_projector(spec)
+
+
+def test_make_projector_rejects_unknown_aperture_code_and_flags(L):
+    from paper_2211_03516_gb300 import vamrt
+    for field, value, msg in (("aperture", 9, "unknown aperture pattern"), ("aperture_flags", 2, "aperture_flags")):
+        g, keep = vamrt._to_struct(_spec())
+        setattr(g, field, value)
+        h = ctypes.c_void_p()
+        assert L.vamrt_make_projector(ctypes.byref(g), None, ctypes.byref(h)) == vamrt.VAMRT_EINVAL
+        L.vamrt_last_error.restype = ctypes.c_char_p
+        assert msg in L.vamrt_last_error().decode()
 
 
 def test_null_arguments_are_einval(L):

@@ -37,6 +37,12 @@ def vamrt():
     return V
 
 
+def resin_mask(w):
+    """Resin voxels: centres within the inner radius of the vial axis."""
+    Z, Y, X = I.voxel_centres(w)
+    return X ** 2 + Y ** 2 <= w.r_inner_mm ** 2
+
+
 def gpu(x, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV, dtype)
 
@@ -55,7 +61,7 @@ LENS_SMALL = REFRACT_SMALL.scaled(lens=I.telecentric_relay(), pupil_pattern="hex
 
 
 def _oracle_table(w, pupil):
-    M = pupil.shape[0]
+    M = w.rays_per_pixel
     n = w.nu * w.nv * M
     A = np.zeros((n, 4))
     B = np.zeros((n, 4))
@@ -79,8 +85,14 @@ def _oracle_table(w, pupil):
 
 
 @pytest.mark.parametrize("w", [REFRACT_SMALL, REFRACT_SMALL.scaled(pupil_mm=math.inf, f_number=5.0),
-                               I.TINY, LENS_SMALL], ids=["nontelecentric", "telecentric", "tiny", "lens_train"])
+                               I.TINY, LENS_SMALL, MID_CROP.scaled(n_angles=2),
+                               REFRACT_SMALL.scaled(jitter_per_pixel=True, rays_per_pixel=7)],
+                         ids=["nontelecentric", "telecentric", "tiny", "lens_train", "stratified_per_pixel",
+                              "sunflower_per_pixel"])
 def test_ray_table_matches_oracle_trace(vamrt, w):
+    """The library's ray table (its own stop sampling, tracing and segment) against the
+    oracle's trace of every ray: named patterns with shared and per-pixel jitter, the
+    hexagonal filling through the lens train, telecentric and chief-ray printers."""
     pupil = I.workload_pupil(w)
     P = vamrt.Projector.from_workload(w, pupil)
     a4, b4, j2 = P.ray_table()
@@ -199,10 +211,13 @@ def test_optimizer_matches_oracle_per_iteration(vamrt):
     P = vamrt.Projector.from_workload(w, pupil)
     f = I.make_target(w)
     res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0)
-    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
-                                          n_iter=w.osmo_iters, tol=0.0)
+    g_ref, dn_ref, m_ref, e_ref, v_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil),
+                                                 lambda g: O.forward(w, g, pupil), n_iter=w.osmo_iters, tol=0.0,
+                                                 resin=resin_mask(w))
     assert res["iterations"] == w.osmo_iters and not res["converged"]
     np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
+    # V decides on thresholded FP32 doses: a few voxels at a bin edge may flip
+    np.testing.assert_allclose(res["vers"], v_ref, rtol=0, atol=1e-4)
     assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
     assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL
     assert rel_l2(res["model"].cpu().numpy(), m_ref) <= FP32_TOL
@@ -215,8 +230,8 @@ def test_relaxed_optimizer_matches_oracle_per_iteration(vamrt):
     P = vamrt.Projector.from_workload(w, pupil)
     f = I.make_target(w)
     res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, step=4.0)
-    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
-                                          n_iter=w.osmo_iters, tol=0.0, beta=4.0)
+    g_ref, dn_ref, m_ref, e_ref, _ = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                             n_iter=w.osmo_iters, tol=0.0, beta=4.0, resin=resin_mask(w))
     np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
     assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
     assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL
@@ -235,8 +250,8 @@ def test_momentum_optimizer_matches_oracle_per_iteration(vamrt):
     pupil = I.workload_pupil(w)
     P = vamrt.Projector.from_workload(w, pupil)
     f = I.make_target(w)
-    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
-                                          n_iter=w.osmo_iters, tol=0.0, beta=4.0, mu=0.5)
+    g_ref, dn_ref, m_ref, e_ref, _ = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                             n_iter=w.osmo_iters, tol=0.0, beta=4.0, mu=0.5, resin=resin_mask(w))
     res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, step=4.0, momentum=0.5)
     np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
     assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
@@ -252,27 +267,32 @@ def test_momentum_optimizer_matches_oracle_per_iteration(vamrt):
         P.optimize(gpu(f), max_iter=1, momentum=1.0)
 
 
-def test_optimizer_stops_at_tolerance(vamrt):
+def test_optimizer_stops_at_the_papers_tolerance(vamrt):
+    """Sec. 2.7 stops once the absolute relative error is below 0.5 %, read as the voxel
+    error rate V of the normalised dose.  On the 64^3 workload the plain loop gets there
+    (V = 0.49 % at iteration 12 in the FP64 oracle): the GPU stops at the same iteration
+    as the oracle, with V below 0.5 % only at that last iteration; reading V only every
+    4 iterations stops at the first checked iteration past it."""
     w = I.TINY
     pupil = I.workload_pupil(w)
     P = vamrt.Projector.from_workload(w, pupil)
-    f = gpu(I.make_target(w))
-    full = P.optimize(f, max_iter=6, tol=0.0)
-    E = full["errors"]
-    assert len(E) == 6 and not full["converged"]
-    i_best = int(np.argmin(E[1:])) + 1
-    tol = float(E[i_best]) * 1.0000001
-    first = int(np.nonzero(E < tol)[0][0])        # first iteration below tol
-    res = P.optimize(f, max_iter=6, tol=tol)
-    assert res["converged"] and res["iterations"] == first + 1
-    # the dose sums are not bitwise reproducible (atomic order); E agrees to ~1e-10
-    np.testing.assert_allclose(res["errors"], E[:first + 1], rtol=1e-7)
-    # checking every 4 iterations reads E only after iterations 4 and 6
-    res2 = P.optimize(f, max_iter=6, tol=tol, check_every=4)
-    checks = [4, 6]
-    stop = next((c for c in checks if E[c - 1] < tol), None)
-    assert res2["converged"] == (stop is not None)
-    assert res2["iterations"] == (stop if stop else 6)
+    f_np = I.make_target(w)
+    f = gpu(f_np)
+    _, _, _, e_ref, v_ref = OS.osmo(f_np, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
+                                    n_iter=20, tol=0.005, resin=resin_mask(w))
+    assert v_ref[-1] < 0.005 and np.all(v_ref[:-1] >= 0.005) and len(v_ref) < 20
+    res = P.optimize(f, max_iter=20, tol=0.005)
+    assert res["converged"] and res["iterations"] == len(v_ref)
+    np.testing.assert_allclose(res["vers"], v_ref, rtol=0, atol=1e-4)
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
+    assert res["final_ver"] < 0.005 and res["final_error"] > 0.5     # E stays far above 0.5 %
+    n = len(v_ref)
+    res4 = P.optimize(f, max_iter=20, tol=0.005, check_every=4)
+    assert res4["converged"] and res4["iterations"] == 4 * ((n + 3) // 4)
+    assert np.all(np.isnan(res4["vers"][[i for i in range(res4["iterations"]) if (i + 1) % 4]]))
+    # the E criterion never fires on this binary target
+    resE = P.optimize(f, max_iter=6, tol=0.005, stop="error")
+    assert not resE["converged"] and resE["iterations"] == 6
 
 
 # ---- full-size workload (256^3, 360 angles, 256^2 pixels, 16 rays/pixel) -------------
@@ -327,8 +347,9 @@ def test_optimizer_bf16_storage_within_bound(vamrt):
     P = vamrt.Projector.from_workload(w, pupil)
     f = I.make_target(w)
     res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, proj_dtype=torch.bfloat16, dose_dtype=torch.bfloat16)
-    g_ref, dn_ref, m_ref, e_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil), lambda g: O.forward(w, g, pupil),
-                                          n_iter=w.osmo_iters, tol=0.0)
+    g_ref, dn_ref, m_ref, e_ref, v_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil),
+                                                 lambda g: O.forward(w, g, pupil), n_iter=w.osmo_iters, tol=0.0,
+                                                 resin=resin_mask(w))
     np.testing.assert_allclose(res["errors"], e_ref, rtol=BF16_DOSE_TOL)
     assert rel_l2(res["proj"].float().cpu().numpy(), g_ref) <= BF16_DOSE_TOL
     assert rel_l2(res["dose"].float().cpu().numpy(), dn_ref) <= BF16_DOSE_TOL
@@ -364,7 +385,8 @@ def test_projection_space_optimiser_matches_oracle(vamrt):
     g0 = np.maximum(0.0, O.adjoint(w, f, pupil))
     res = P.optimize(gpu(f), proj=gpu(g0), max_iter=5, tol=0.0, mode="projections", step=0.5)
     g_ref, dn_ref, e_ref = OS.osmo_projections(f, g0, lambda m: O.adjoint(w, m, pupil),
-                                               lambda g: O.forward(w, g, pupil), n_iter=5, alpha=0.5)
+                                               lambda g: O.forward(w, g, pupil), n_iter=5, alpha=0.5,
+                                               resin=resin_mask(w))
     np.testing.assert_allclose(res["errors"], e_ref, rtol=FP32_TOL)
     assert rel_l2(res["proj"].cpu().numpy(), g_ref) <= FP32_TOL
     assert rel_l2(res["dose"].cpu().numpy(), dn_ref) <= FP32_TOL

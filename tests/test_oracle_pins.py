@@ -118,7 +118,7 @@ def test_sample_count_closed_form_with_z_clip():
 # --- a1: ray generator ------------------------------------------------------------------
 def test_ray_generator_definition_non_telecentric():
     w = refracting_w()
-    P = pupil_samples("sunflower", 5, seed=3)
+    P = pupil_samples("disk", 5, seed=3)
     D = w.pupil_mm / w.f_number
     for (u, v, a) in [(0, 0, 0), (10, 3, 2), (20, 6, 4), (7, 1, 1)]:
         r = O.trace(w, P, u, v, a)
@@ -126,6 +126,124 @@ def test_ray_generator_definition_non_telecentric():
         Q = np.array([pixel_x(w)[u], 0.0, pixel_z(w)[v]])
         np.testing.assert_allclose(r["origin"], C, atol=1e-14)
         np.testing.assert_allclose(r["d0"], (Q - C) / np.linalg.norm(Q - C), atol=1e-15)
+
+
+# --- a1: aperture-stop sampling (Sec. 2.1; patterns of the workloads) --------------------
+def test_splitmix64_reference_output():
+    """splitmix64 from state 0 gives 0xE220A8397B1DCDAF, the first output of the published
+    generator seeded with 0; the jitter number is its top 53 bits scaled by 2^-53."""
+    assert O.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert O.jitter(0, 0, 0, 0, 0) == (0xE220A8397B1DCDAF >> 11) / 2.0 ** 53
+
+
+def test_jitter_numbers_are_uniform_and_keyed_by_every_index():
+    """Chi-square of 20000 jitter numbers over 20 bins stays in the bulk of its distribution
+    (19 degrees of freedom), and changing any one of u, v, a, c or the seed changes it."""
+    vals = np.array([O.jitter(7, u, v, a, c) for u in range(25) for v in range(20) for a in range(20) for c in (0, 1)])
+    assert vals.min() >= 0.0 and vals.max() < 1.0
+    counts = np.histogram(vals, bins=20, range=(0.0, 1.0))[0]
+    exp = vals.size / 20
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    assert chi2 < 43.8                      # 99.9th percentile of chi-square(19)
+    base = O.jitter(7, 3, 4, 5, 0)
+    for args in ((8, 3, 4, 5, 0), (7, 4, 4, 5, 0), (7, 3, 5, 5, 0), (7, 3, 4, 6, 0), (7, 3, 4, 5, 1)):
+        assert O.jitter(*args) != base
+
+
+def _uncentric(x, y):
+    """Inverse of the concentric square-to-disk map: the point of [-1,1]^2 that maps to
+    (x, y) (written from the map's definition: a square ring of half-width r goes to the
+    circle of radius r, its four sides to the four quarter-circles centred on the axes)."""
+    r = math.hypot(x, y)
+    phi = math.atan2(y, x)
+    if phi < -math.pi / 4:
+        phi += 2 * math.pi
+    if phi <= math.pi / 4:                   # right side: p = r, phi = (pi/4) q / p
+        return r, 4 * phi * r / math.pi
+    if phi <= 3 * math.pi / 4:               # top: q = r, phi = pi/2 - (pi/4) p / q
+        return (math.pi / 2 - phi) * 4 * r / math.pi, r
+    if phi <= 5 * math.pi / 4:               # left: p = -r, phi - pi = (pi/4) q / p
+        return -r, -4 * (phi - math.pi) * r / math.pi
+    return (phi - 3 * math.pi / 2) * 4 * r / math.pi, -r    # bottom: q = -r
+
+
+def test_stratified_pattern_one_point_per_stratum():
+    """n x n stratified jitter: ray a = i n + k of every pixel lies in the unit disk and maps
+    back (inverse concentric map) into stratum (i, k) of [-1,1]^2; per-pixel jitter gives
+    different points to different pixels, shared jitter the same ones."""
+    w = small_w(pupil_mm=60.0, f_number=3.0, pupil_pattern="stratified4x4", rays_per_pixel=16)
+    ap = I.workload_pupil(w)
+    assert ap.per_pixel
+    n = 4
+    for (u, v) in [(0, 0), (5, 2), (20, 6)]:
+        pts = O.aperture_points(w, ap, u, v)
+        assert np.all(np.hypot(pts[:, 0], pts[:, 1]) <= 1.0)
+        for a, (x, y) in enumerate(pts):
+            p, q = _uncentric(x, y)
+            assert (int((p + 1) * n / 2), int((q + 1) * n / 2)) == (a // n, a % n)
+    assert not np.array_equal(O.aperture_points(w, ap, 0, 0), O.aperture_points(w, ap, 1, 0))
+    shared = I.Aperture("stratified", 16, seed=0, per_pixel=False)
+    np.testing.assert_array_equal(O.aperture_points(w, shared, 0, 0), O.aperture_points(w, shared, 9, 3))
+
+
+def test_stratified_pattern_is_uniform_over_the_disk():
+    """The concentric map preserves area fractions, so jittered strata fill the disk
+    uniformly: over 400 pixels x 16 rays the fraction inside r = 1/2 is 1/4 and inside the
+    quarter x > 0, y > 0 is 1/4 (within a few binomial standard deviations)."""
+    w = small_w(nu=20, nv=20, pupil_mm=60.0, f_number=3.0, pupil_pattern="stratified4x4", rays_per_pixel=16)
+    ap = I.workload_pupil(w)
+    pts = np.concatenate([O.aperture_points(w, ap, u, v) for u in range(20) for v in range(20)])
+    inner = np.mean(np.hypot(pts[:, 0], pts[:, 1]) < 0.5)
+    quad = np.mean((pts[:, 0] > 0) & (pts[:, 1] > 0))
+    sd = math.sqrt(0.25 * 0.75 / len(pts))
+    assert abs(inner - 0.25) < 4 * sd and abs(quad - 0.25) < 4 * sd
+
+
+def test_sunflower_pattern_radii_and_golden_angle():
+    """Sunflower: r_a = sqrt((a + 1/2) / M) and consecutive azimuths a golden angle
+    pi (3 - sqrt 5) apart; the turn of the whole pattern is shared by every pixel unless
+    drawn per pixel."""
+    w = refracting_w(rays_per_pixel=8)
+    ap = I.workload_pupil(w)
+    assert not ap.per_pixel
+    pts = O.aperture_points(w, ap, 3, 2)
+    M = 8
+    np.testing.assert_allclose(np.hypot(pts[:, 0], pts[:, 1]), np.sqrt((np.arange(M) + 0.5) / M), rtol=1e-14)
+    ang = np.unwrap(np.arctan2(pts[:, 1], pts[:, 0]))
+    dphi = np.mod(np.diff(ang), 2 * np.pi)
+    np.testing.assert_allclose(dphi, np.pi * (3 - np.sqrt(5.0)), rtol=1e-12)
+    np.testing.assert_array_equal(pts, O.aperture_points(w, ap, 0, 0))
+    per = I.Aperture("sunflower", M, seed=0, per_pixel=True)
+    a0, a1 = O.aperture_points(w, per, 0, 0), O.aperture_points(w, per, 1, 0)
+    assert not np.allclose(a0, a1)
+    np.testing.assert_allclose(np.hypot(a1[:, 0], a1[:, 1]), np.hypot(a0[:, 0], a0[:, 1]), rtol=1e-14)
+
+
+def test_hexagonal_filling_is_a_hex_lattice_in_the_disk():
+    """Sec. 2.1 / Sec. 3.2: 13 rays, the points of a hexagonal lattice of spacing 1/2 inside
+    the unit disk: radii 0, 1/2 (six) and sqrt(3)/2 (six), every point's nearest neighbour
+    exactly 1/2 away, inner ring at multiples of 60 degrees, outer ring 30 degrees off."""
+    w = refracting_w(pupil_pattern="hex13", rays_per_pixel=13)
+    pts = O.aperture_points(w, I.workload_pupil(w), 4, 1)
+    r = np.hypot(pts[:, 0], pts[:, 1])
+    np.testing.assert_allclose(np.sort(r), [0.0] + [0.5] * 6 + [math.sqrt(3) / 2] * 6, atol=1e-15)
+    dist = np.hypot(pts[:, None, 0] - pts[None, :, 0], pts[:, None, 1] - pts[None, :, 1])
+    np.fill_diagonal(dist, np.inf)
+    np.testing.assert_allclose(dist.min(axis=1), 0.5, rtol=1e-13)
+    deg = np.degrees(np.arctan2(pts[1:, 1], pts[1:, 0])) % 360
+    np.testing.assert_allclose(np.sort(deg[r[1:] < 0.6]), [0, 60, 120, 180, 240, 300], atol=1e-12)
+    np.testing.assert_allclose(np.sort(deg[r[1:] > 0.6]), [30, 90, 150, 210, 270, 330], atol=1e-12)
+
+
+def test_named_pattern_drives_the_traced_rays():
+    """The traced ray of (u, v, a) leaves the stop point the pattern gives for that pixel."""
+    w = small_w(pupil_mm=60.0, f_number=3.0, pupil_pattern="stratified4x4", rays_per_pixel=16)
+    ap = I.workload_pupil(w)
+    D = w.pupil_mm / w.f_number
+    for (u, v, a) in [(0, 0, 0), (10, 3, 7), (20, 6, 15)]:
+        xi, eta = O.aperture_points(w, ap, u, v)[a]
+        r = O.trace(w, ap, u, v, a)
+        np.testing.assert_allclose(r["origin"], [xi * D / 2, -w.pupil_mm, eta * D / 2], atol=1e-14)
 
 
 def test_ray_generator_telecentric_cone_matches_paper_divergence():
@@ -162,7 +280,7 @@ def test_snell_invariants_across_coaxial_cylinders():
     # a thick wall (R_in = 3, R_o = 6): rays with n_glass R_in < b < R_o only cross the glass
     w = refracting_w(nu=15, pixel_u_mm=0.9, nv=5, pixel_v_mm=1.3, n_glass=1.52, n_resin=1.43,
                      r_inner_mm=3.0, wall_mm=3.0)
-    P = pupil_samples("sunflower", 5, seed=9)
+    P = pupil_samples("disk", 5, seed=9)
     Ro, Ri = w.r_inner_mm + w.wall_mm, w.r_inner_mm
     n0, n1, n2 = w.n_outside, w.n_glass, w.n_resin
     seen = {-1: 0, 0: 0, 1: 0, 2: 0}
@@ -219,7 +337,7 @@ def _fresnel_angles(ti, tt):
 
 def test_fresnel_matches_angle_form_and_scalar_snell():
     w = refracting_w(nu=15, pixel_u_mm=0.8, n_glass=1.52, n_resin=1.43)
-    P = pupil_samples("sunflower", 5, seed=9)
+    P = pupil_samples("disk", 5, seed=9)
     Ro, Ri = w.r_inner_mm + w.wall_mm, w.r_inner_mm
     checked = 0
     for r in _rays(w, P):
@@ -258,7 +376,7 @@ def test_adjoint_identity_refracting_finite_etendue():
     """<A g, V> = <g, P V>: the dose operator is the exact transpose of the projection."""
     w = refracting_w(nx=17, ny=16, nz=9, nu=11, nv=5, pixel_u_mm=0.9, pixel_v_mm=0.7, n_angles=5,
                      r_inner_mm=3.0, wall_mm=0.8)
-    P = pupil_samples("sunflower", 5, seed=4)
+    P = pupil_samples("disk", 5, seed=4)
     rng = np.random.default_rng(0)
     V = rng.random(w.vol_shape)
     g = rng.random(w.proj_shape)
@@ -270,7 +388,7 @@ def test_adjoint_identity_refracting_finite_etendue():
 def test_dose_matrix_is_transpose_of_projection_matrix():
     w = refracting_w(nx=8, ny=8, nz=4, nu=5, nv=3, pixel_u_mm=0.5, pixel_v_mm=0.5, n_angles=3,
                      r_inner_mm=1.2, wall_mm=0.3, rays_per_pixel=2, pupil_pattern="sunflower", voxel_mm=0.5)
-    P = pupil_samples("sunflower", 2, seed=1)
+    P = pupil_samples("disk", 2, seed=1)
     nvox, npix = int(np.prod(w.vol_shape)), int(np.prod(w.proj_shape))
     At = np.zeros((npix, nvox))
     for i in range(nvox):
@@ -313,7 +431,7 @@ def test_brute_force_fine_step_convergence():
     w0 = refracting_w(nx=12, ny=12, nz=10, nu=8, nv=6, pixel_u_mm=0.45, pixel_v_mm=0.45, n_angles=4,
                       r_inner_mm=2.2, wall_mm=0.5, pupil_mm=30.0, f_number=3.0, rays_per_pixel=3,
                       mu_per_mm=0.3)
-    P = pupil_samples("sunflower", 3, seed=2)
+    P = pupil_samples("disk", 3, seed=2)
     V = np.random.default_rng(5).random(w0.vol_shape)
     th = default_angles(w0.n_angles)
     pix = [(0, 3, 3), (1, 2, 4), (2, 4, 1), (3, 1, 6), (1, 5, 3)]
@@ -355,14 +473,90 @@ def test_paper_printed_optics_numbers():
 def test_osmo_fixed_point_and_nonnegativity():
     f = np.array([1.0, 0.0, 1.0, 1.0, 0.0])
     ident = lambda x: x.copy()
-    g, dn, m, err = OS.osmo(f, ident, ident, n_iter=5)
+    g, dn, m, err, ver = OS.osmo(f, ident, ident, n_iter=5)
     assert len(err) == 1 and err[0] == 0.0
     np.testing.assert_array_equal(m, f)
     rng = np.random.default_rng(0)
     M = rng.random((4, 5))
-    g, dn, m, err = OS.osmo(f, lambda x: M @ x - 0.8, lambda y: M.T @ y, n_iter=6)
+    g, dn, m, err, ver = OS.osmo(f, lambda x: M @ x - 0.8, lambda y: M.T @ y, n_iter=6)
     assert np.all(m >= 0) and np.all(g >= 0) and dn.max() == 1.0
     assert np.all(np.isfinite(err))
+
+
+# A two-voxel, two-pixel toy printer: dose = B g, projection = B^T m.  Its iterates are
+# worked out by hand below (exact fractions), so a dropped term, a wrong sign or a
+# transposed operator in either iteration changes them.
+B_TOY = np.array([[2.0, 1.0], [1.0, 1.0]])
+
+
+def test_osmo_two_iterations_by_hand():
+    """Object-space iteration on the toy printer, f = (1, 1/2), m0 = f:
+    g0 = B^T m0 = (5/2, 3/2); d0 = B g0 = (13/2, 4); dn0 = (1, 8/13); E0 = (3/26)/(3/2) = 1/13;
+    m1 = m0 + f - dn0 = (1, 5/13).  g1 = (31/13, 18/13); d1 = (80/13, 49/13); dn1 = (1, 49/80);
+    E1 = (9/80)/(3/2) = 3/40; m2 = (1, 5/13 + 1/2 - 49/80) = (1, 283/1040)."""
+    f = np.array([1.0, 0.5])
+    g, dn, m, err, _ = OS.osmo(f, lambda x: B_TOY.T @ x, lambda y: B_TOY @ y, n_iter=1, tol=0.0)
+    np.testing.assert_allclose(g, [2.5, 1.5], rtol=1e-15)
+    np.testing.assert_allclose(dn, [1.0, 8.0 / 13.0], rtol=1e-15)
+    np.testing.assert_allclose(err, [1.0 / 13.0], rtol=1e-14)
+    np.testing.assert_allclose(m, [1.0, 5.0 / 13.0], rtol=1e-15)
+    g, dn, m, err, _ = OS.osmo(f, lambda x: B_TOY.T @ x, lambda y: B_TOY @ y, n_iter=2, tol=0.0)
+    np.testing.assert_allclose(g, [31.0 / 13.0, 18.0 / 13.0], rtol=1e-15)
+    np.testing.assert_allclose(dn, [1.0, 49.0 / 80.0], rtol=1e-15)
+    np.testing.assert_allclose(err, [1.0 / 13.0, 3.0 / 40.0], rtol=1e-14)
+    np.testing.assert_allclose(m, [1.0, 283.0 / 1040.0], rtol=1e-14)
+
+
+def test_osmo_model_clamp_by_hand():
+    """f = (1, 0): g0 = (2, 1), d0 = (5, 3), dn0 = (1, 3/5), E0 = 3/5; the update would take
+    the void voxel's model to -3/5 and the clamp holds it at 0, so m1 = f."""
+    f = np.array([1.0, 0.0])
+    g, dn, m, err, _ = OS.osmo(f, lambda x: B_TOY.T @ x, lambda y: B_TOY @ y, n_iter=1, tol=0.0)
+    np.testing.assert_allclose(dn, [1.0, 0.6], rtol=1e-15)
+    np.testing.assert_allclose(err, [0.6], rtol=1e-15)
+    np.testing.assert_array_equal(m, [1.0, 0.0])
+
+
+def test_osmo_normalises_by_the_resin_maximum():
+    """The dose is normalised by its maximum over the resin voxels only: with voxel 0
+    outside the resin, dn0 = d0 / d0[1] = (13/8, 1) for the toy's f = (1, 1/2)."""
+    f = np.array([1.0, 0.5])
+    _, dn, _, _, _ = OS.osmo(f, lambda x: B_TOY.T @ x, lambda y: B_TOY @ y, n_iter=1, tol=0.0,
+                             resin=np.array([False, True]))
+    np.testing.assert_allclose(dn, [13.0 / 8.0, 1.0], rtol=1e-15)
+
+
+def test_osmo_projections_closed_form():
+    """Projection-space iteration on the toy printer B = [[2, 1], [0, 1]] (the second voxel
+    is reached by the second pixel only), f = (1, 0), g0 = (1, 1), alpha = 1:
+    g_k = (1, c_k) with c_{k+1} = c_k - c_k / (2 + c_k) and E_k = c_k / (2 + c_k):
+    c = 1, 2/3, 5/12; E = 1/3, 1/4.  The fixed point g = (1, 0) prints f exactly (E = 0).
+    With alpha = 1/2 the displacement of the first step halves: c1 = 1 - 1/6."""
+    f = np.array([1.0, 0.0])
+    B = np.array([[2.0, 1.0], [0.0, 1.0]])
+    project, dose = (lambda x: B.T @ x), (lambda y: B @ y)
+    g, dn, err = OS.osmo_projections(f, np.array([1.0, 1.0]), project, dose, n_iter=2, alpha=1.0)
+    np.testing.assert_allclose(err, [1.0 / 3.0, 1.0 / 4.0], rtol=1e-15)
+    np.testing.assert_allclose(g, [1.0, 5.0 / 12.0], rtol=1e-15)
+    g, _, _ = OS.osmo_projections(f, np.array([1.0, 1.0]), project, dose, n_iter=1, alpha=0.5)
+    np.testing.assert_allclose(g, [1.0, 5.0 / 6.0], rtol=1e-15)
+    g, dn, err = OS.osmo_projections(f, np.array([1.0, 0.0]), project, dose, n_iter=3)
+    np.testing.assert_array_equal(g, [1.0, 0.0])
+    np.testing.assert_array_equal(err, [0.0, 0.0, 0.0])
+
+
+def test_osmo_stops_on_the_voxel_error_rate():
+    """The stop reads Sec. 2.7's 'absolute relative error below 0.5 %' as the voxel error
+    rate V of the normalised dose: the loop ends after the first iteration whose V is below
+    tol, and the dose error E is reported beside it.  On the toy printer with f = (1, 0),
+    V0 = 0 (the threshold between 3/5 and 1 separates the voxels) while E0 = 3/5, so a
+    0.5 % stop on V ends after one iteration and a 0.5 % stop on E does not."""
+    f = np.array([1.0, 0.0])
+    project, dose = (lambda x: B_TOY.T @ x), (lambda y: B_TOY @ y)
+    _, _, _, err, ver = OS.osmo(f, project, dose, n_iter=4, tol=0.005)
+    assert len(err) == 1 and ver[0] == 0.0 and abs(err[0] - 0.6) < 1e-15
+    _, _, _, err, ver = OS.osmo(f, project, dose, n_iter=4, tol=0.005, stop="error")
+    assert len(err) == 4 and np.all(err > 0.005)
 
 
 def test_osmo_relaxed_step_scales_the_model_update():
@@ -373,14 +567,14 @@ def test_osmo_relaxed_step_scales_the_model_update():
     tilt = np.array([1.0, 1.05, 0.9, 1.1])
     project = lambda x: tilt * x
     dose = lambda y: y.copy()
-    _, _, m1, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0)
-    _, _, m3, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=3.0)
+    _, _, m1, _, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0)
+    _, _, m3, _, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=3.0)
     assert np.all(m1 > 0) and np.all(m3 > 0)
     np.testing.assert_allclose(m3 - f, 3.0 * (m1 - f), rtol=0, atol=1e-15)
     assert np.abs(m1 - f).max() > 0.05
     ident = lambda x: x.copy()
     fb = np.array([1.0, 0.0, 1.0])
-    _, _, m, err = OS.osmo(fb, ident, ident, n_iter=3, tol=0.0, beta=4.0)
+    _, _, m, err, _ = OS.osmo(fb, ident, ident, n_iter=3, tol=0.0, beta=4.0)
     np.testing.assert_array_equal(m, fb)
     assert np.all(np.array(err) == 0.0)
 
@@ -393,15 +587,15 @@ def test_osmo_momentum_adds_the_previous_step():
     tilt = np.array([1.0, 1.05, 0.9, 1.1])
     project = lambda x: tilt * x
     dose = lambda y: y.copy()
-    _, _, m1, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0)
-    _, _, m1_mu, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, mu=0.5)
+    _, _, m1, _, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0)
+    _, _, m1_mu, _, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, mu=0.5)
     np.testing.assert_array_equal(m1_mu, m1)
-    _, _, m2, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, m0=m1)
-    _, _, m2_mu, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, mu=0.5, m0=m1, m_prev=f)
+    _, _, m2, _, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, m0=m1)
+    _, _, m2_mu, _, _ = OS.osmo(f, project, dose, n_iter=1, tol=0.0, beta=2.0, mu=0.5, m0=m1, m_prev=f)
     assert np.all(m2 > 0) and np.all(m2_mu > 0)
     np.testing.assert_allclose(m2_mu - m2, 0.5 * (m1 - f), rtol=0, atol=1e-15)
     assert np.abs(m1 - f).max() > 0.05
-    _, _, m2_two, _ = OS.osmo(f, project, dose, n_iter=2, tol=0.0, beta=2.0, mu=0.5)
+    _, _, m2_two, _, _ = OS.osmo(f, project, dose, n_iter=2, tol=0.0, beta=2.0, mu=0.5)
     np.testing.assert_allclose(m2_two, m2_mu, rtol=0, atol=1e-15)
 
 
@@ -592,3 +786,45 @@ def test_export_u8_codes():
     np.testing.assert_array_equal(codes[1:4], np.rint(255 * g[1:4] / c).astype(np.uint8))
     codes2, _ = OS.export_u8(np.array([0.5, 1.5, 1.0, 1.0]))   # c = 1 + 3 * sqrt(1/8)
     assert codes2.dtype == np.uint8 and codes2.max() <= 255
+
+
+# --- warm-start network reference (oracle/unet_ref.py) -------------------------------------
+def _ref_arch():
+    return [("enc0a", 16, 16, 27), ("enc0b", 16, 16, 27), ("enc1a", 16, 32, 27), ("enc1b", 32, 32, 27),
+            ("enc2a", 32, 64, 27), ("enc2b", 64, 64, 27), ("bota", 64, 128, 27), ("botb", 128, 128, 27),
+            ("dec2a", 192, 64, 27), ("dec2b", 64, 64, 27), ("dec1a", 96, 32, 27), ("dec1b", 32, 32, 27),
+            ("dec0a", 48, 16, 27), ("dec0b", 16, 16, 27), ("head", 16, 16, 1)]
+
+
+def test_unet_reference_head_and_loss_in_closed_form():
+    """With every convolution weight zero the network is constant: the last decoder layer
+    outputs relu(b_dec0b), the head z = W_head relu(b_dec0b) + b_head (channel 0 used), and
+    out = in_scale base + z.  Loss, dL/db_head[0] and dL/dW_head[0, c] then have closed forms
+    (mean squared error over the first n_angles slices): a wrong head channel, a missing
+    input scale, a dropped 1/2 or mean, or a gradient through the wrong channel fails."""
+    from oracle import unet_ref
+    rng = np.random.default_rng(5)
+    arch = _ref_arch()
+    weights = {n: (np.zeros((co, t, ci)), np.zeros(co)) for (n, ci, co, t) in arch}
+    b_dec = rng.uniform(-1.0, 1.0, 16)
+    weights["dec0b"] = (np.zeros((16, 27, 16)), b_dec)
+    Wh = rng.standard_normal((16, 1, 16))
+    bh = rng.standard_normal(16)
+    weights["head"] = (Wh, bh)
+    Dp, V, U, A = 8, 8, 8, 6
+    x = rng.random((Dp, V, U, 16))
+    base = rng.random((A, V, U))
+    target = rng.random((A, V, U))
+    s = 0.7
+    loss, z, grads = unet_ref.loss_and_grads(arch, weights, x, target, A, base, s)
+    h = np.maximum(b_dec, 0.0)
+    z0 = Wh[0, 0] @ h + bh[0]
+    out = s * base + z0
+    r = out - target
+    assert abs(loss - 0.5 * np.mean(r ** 2)) <= 1e-12 * abs(loss)
+    np.testing.assert_allclose(z[..., 0], z0, rtol=1e-12)
+    gW, gb = grads["head"]
+    np.testing.assert_allclose(gb[0], np.mean(r), rtol=1e-10)
+    np.testing.assert_allclose(gb[1:], 0.0, atol=1e-15)
+    np.testing.assert_allclose(gW[0, 0], np.mean(r) * h, rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(gW[1:], 0.0, atol=1e-15)

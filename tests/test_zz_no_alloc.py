@@ -70,6 +70,24 @@ def test_static_dose_matches_forward_dose_twice(V, name):
         assert rel_l2(out, ref) <= FP32_TOL
 
 
+def test_static_dose_leaves_device_memory_unchanged(V):
+    """The entry point's reason to exist: two calls in a row change neither the device's
+    free memory (cudaMemGetInfo) nor what torch's allocator holds."""
+    w = WORKLOADS["refracting_ragged"]
+    P = V.Projector.from_workload(w, I.workload_pupil(w))
+    g = torch.from_numpy(I.random_projections(w, seed=13)).to(DEV)
+    ref = P.forward_dose(g)
+    out = torch.empty(w.vol_shape, device=DEV)
+    torch.cuda.synchronize()
+    free0, held0 = torch.cuda.mem_get_info(DEV)[0], torch.cuda.memory_allocated(DEV)
+    for _ in range(2):
+        assert static_dose(V, P, g, out) == V.VAMRT_OK, V.lib().vamrt_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(DEV)[0] == free0
+    assert torch.cuda.memory_allocated(DEV) == held0
+    assert rel_l2(out, ref) <= FP32_TOL
+
+
 def test_static_dose_accumulate_and_bf16(V):
     w = WORKLOADS["refracting_ragged"]
     P = V.Projector.from_workload(w, I.workload_pupil(w))
