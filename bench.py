@@ -389,6 +389,10 @@ def run_gpu(args, rank, world):
     w = I.WORKLOADS[args.workload]
     if args.angles:
         w = w.scaled(n_angles=args.angles)
+    if args.nz:
+        w = w.scaled(nz=args.nz)
+    if args.nv:
+        w = w.scaled(nv=args.nv)
     pupil = I.workload_pupil(w)
     target_np = I.make_target(w)
     t0 = time.perf_counter()
@@ -478,7 +482,7 @@ def run_gpu(args, rank, world):
     vol_b, proj_b = 4 * math.prod(w.vol_shape), 4 * math.prod(w.proj_shape)
     # compulsory DRAM bytes of one launch: volume in + projections out (adjoint) or
     # projections in + dose accumulator out (forward), plus the ray table once per angle
-    compulsory = vol_b + proj_b + 40 * n_rays * w.n_angles
+    compulsory = vol_b + proj_b + 72 * n_rays * w.n_angles
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tf):
@@ -563,6 +567,8 @@ def main():
     ap.add_argument("--impl", default="vamrt", choices=["vamrt", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--angles", type=int, default=0, help="override the angle count (small profiling cases)")
+    ap.add_argument("--nz", type=int, default=0, help="override the grid's plane count (small profiling cases)")
+    ap.add_argument("--nv", type=int, default=0, help="override the pixel row count (small profiling cases)")
     ap.add_argument("--cpu-rows", type=int, default=128)
     ap.add_argument("--ref-rows", type=int, default=32)
     ap.add_argument("--ttt-workload", default=TTT_WORKLOAD,
@@ -581,6 +587,9 @@ def main():
     ap.add_argument("--ws-eval", type=int, default=4, help="held-out targets for the warm-start comparison")
     ap.add_argument("--network-only", action="store_true",
                     help="time the warm-start network's convolutions alone and print their JSON")
+    ap.add_argument("--warmstart-only", action="store_true",
+                    help="run only the learned warm-start comparison (--ws-train pairs, --ws-eval held-out "
+                         "targets) and print its JSON")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -588,6 +597,10 @@ def main():
         run_reference(args, rank, world)
     elif args.network_only:
         run_network_only(args)
+    elif args.warmstart_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(warm_start_time_to_target(args)), flush=True)
     else:
         run_gpu(args, rank, world)
 

@@ -160,7 +160,7 @@ typedef struct {
  * ray generation, vector Snell's law and Fresnel transmission at both cylinder surfaces,
  * the in-resin segment).  The vial is rotationally symmetric about z, so the segment at
  * angle theta_k is the theta = 0 segment rotated; only the theta = 0 table is stored
- * (40 B per ray, FP32).  Synchronises `stream` (a cudaStream_t, NULL = legacy default)
+ * (72 B per ray, FP64 positions and directions).  Synchronises `stream` (a cudaStream_t, NULL = legacy default)
  * before returning.  *out receives a handle to release with vamrt_destroy_projector.
  * Errors: EINVAL (bad geometry), ENOMEM, ECUDA.
  */
@@ -452,8 +452,8 @@ vamrt_status vamrt_export_u8(vamrt_projector *p, const void *proj, vamrt_dtype p
                              float *dequant, double *clip, void *stream);
 
 /*
- * Copy the theta = 0 ray table to HOST arrays of n_rays entries each (ray index
- * r = (a nv + v) nu + u):  a4[r] = (e_x, e_y, e_z, delta) in voxel units (entry point
+ * Copy the theta = 0 ray table (kept in FP64 on the device), rounded to FP32, to HOST
+ * arrays of n_rays entries each (ray index r = (a nv + v) nu + u):  a4[r] = (e_x, e_y, e_z, delta) in voxel units (entry point
  * relative to the axis, sample spacing);  b4[r] = (d_x, d_y, d_z, T1 T2 delta_mm / M);
  * j2[r] = (j_lo, j_hi), the samples whose footprint reaches the grid (-1 < q_z < nz).
  * Any pointer may be NULL.  Synchronous.

@@ -23,13 +23,22 @@
 // global memory with the same arithmetic.
 //
 // Sample positions.  Per ray and angle the entry point and direction are rotated into the
-// vial frame in FP64 and converted to Q32.32 fixed point; sample j sits at
-// q0 + j * step exactly (integer adds), so positions carry no accumulated rounding and the
-// footprint of a run of samples is bounded by the cells of its two end samples.
+// vial frame in FP64 and converted to Q32.32 fixed point, sample j at q0 + j * step.
+// Inside a box a chunk is walked backwards from its last sample, whose Q32.32 position is
+// cut to a 32-bit Q9.23 offset from the box origin, by the step cut to Q9.23 (one 32-bit
+// add per axis and sample; the drift stays below 2^-23 voxel per sample and resets every
+// chunk).  Walking backwards lets the Beer-Lambert factor enter by Horner's rule (one
+// fused multiply-add per sample).  Positions are linear in j, so the cells a chunk visits
+// lie between the cells of its two end positions, which the box is built from.
+//
+// Grid order.  Blocks are launched pixel-column tile fastest, then angle, then pixel-row
+// tile, so the blocks resident together share a row tile: one slab of z planes of the
+// volume (and one band of the ray table), which stays in L2 while every angle passes
+// over it -- volumes far larger than L2 are then read from HBM about once per row tile.
 //
 // The caller's volume is copied into a scratch volume with one voxel of zero halo (zero
-// padding outside the grid, Sec. 2.2's weights then need no bounds tests); index clamps
-// remain only as a guard that never binds for valid geometry.
+// padding outside the grid, Sec. 2.2's weights then need no bounds tests).  Each ray's
+// sample range is trimmed once so that every sample's cell lies inside the padded grid.
 #include <cuda_bf16.h>
 #include <limits.h>
 
@@ -114,23 +123,32 @@ struct Ray {
     float att;                // log2 of the Beer-Lambert factor per sample
     float w;                  // T1 T2 delta_mm / M
     float ey, dy;             // theta = 0 frame: y(j) = ey + (j + 1/2) dy (voxels)
+    float inv_dy;             // 1 / dy
     int jlo, jhi;
 };
+
+// Q32.32 z of sample j lies in [0, pz - 1): its cell and the cell above are inside the
+// padded grid.
+__device__ __forceinline__ bool z_inside(const OpParams &P, const Ray &R, int j)
+{
+    const long long qz = R.q0z + (long long)j * R.sz;
+    return qz >= 0 && qz < ((long long)(P.pz - 1) << 32);
+}
 
 __device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 cs, Ray &R, bool unattenuated)
 {
     const int2 J = P.J[r];
     if (J.x >= J.y) return false;
-    const float4 A = P.A[r], B = P.B[r];
+    const double4 A = P.A[r], B = P.B[r];
     const double c = cs.x, s = cs.y;
     const double ex = A.x, ey = A.y, dl = A.w;
-    const double stx = (c * (double)B.x - s * (double)B.y) * dl;
-    const double sty = (s * (double)B.x + c * (double)B.y) * dl;
-    const double stz = (double)B.z * dl;
+    const double stx = (c * B.x - s * B.y) * dl;
+    const double sty = (s * B.x + c * B.y) * dl;
+    const double stz = B.z * dl;
     // sample 0 sits half a step inside the entry point
     const double q0x = P.cx + (c * ex - s * ey) + 0.5 * stx;
     const double q0y = P.cy + (s * ex + c * ey) + 0.5 * sty;
-    const double q0z = P.cz + (double)A.z + 0.5 * stz;
+    const double q0z = P.cz + A.z + 0.5 * stz;
     R.q0x = __double2ll_rn(q0x * kFix);
     R.q0y = __double2ll_rn(q0y * kFix);
     R.q0z = __double2ll_rn(q0z * kFix);
@@ -138,13 +156,21 @@ __device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 
     R.sy = __double2ll_rn(sty * kFix);
     R.sz = __double2ll_rn(stz * kFix);
     // the paper-literal projection (Sec. 2.4): no Beer-Lambert or Fresnel factor, weight delta / M
-    R.att = unattenuated ? 0.f : P.neg_mu_vox_log2e * A.w;
-    R.w = unattenuated ? A.w * P.h_over_m : B.w;
-    R.ey = A.y;
-    R.dy = A.w * B.y;
-    R.jlo = J.x;
-    R.jhi = J.y;
-    return true;
+    R.att = unattenuated ? 0.f : P.neg_mu_vox_log2e * (float)A.w;
+    R.w = unattenuated ? (float)A.w * P.h_over_m : (float)B.w;
+    R.ey = (float)A.y;
+    R.dy = (float)(A.w * B.y);
+    R.inv_dy = 1.0f / R.dy;
+    // The traced sample range [j_lo, j_hi) keeps -1 < q_z < nz in FP64; the FP32 table's
+    // rounding can put an end sample a hair outside.  Drop such end samples (their
+    // in-grid weight is ~1e-5 of a sample's) so that no sample needs a clamp later.
+    int jlo = J.x, jhi = J.y;
+    for (int t = 0; t < 4 && jlo < jhi && !z_inside(P, R, jlo); ++t) ++jlo;
+    for (int t = 0; t < 4 && jlo < jhi && !z_inside(P, R, jhi - 1); ++t) --jhi;
+    if (jlo < jhi && !(z_inside(P, R, jlo) && z_inside(P, R, jhi - 1))) jhi = jlo;   // never for valid tables
+    R.jlo = jlo;
+    R.jhi = jhi;
+    return jlo < jhi;
 }
 
 // rays that hardly advance along y are taken whole in their first chunk
@@ -156,24 +182,27 @@ __device__ __forceinline__ int chunk_of(const OpParams &P, const Ray &R, int j)
     return (int)floorf((y - P.y0) * (1.0f / kChunkVox));
 }
 
-// first sample whose y lies at or beyond the start of chunk c (monotone in c)
-__device__ __forceinline__ int chunk_start(const OpParams &P, const Ray &R, int c)
+// First sample whose y lies at or beyond the boundary at half-chunk h, i.e. at
+// y0 + h * kChunkVox / 2 (monotone in h).  Chunk c spans half-chunks 2c and 2c + 1; a
+// chunk whose box does not fit is walked as its two halves.
+__device__ __forceinline__ int half_start(const OpParams &P, const Ray &R, int h)
 {
-    const float yc = P.y0 + (float)(c * kChunkVox);
-    const float j = ceilf((yc - R.ey) / R.dy - 0.5f);
+    const float yc = P.y0 + (float)(h * (kChunkVox / 2));
+    const float j = ceilf((yc - R.ey) * R.inv_dy - 0.5f);
     return (int)fminf(fmaxf(j, (float)R.jlo), (float)R.jhi);
 }
 
-__device__ __forceinline__ void chunk_samples(const OpParams &P, const Ray &R, int c, int cmin, int cmax, int &jl,
-                                              int &jh)
+// Samples [jl, jh) of half-chunks [h0, h1) of a ray whose samples span chunks cmin..cmax.
+__device__ __forceinline__ void range_samples(const OpParams &P, const Ray &R, int h0, int h1, int cmin, int cmax,
+                                              int &jl, int &jh)
 {
     if (!(R.dy > kMinDy)) {
-        jl = (c == cmin) ? R.jlo : R.jhi;
+        jl = (h0 == 2 * cmin) ? R.jlo : R.jhi;
         jh = R.jhi;
         return;
     }
-    jl = (c == cmin) ? R.jlo : chunk_start(P, R, c);
-    jh = (c == cmax) ? R.jhi : chunk_start(P, R, c + 1);
+    jl = (h0 == 2 * cmin) ? R.jlo : half_start(P, R, h0);
+    jh = (h1 == 2 * cmax + 2) ? R.jhi : half_start(P, R, h1);
 }
 
 struct Cell {
@@ -187,23 +216,21 @@ __device__ __forceinline__ float frac32(long long q)
     return __uint_as_float(0x3f800000u | ((unsigned)q >> 9)) - 1.0f;
 }
 
-// Cell of a sample.  x and y stay inside the padded grid by construction (the grid is
-// validated to enclose the resin cylinder with a margin); z is clamped because the
-// sample range in z comes from the FP64 trace while positions here come from the FP32
-// table (a clamp that binds only for samples whose in-grid weight is ~0).
-__device__ __forceinline__ Cell cell_of(const OpParams &P, long long qx, long long qy, long long qz)
+// Cell of a sample at an absolute Q32.32 position (inside the padded grid: z by the ray's
+// sample range, x and y because the grid encloses the resin cylinder with a margin).
+__device__ __forceinline__ Cell cell_of(long long qx, long long qy, long long qz)
 {
     Cell c;
     c.ix = (int)(qx >> 32);
     c.iy = (int)(qy >> 32);
-    c.iz = min(max((int)(qz >> 32), 0), P.pz - 2);
+    c.iz = (int)(qz >> 32);
     c.fx = frac32(qx);
     c.fy = frac32(qy);
     c.fz = frac32(qz);
     return c;
 }
 
-// Addressing of a sample's corner (0,0,0): shared-memory box or global padded volume.
+// Addressing of a sample's corner (0,0,0) in the global padded volume.
 struct BoxAddr {
     int sx, sxy;
     __device__ __forceinline__ int operator()(const Cell &c) const { return c.iz * sxy + c.iy * sx + c.ix; }
@@ -212,18 +239,6 @@ struct BoxAddr {
 // i / d for 0 <= i < 2^22 and 1 <= d < 2^10 through an FP32 reciprocal: (i + 1/2) / d
 // lies at least 1/(2d) from an integer, well beyond the product's rounding error.
 __device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
-
-// Voxel sources for the gather: the global padded volume (read-only path) or the
-// shared-memory box.
-template <typename VT>
-struct GlobalSrc {
-    const VT *p;
-    __device__ __forceinline__ float operator()(int i) const { return ld1(p + i); }
-};
-struct SmemSrc {
-    const float *p;
-    __device__ __forceinline__ float operator()(int i) const { return p[i]; }
-};
 
 // Packed FP32 pairs (sm_100 family): one instruction performs two independent
 // round-to-nearest operations, so the results are bit-identical to the scalar forms while
@@ -262,36 +277,38 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return r;
 }
 
+// Trilinear value at a cell from its 8 corners (x-lerps of the z = 0 and z = 1 corners
+// in pairs, then the y-lerps, then z).
+__device__ __forceinline__ float trilerp(float fx, float fy, float fz, float v000, float v100, float v010, float v110,
+                                         float v001, float v101, float v011, float v111)
+{
+    const f32x2 fx2 = pk2(fx, fx);
+    const f32x2 a0 = pk2(v000, v001), a1 = pk2(v010, v011);
+    const f32x2 x0 = fma2(fx2, sub2(pk2(v100, v101), a0), a0);   // (x00, x01)
+    const f32x2 x1 = fma2(fx2, sub2(pk2(v110, v111), a1), a1);   // (x10, x11)
+    float y0, y1;
+    upk2(fma2(pk2(fy, fy), sub2(x1, x0), x0), y0, y1);
+    return fmaf(fz, y1 - y0, y0);
+}
+
+// ---- global-memory walks (chunks whose box does not fit in shared memory) ----------
 // Beer-Lambert factor of samples jl, jl+1, ...: exact exp2 at the start of each run,
-// then one multiply per sample (runs are one chunk long, ~30 samples, so the product
-// drifts by a few 1e-7 at most).
-template <class Src, class Addr>
-__device__ __forceinline__ float walk_gather(const OpParams &P, const Ray &R, int jl, int jh, const Src &src,
-                                             const Addr &addr)
+// then one multiply per sample.
+template <typename VT>
+__device__ __noinline__ float walk_gather_global(const OpParams &P, const Ray &R, int jl, int jh, const VT *vol)
 {
     long long qx = R.q0x + (long long)jl * R.sx;
     long long qy = R.q0y + (long long)jl * R.sy;
     long long qz = R.q0z + (long long)jl * R.sz;
-    const int sx = addr.sx, sxy = addr.sxy;
+    const int sx = P.px, sxy = P.px * P.py;
     float att = exp2f(R.att * ((float)jl + 0.5f));
     const float ratio = exp2f(R.att);
     float acc = 0.f;
-#pragma unroll 2
     for (int j = jl; j < jh; ++j) {
-        const Cell c = cell_of(P, qx, qy, qz);
-        const int b = addr(c);
-        const float v000 = src(b), v100 = src(b + 1);
-        const float v010 = src(b + sx), v110 = src(b + sx + 1);
-        const float v001 = src(b + sxy), v101 = src(b + sxy + 1);
-        const float v011 = src(b + sxy + sx), v111 = src(b + sxy + sx + 1);
-        // x-lerps of the z = 0 and z = 1 corners in pairs, then the y-lerps, then z
-        const f32x2 fx2 = pk2(c.fx, c.fx);
-        const f32x2 a0 = pk2(v000, v001), a1 = pk2(v010, v011);
-        const f32x2 x0 = fma2(fx2, sub2(pk2(v100, v101), a0), a0);   // (x00, x01)
-        const f32x2 x1 = fma2(fx2, sub2(pk2(v110, v111), a1), a1);   // (x10, x11)
-        float y0, y1;
-        upk2(fma2(pk2(c.fy, c.fy), sub2(x1, x0), x0), y0, y1);
-        const float val = fmaf(c.fz, y1 - y0, y0);
+        const Cell c = cell_of(qx, qy, qz);
+        const VT *p = vol + (c.iz * sxy + c.iy * sx + c.ix);
+        const float val = trilerp(c.fx, c.fy, c.fz, ld1(p), ld1(p + 1), ld1(p + sx), ld1(p + sx + 1), ld1(p + sxy),
+                                  ld1(p + sxy + 1), ld1(p + sxy + sx), ld1(p + sxy + sx + 1));
         acc = fmaf(att, val, acc);
         att *= ratio;
         qx += R.sx;
@@ -318,9 +335,9 @@ __device__ __forceinline__ Shares shares(float w, const Cell &c)
     return S;
 }
 
-// Global fallback: FP32 reductions straight into the padded accumulator.
-__device__ __forceinline__ void walk_scatter_global(const OpParams &P, const Ray &R, int jl, int jh, float wray,
-                                                    float *dst)
+// FP32 reductions straight into the padded accumulator.
+__device__ __noinline__ void walk_scatter_global(const OpParams &P, const Ray &R, int jl, int jh, float wray,
+                                                 float *dst)
 {
     long long qx = R.q0x + (long long)jl * R.sx;
     long long qy = R.q0y + (long long)jl * R.sy;
@@ -329,7 +346,7 @@ __device__ __forceinline__ void walk_scatter_global(const OpParams &P, const Ray
     float att = exp2f(R.att * ((float)jl + 0.5f));
     const float ratio = exp2f(R.att);
     for (int j = jl; j < jh; ++j) {
-        const Cell c = cell_of(P, qx, qy, qz);
+        const Cell c = cell_of(qx, qy, qz);
         float *p = dst + (c.iz * sxy + c.iy * sx + c.ix);
         const Shares S = shares(wray * att, c);
         atomicAdd(p, S.s000);
@@ -347,35 +364,82 @@ __device__ __forceinline__ void walk_scatter_global(const OpParams &P, const Ray
     }
 }
 
+// ---- shared-memory walks ------------------------------------------------------------
+// Inside a box the walk runs backwards, from the chunk's last sample jh-1 (anchored
+// exactly: its Q32.32 position cut to Q9.23 relative to the box origin) down to jl,
+// stepping by the ray's advance rounded to Q9.23.  All positions are then a linear
+// integer function of j, so the cells they visit lie between the cells of the two end
+// positions, which the box is built from (chunk_bounds computes the far end exactly as
+// the walk reaches it).  The truncated step drifts by < 2^-23 voxel per sample.
+struct Q23 {
+    int x, y, z;
+};
+
+// the Q32.32 step rounded to Q9.23 (any fixed integer step keeps the walk linear in j)
+__device__ __forceinline__ long long step23(long long s) { return (s + 256) >> 9; }
+
+// Absolute Q9.23 position of a chunk's last sample jh-1: the walk's exact anchor.
+struct Anchor {
+    long long x, y, z;
+};
+__device__ __forceinline__ Anchor anchor_at(const Ray &R, int jh)
+{
+    const long long j1 = jh - 1;
+    return Anchor{(R.q0x + j1 * R.sx) >> 9, (R.q0y + j1 * R.sy) >> 9, (R.q0z + j1 * R.sz) >> 9};
+}
+
+__device__ __forceinline__ float frac23(int q) { return __uint_as_float(0x3f800000u | ((unsigned)q & 0x7fffffu)) - 1.0f; }
+
+// Gather over samples jh-1 down to jl, Horner form: returns sum_j r^(j - jl) v_j,
+// r = the Beer-Lambert factor per sample (the caller multiplies by r^(jl + 1/2)).
+__device__ __forceinline__ float walk_gather_box(const Ray &R, const Anchor &an, int jl, int jh, int ox, int oy,
+                                                 int oz, const float *box, int sx, int sxy)
+{
+    int qx = (int)(an.x - ((long long)ox << 23));
+    int qy = (int)(an.y - ((long long)oy << 23));
+    int qz = (int)(an.z - ((long long)oz << 23));
+    const int dx = (int)step23(R.sx), dy = (int)step23(R.sy), dz = (int)step23(R.sz);
+    const float ratio = exp2f(R.att);
+    float acc = 0.f;
+#pragma unroll 2
+    for (int j = jh - 1; j >= jl; --j) {
+        const int b = (qz >> 23) * sxy + (qy >> 23) * sx + (qx >> 23);
+        const float *p = box + b;
+        const float val = trilerp(frac23(qx), frac23(qy), frac23(qz), p[0], p[1], p[sx], p[sx + 1], p[sxy],
+                                  p[sxy + 1], p[sxy + sx], p[sxy + sx + 1]);
+        acc = fmaf(acc, ratio, val);
+        qx -= dx;
+        qy -= dy;
+        qz -= dz;
+    }
+    return acc;
+}
+
 // Shared-memory box: fixed-point integer accumulation.  Shared-memory integer atomics
 // are native, FP32 ones are not.  `scale` maps the largest ray weight of the block to
 // well under 2^22, so every share rounds exactly through the 1.5 * 2^23 trick, and the
 // bound on shares per voxel and chunk keeps every box sum below 2^31.
-__device__ __forceinline__ int to_fixed(float x, float scale)
+__device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an, int jl, int jh, float wray,
+                                                 float scale, int ox, int oy, int oz, int *box, int sx, int sxy)
 {
-    return __float_as_int(fmaf(x, scale, 12582912.0f)) - 0x4B400000;
-}
-
-__device__ __forceinline__ void walk_scatter_box(const OpParams &P, const Ray &R, int jl, int jh, float wray,
-                                                 float scale, int *box, const BoxAddr &addr)
-{
-    long long qx = R.q0x + (long long)jl * R.sx;
-    long long qy = R.q0y + (long long)jl * R.sy;
-    long long qz = R.q0z + (long long)jl * R.sz;
-    const int sx = addr.sx, sxy = addr.sxy;
-    float att = exp2f(R.att * ((float)jl + 0.5f));
-    const float ratio = exp2f(R.att);
-    const float ws = wray * scale;
+    int qx = (int)(an.x - ((long long)ox << 23));
+    int qy = (int)(an.y - ((long long)oy << 23));
+    int qz = (int)(an.z - ((long long)oz << 23));
+    const int dx = (int)step23(R.sx), dy = (int)step23(R.sy), dz = (int)step23(R.sz);
+    // weight of sample jh-1, then one division by the per-sample factor per step down
+    float w = wray * scale * exp2f(R.att * ((float)(jh - 1) + 0.5f));
+    const float inv_ratio = exp2f(-R.att);
+    const f32x2 magic = pk2(12582912.0f, 12582912.0f);
 #pragma unroll 2
-    for (int j = jl; j < jh; ++j) {
-        const Cell c = cell_of(P, qx, qy, qz);
-        int *p = box + addr(c);
-        // the eight shares of shares() in pairs (z = 0, z = 1), converted to fixed point by
-        // the same 1.5 * 2^23 addition
-        const float w = ws * att, wz1 = w * c.fz, wz0 = w - wz1;
-        const f32x2 fx2 = pk2(c.fx, c.fx), magic = pk2(12582912.0f, 12582912.0f);
+    for (int j = jh - 1; j >= jl; --j) {
+        const float fx = frac23(qx), fy = frac23(qy), fz = frac23(qz);
+        int *p = box + ((qz >> 23) * sxy + (qy >> 23) * sx + (qx >> 23));
+        // the eight shares in pairs (z = 0, z = 1), converted to fixed point by the same
+        // 1.5 * 2^23 addition
+        const float wz1 = w * fz, wz0 = w - wz1;
+        const f32x2 fx2 = pk2(fx, fx);
         const f32x2 z = pk2(wz0, wz1);
-        const f32x2 w1 = mul2(z, pk2(c.fy, c.fy));         // (w01, w11)
+        const f32x2 w1 = mul2(z, pk2(fy, fy));             // (w01, w11)
         const f32x2 w0 = sub2(z, w1);                      // (w00, w10)
         const f32x2 s1a = mul2(w0, fx2), s1b = mul2(w1, fx2);   // (s100, s101), (s110, s111)
         int i000, i001, i100, i101, i010, i011, i110, i111;
@@ -391,16 +455,32 @@ __device__ __forceinline__ void walk_scatter_box(const OpParams &P, const Ray &R
         atomicAdd(p + sxy + 1, i101 - 0x4B400000);
         atomicAdd(p + sxy + sx, i011 - 0x4B400000);
         atomicAdd(p + sxy + sx + 1, i111 - 0x4B400000);
-        att *= ratio;
-        qx += R.sx;
-        qy += R.sy;
-        qz += R.sz;
+        w *= inv_ratio;
+        qx -= dx;
+        qy -= dy;
+        qz -= dz;
     }
+}
+
+// Cell bounds of a chunk's samples: the cell of its anchor (sample jh-1) and the cell the
+// backward walk reaches at jl.
+__device__ __forceinline__ void chunk_bounds(const Ray &R, const Anchor &an, int jl, int jh, int lo[3], int hi[3])
+{
+    const long long n = (long long)(jh - 1 - jl);
+    const long long bx = an.x - n * step23(R.sx), by = an.y - n * step23(R.sy), bz = an.z - n * step23(R.sz);
+    const int c0x = (int)(an.x >> 23), c0y = (int)(an.y >> 23), c0z = (int)(an.z >> 23);
+    const int c1x = (int)(bx >> 23), c1y = (int)(by >> 23), c1z = (int)(bz >> 23);
+    lo[0] = min(c0x, c1x); hi[0] = max(c0x, c1x) + 1;
+    lo[1] = min(c0y, c1y); hi[1] = max(c0y, c1y) + 1;
+    lo[2] = min(c0z, c1z); hi[2] = max(c0z, c1z) + 1;
 }
 
 // ---------------------------------------------------------------------------------
 // the tiled traversal, adjoint (FWD = false) or forward (FWD = true)
 // ---------------------------------------------------------------------------------
+// Box extents stay below 256 voxels per axis (Q9.23 box-relative positions).
+constexpr int kMaxBoxExtent = 255;
+
 template <bool FWD, typename VT, typename PT>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     tiled_kernel(const OpParams P, const VT *__restrict__ vol, PT *__restrict__ proj, float *__restrict__ acc,
@@ -410,13 +490,16 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     __shared__ int s_box[3][6];   // per chunk (rotating): min x,y,z and max x,y,z of the footprint
     __shared__ int s_rng[3][3];   // per aperture sample (rotating): first and last chunk, max |ray weight| bits
 
-    // lanes run down a pixel column (v), warps across columns (u): at every step the 32
+    // Grid: x = pixel-column tile, y = angle, z = pixel-row tile.  Blocks launch x fastest,
+    // so the blocks resident at a time share one row tile -- one slab of z planes of the
+    // volume and one band of the ray table, which then stay in L2 across the angles.
+    // Lanes run down a pixel column (v), warps across columns (u): at every step the 32
     // samples of a warp are stacked along z, one voxel plane apart, so with an odd plane
-    // stride their shared-memory words fall in distinct banks
+    // stride their shared-memory words fall in distinct banks.
     const int tid = threadIdx.y * kTileV + threadIdx.x;
     const int u = blockIdx.x * kTileU + threadIdx.y;
-    const int v = blockIdx.y * kTileV + threadIdx.x;
-    const int k = blockIdx.z;
+    const int k = blockIdx.y;
+    const int v = blockIdx.z * kTileV + threadIdx.x;
     const bool valid = u < P.nu && v < P.nv;
     const double2 cs = P.cs[k];
     const int64_t pix_index = ((int64_t)k * P.nv + v) * P.nu + u;
@@ -467,20 +550,22 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
         }
         float ray_acc = 0.f;
 
+        // Chunks of kChunkVox voxels along y; a chunk whose box does not fit in shared memory
+        // is retried as its two halves (block-uniform decision), and a half that still does
+        // not fit runs on global memory.
         for (int c = cmin; c <= cmax; ++c) {
+          int nsplit = 1;
+          for (int part = 0; part < nsplit; ++part) {
             const int rb = n_chunk % 3;
             ++n_chunk;
+            const int h0 = 2 * c + part * (2 / nsplit), h1 = h0 + 2 / nsplit;
             int jl = 0, jh = 0;
-            if (active) chunk_samples(P, R, c, cmin, cmax, jl, jh);
+            if (active) range_samples(P, R, h0, h1, cmin, cmax, jl, jh);
             int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+            Anchor an{0, 0, 0};
             if (jl < jh) {
-                const Cell c0 = cell_of(P, R.q0x + (long long)jl * R.sx, R.q0y + (long long)jl * R.sy,
-                                        R.q0z + (long long)jl * R.sz);
-                const long long j1 = jh - 1;
-                const Cell c1 = cell_of(P, R.q0x + j1 * R.sx, R.q0y + j1 * R.sy, R.q0z + j1 * R.sz);
-                lo[0] = min(c0.ix, c1.ix); hi[0] = max(c0.ix, c1.ix) + 1;
-                lo[1] = min(c0.iy, c1.iy); hi[1] = max(c0.iy, c1.iy) + 1;
-                lo[2] = min(c0.iz, c1.iz); hi[2] = max(c0.iz, c1.iz) + 1;
+                an = anchor_at(R, jh);
+                chunk_bounds(R, an, jl, jh, lo, hi);
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -497,81 +582,83 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
             __syncthreads();
             const int bx0 = s_box[rb][0] & ~3, by0 = s_box[rb][1], bz0 = s_box[rb][2];
             const int hx = s_box[rb][3], hy = s_box[rb][4], hz = s_box[rb][5];
+            const bool lo_inside = s_box[rb][0] >= 0 && by0 >= 0 && bz0 >= 0;
             if (tid == 0) {
                 const int nb = (rb + 2) % 3;
                 s_box[nb][0] = s_box[nb][1] = s_box[nb][2] = INT_MAX;
                 s_box[nb][3] = s_box[nb][4] = s_box[nb][5] = INT_MIN;
             }
-            if (hx == INT_MIN) continue;                      // no samples in this chunk
+            if (hx == INT_MIN) continue;                      // no samples in this range
             const int ex = ((hx + 4) & ~3) - bx0;             // x extent, a multiple of 4
             const int ey = hy + 1 - by0, ez = hz + 1 - bz0;
             const int sx = ex + 1, sxy = sx * (ey | 1);       // odd row and plane strides
             const int ex4 = ex >> 2;
             const int n4 = ex4 * ey * ez;
             const float inv_ex4 = 1.0f / (float)ex4, inv_ey = 1.0f / (float)ey;
-            if ((long long)sxy * ez <= kBoxFloats) {
+            // the box path needs the box inside the padded grid (the backward walk's truncated
+            // step can carry a sample a hair past a grid face: such ranges run on global
+            // memory with exact positions) and extents a Q9.23 offset can hold
+            const bool in_grid = lo_inside && hx <= P.px - 1 && hy <= P.py - 1 && hz <= P.pz - 1;
+            const bool fits = (long long)sxy * ez <= kBoxFloats && ex <= kMaxBoxExtent && ey <= kMaxBoxExtent &&
+                              ez <= kMaxBoxExtent;
+            if (!fits && nsplit == 1 && in_grid) {
+                nsplit = 2;          // the same decision in every thread: retry as two halves
+                part = -1;
+                continue;
+            }
+            if (fits && in_grid) {
                 if (!FWD) {
-                    if (ex4 <= kThreads) {
-                        // thread -> (row r0, 16-byte group x4) once; rows advance by `per`
-                        const int per = kThreads / ex4;
-                        const int r0 = fdiv(tid, inv_ex4), x4 = tid - r0 * ex4;
-                        if (r0 < per) {
-                            int zz = fdiv(r0, inv_ey), yy = r0 - zz * ey;
-                            const int dq = fdiv(per, inv_ey), dr = per - dq * ey;
-                            const VT *src = vol + (int64_t)bz0 * pxy + (int64_t)by0 * P.px + bx0 + 4 * x4;
-                            for (int r = r0; r < ey * ez; r += per) {
-                                const float4 q = ld4(src + (int64_t)zz * pxy + (int64_t)yy * P.px);
-                                float *b = box + zz * sxy + yy * sx + 4 * x4;
-                                b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
-                                zz += dq;
-                                yy += dr;
-                                if (yy >= ey) { yy -= ey; ++zz; }
-                            }
-                        }
-                    } else {
-                        for (int i = tid; i < n4; i += kThreads) {
-                            const int t = fdiv(i, inv_ex4), x4 = i - t * ex4;
-                            const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
-                            const float4 q =
-                                ld4(vol + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
+                    // thread -> (row r0, 16-byte group x4) once; rows advance by `per` (ex4 <= 64
+                    // here: extents are below 256)
+                    const int rows = ey * ez;
+                    const int per = kThreads / ex4;
+                    const int r0 = fdiv(tid, inv_ex4), x4 = tid - r0 * ex4;
+                    if (r0 < per) {
+                        int zz = fdiv(r0, inv_ey), yy = r0 - zz * ey;
+                        const int dq = fdiv(per, inv_ey), dr = per - dq * ey;
+                        const VT *src = vol + (int64_t)bz0 * pxy + (int64_t)by0 * P.px + bx0 + 4 * x4;
+                        for (int r = r0; r < rows; r += per) {
+                            const float4 q = ld4(src + (int64_t)zz * pxy + (int64_t)yy * P.px);
                             float *b = box + zz * sxy + yy * sx + 4 * x4;
                             b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
+                            zz += dq;
+                            yy += dr;
+                            if (yy >= ey) { yy -= ey; ++zz; }
                         }
                     }
                 } else {
                     for (int i = tid; i < sxy * ez; i += kThreads) box[i] = 0.f;
                 }
                 __syncthreads();
-                // box-relative addressing folded into the base pointer
-                const BoxAddr addr{sx, sxy};
-                const int off = bz0 * sxy + by0 * sx + bx0;
                 if (jl < jh) {
                     if (!FWD)
-                        ray_acc += walk_gather(P, R, jl, jh, SmemSrc{box - off}, addr);
+                        ray_acc += exp2f(R.att * ((float)jl + 0.5f)) *
+                                   walk_gather_box(R, an, jl, jh, bx0, by0, bz0, box, sx, sxy);
                     else
-                        walk_scatter_box(P, R, jl, jh, wray, scale, reinterpret_cast<int *>(box) - off, addr);
+                        walk_scatter_box(R, an, jl, jh, wray, scale, bx0, by0, bz0, reinterpret_cast<int *>(box),
+                                         sx, sxy);
                 }
                 if (FWD) {
                     __syncthreads();
                     const float inv = 1.0f / scale;
                     const int *ib = reinterpret_cast<const int *>(box);
                     for (int i = tid; i < n4; i += kThreads) {
-                        const int t = fdiv(i, inv_ex4), x4 = i - t * ex4;
+                        const int t = fdiv(i, inv_ex4), xq = i - t * ex4;
                         const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
-                        const int *b = ib + zz * sxy + yy * sx + 4 * x4;
+                        const int *b = ib + zz * sxy + yy * sx + 4 * xq;
                         const int b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
                         if ((b0 | b1 | b2 | b3) != 0)
-                            red_v4(acc + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4,
+                            red_v4(acc + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * xq,
                                    make_float4((float)b0 * inv, (float)b1 * inv, (float)b2 * inv, (float)b3 * inv));
                     }
                 }
             } else if (jl < jh) {
-                const BoxAddr addr{P.px, pxy};
                 if (!FWD)
-                    ray_acc += walk_gather(P, R, jl, jh, GlobalSrc<VT>{vol}, addr);
+                    ray_acc += walk_gather_global(P, R, jl, jh, vol);
                 else
                     walk_scatter_global(P, R, jl, jh, wray, acc);
             }
+          }
         }
         if (!FWD && active) pix = fmaf(R.w, ray_acc, pix);
     }
@@ -594,7 +681,7 @@ inline unsigned grid_for(const vamrt_projector *p, int64_t n, int threads)
 
 inline dim3 op_grid(const OpParams &P)
 {
-    return dim3((P.nu + kTileU - 1) / kTileU, (P.nv + kTileV - 1) / kTileV, P.n_angles);
+    return dim3((P.nu + kTileU - 1) / kTileU, P.n_angles, (P.nv + kTileV - 1) / kTileV);
 }
 
 constexpr size_t kSmem = sizeof(float) * kBoxFloats;

@@ -7,7 +7,9 @@
 // unpolarised Fresnel transmission, does the same at the inner cylinder, and runs
 // straight through the resin to the inner wall on the far side.  Everything up to the
 // stored segment is FP64: the quadratic near grazing incidence and the refraction are
-// where FP32 would lose the geometry.  The segment is stored in FP32, in voxel units.
+// where FP32 would lose the geometry.  The segment is stored in FP64, in voxel units: on a
+// 768-voxel grid an FP32 entry point or direction would already misplace far samples by
+// ~1e-5 voxel.
 #include <math.h>
 
 #include "internal.cuh"
@@ -190,7 +192,7 @@ __device__ void stop_point(const TraceParams &P, int u, int v, int a, double &xi
     }
 }
 
-__global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *__restrict__ B,
+__global__ void raytable_kernel(TraceParams P, double4 *__restrict__ A, double4 *__restrict__ B,
                                 int2 *__restrict__ J, unsigned long long *__restrict__ counters)
 {
     const int64_t n_rays = (int64_t)P.nu * P.nv * P.M;
@@ -200,8 +202,8 @@ __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *_
     const int v = (int)((r / P.nu) % P.nv);
     const int a = (int)(r / ((int64_t)P.nu * P.nv));
 
-    A[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-    B[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    A[r] = make_double4(0.0, 0.0, 0.0, 0.0);
+    B[r] = make_double4(0.0, 0.0, 0.0, 0.0);
     J[r] = make_int2(0, 0);
 
     // image point of the pixel in the best-focus plane y = 0
@@ -259,8 +261,8 @@ __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *_
     if (jhi <= jlo) { jlo = 0; jhi = 0; }
 
     const double inv_h = 1.0 / P.h;
-    A[r] = make_float4((float)(e.x * inv_h), (float)(e.y * inv_h), (float)(e.z * inv_h), (float)(delta * inv_h));
-    B[r] = make_float4((float)dr.x, (float)dr.y, (float)dr.z, (float)(T1 * T2 * delta / P.M));
+    A[r] = make_double4(e.x * inv_h, e.y * inv_h, e.z * inv_h, delta * inv_h);
+    B[r] = make_double4(dr.x, dr.y, dr.z, T1 * T2 * delta / P.M);
     J[r] = make_int2(jlo, jhi);
     atomicAdd(&counters[0], 1ull);
     atomicAdd(&counters[1], (unsigned long long)(jhi - jlo));
@@ -268,7 +270,7 @@ __global__ void raytable_kernel(TraceParams P, float4 *__restrict__ A, float4 *_
 
 }  // namespace
 
-cudaError_t launch_raytable(const TraceParams &T, float4 *A, float4 *B, int2 *J,
+cudaError_t launch_raytable(const TraceParams &T, double4 *A, double4 *B, int2 *J,
                             unsigned long long *counters, cudaStream_t s)
 {
     const int64_t n = (int64_t)T.nu * T.nv * T.M;
