@@ -115,45 +115,89 @@ def reduce_max(value: float, dist, device) -> float:
 
 
 def cpu_threads() -> int:
-    """Host cores the oracle sample runs on: one thread per core (the oracle's C calls
-    release the GIL, so the threads run in parallel)."""
+    """Host cores the oracle sample runs on: one worker process per core."""
     return os.cpu_count() or 1
 
 
-def oracle_sample(w, pupil, target, rows, angle=0, threads=None):
-    """Oracle A^T then A over pixel rows `rows` of one angle, split over host threads:
-    each pixel's projection (FP64 oracle), clamped at 0 as the optimiser does, then the dose
-    of those pixels (sparse, FP64).  Returns (samples, wall seconds, threads)."""
-    import concurrent.futures as cf
+def _oracle_rows_worker(job):
+    """One worker of the CPU baseline (a spawned process): for every pixel of its rows, the
+    FP64 oracle's projection value (Sec. 2.4) and then that pixel's dose contributions
+    (Sec. 2.5), through the oracle's own C entry points.  Returns the seconds spent."""
+    import ctypes
 
     from oracle import vam_oracle as O
-    threads = threads or cpu_threads()
-    M = w.rays_per_pixel
-    # samples the chosen pixels visit (counted outside the timed region): per traced ray,
-    # the midpoints whose footprint reaches the grid
-    n = 0
+    w, pupil, vol_path, shape, angle, rows = job
+    vol = np.memmap(vol_path, dtype=np.float64, mode="r", shape=shape)
+    L = O.lib()
+    G = O.geom(w, pupil)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vptr = vol.ctypes.data_as(dp)
+    cap = 1 << 18
+    idx = np.empty(cap, np.int64)
+    val = np.empty(cap, np.float64)
+    t0 = time.perf_counter()
     for v in rows:
         for u in range(w.nu):
-            for a in range(M):
-                r = O.trace(w, pupil, u, v, a)
-                if r["status"] != 2:
-                    continue
-                dl = r["ell"] / r["k"]
-                j = np.arange(r["k"])
-                qz = (r["e"][2] + (j + 0.5) * dl * r["d2"][2]) / w.voxel_mm + 0.5 * (w.nz - 1)
-                n += int(np.count_nonzero((qz > -1) & (qz < w.nz)))
-    vol = target if target.dtype == np.float64 else np.ascontiguousarray(target, dtype=np.float64)
-    chunks = [[(angle, v, u) for u in range(w.nu)] for v in rows]
+            y = L.orc_adjoint_pixel(G.ref, vptr, angle, v, u)
+            n = L.orc_forward_pixel(G.ref, angle, v, u, max(y, 0.0), idx.ctypes.data, val.ctypes.data, cap)
+            if n > cap:
+                cap = int(n)
+                idx = np.empty(cap, np.int64)
+                val = np.empty(cap, np.float64)
+                L.orc_forward_pixel(G.ref, angle, v, u, max(y, 0.0), idx.ctypes.data, val.ctypes.data, cap)
+    return time.perf_counter() - t0
 
-    def work(pix):
-        y = O.adjoint_pixels(w, vol, pupil, pix)
-        O.forward_pixels(w, pupil, pix, np.maximum(y, 0.0))
 
-    t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(work, chunks))
-    dt = time.perf_counter() - t0
-    return 2 * n, dt, threads
+class OracleSampler:
+    """The FP64 oracle timed on the host cores: a pool of `threads` spawned worker processes
+    sharing the volume through a file mapping.  run(rows, angle): oracle A^T then A over
+    those pixel rows of one angle, rows dealt round-robin over the workers -- each pixel's
+    projection (clamped at 0 as the optimiser does), then that pixel's dose contributions.
+    Returns (samples, wall seconds, workers)."""
+
+    def __init__(self, w, pupil, target, threads=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import tempfile
+
+        from oracle import vam_oracle as O
+        O.build()
+        self.w, self.pupil, self.shape = w, pupil, tuple(target.shape)
+        self.threads = threads or cpu_threads()
+        self.tmp = tempfile.TemporaryDirectory()
+        self.path = os.path.join(self.tmp.name, "volume.f64")
+        np.ascontiguousarray(target, dtype=np.float64).tofile(self.path)
+        self.pool = cf.ProcessPoolExecutor(max_workers=self.threads, mp_context=mp.get_context("spawn"))
+        # start every worker (imports, library load) before anything is timed
+        list(self.pool.map(_oracle_rows_worker, [(w, pupil, self.path, self.shape, 0, [])] * self.threads))
+
+    def samples(self, rows):
+        """Samples the chosen pixel rows visit: per traced ray, the midpoints whose footprint
+        reaches the grid (counted outside any timed region)."""
+        from oracle import vam_oracle as O
+        w, n = self.w, 0
+        for v in rows:
+            for u in range(w.nu):
+                for a in range(w.rays_per_pixel):
+                    r = O.trace(w, self.pupil, u, v, a)
+                    if r["status"] != 2:
+                        continue
+                    dl = r["ell"] / r["k"]
+                    j = np.arange(r["k"])
+                    qz = (r["e"][2] + (j + 0.5) * dl * r["d2"][2]) / w.voxel_mm + 0.5 * (w.nz - 1)
+                    n += int(np.count_nonzero((qz > -1) & (qz < w.nz)))
+        return 2 * n
+
+    def run(self, rows, angle=0):
+        jobs = [(self.w, self.pupil, self.path, self.shape, angle, rows[i::self.threads]) for i in range(self.threads)]
+        jobs = [j for j in jobs if j[-1]]
+        t0 = time.perf_counter()
+        list(self.pool.map(_oracle_rows_worker, jobs))
+        return time.perf_counter() - t0, len(jobs)
+
+    def close(self):
+        self.pool.shutdown()
+        self.tmp.cleanup()
 
 
 def sample_rows(w, count):
@@ -167,18 +211,21 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     pupil = I.workload_pupil(w)
-    target = I.make_target(w).astype(np.float64)
+    target = I.make_target(w)
     rows = sample_rows(w, args.ref_rows)
+    S = OracleSampler(w, pupil, target)
+    n_rows = S.samples(rows)
     for _ in range(args.warmup):
-        oracle_sample(w, pupil, target, rows[:1])
-    tot_n, tot_t, threads = 0, 0.0, cpu_threads()
+        S.run(rows[:1])
+    tot_n, tot_t, threads = 0, 0.0, S.threads
     for s in range(args.steps):
-        n, dt, threads = oracle_sample(w, pupil, target, rows, angle=(s * 37) % w.n_angles)
-        tot_n += n
+        dt, threads = S.run(rows, angle=0)
+        tot_n += n_rows
         tot_t += dt
+    S.close()
     value = tot_n / tot_t
     sample = (f"{args.ref_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of one angle per step "
-              f"(of {w.nv} rows x {w.n_angles} angles), projection then dose, FP64 oracle on {threads} threads")
+              f"(of {w.nv} rows x {w.n_angles} angles), projection then dose, FP64 oracle in {threads} worker processes")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
@@ -342,26 +389,43 @@ def warm_start_time_to_target(args):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     rows = WS.compare(P, net, w, range(100000, 100000 + args.ws_eval), plain_iters=w.osmo_iters,
-                      cont_iters=12, step=0.5, dtype=torch.bfloat16, beta=args.ttt_beta, mu=args.ttt_mu)
+                      cont_iters=12, step=0.5, dtype=torch.bfloat16, beta=args.ttt_beta, mu=args.ttt_mu,
+                      loss_iters=args.ws_loss_iters, loss_lr=args.ws_loss_lr)
     network = network_throughput(net, pairs[0][1], pairs[0][2], 1.0)
+
+    def ratio_of(x, r):
+        return None if x is None else x / r["plain_seconds"]
 
     held = []
     for r in rows:
-        ratio = None if r["warm_seconds_to_target"] is None else r["warm_seconds_to_target"] / r["plain_seconds"]
         held.append({"seed": r["seed"], "plain_iterations": w.osmo_iters, "plain_seconds": r["plain_seconds"],
-                     "plain_final_ver": r["plain_final_ver"], "warm_iterations": r["warm_iters_to_target"],
-                     "warm_seconds_incl_inference": r["warm_seconds_to_target"],
-                     "inference_seconds": r["inference_seconds"], "time_ratio": ratio,
-                     "warm_best_ver": min(r["warm_ver"]), "no_network_iterations": r["cold_iters_to_target"],
+                     "plain_final_ver": r["plain_final_ver"],
+                     "warm_loss_iterations": r["warm_loss_iters_to_target"],
+                     "time_ratio": ratio_of(r["warm_loss_seconds_to_target"], r),
+                     "inference_seconds": r["inference_seconds"],
+                     "no_network_loss_iterations": r["cold_loss_iters_to_target"],
+                     "no_network_loss_time_ratio": ratio_of(r["cold_loss_seconds_to_target"], r),
+                     "warm_projection_space_iterations": r["warm_iters_to_target"],
+                     "warm_projection_space_time_ratio": ratio_of(r["warm_seconds_to_target"], r),
                      "relaxed_iterations": r["relaxed_iters_to_target"],
-                     "relaxed_time_ratio": None if r["relaxed_seconds_to_target"] is None
-                     else r["relaxed_seconds_to_target"] / r["plain_seconds"]})
+                     "relaxed_time_ratio": ratio_of(r["relaxed_seconds_to_target"], r)})
+
+    def summary(key):
+        vals = [h[key] for h in held if h[key] is not None]
+        return {"reached": f"{len(vals)}/{len(held)}", "median_time_ratio_of_reached": float(np.median(vals))
+                if vals else None, "median_time_ratio_all": float(np.median([h[key] if h[key] is not None
+                                                                             else float("inf") for h in held]))}
+
     ratios = [h["time_ratio"] for h in held if h["time_ratio"] is not None]
     rel = [h["relaxed_time_ratio"] for h in held if h["relaxed_time_ratio"] is not None]
     return {"workload": w.name, "target": "VER <= 1.01 x plain FP32 final VER",
             "train_pairs": len(pairs), "pair_iterations": w.osmo_iters, "epochs": args.ws_epochs,
             "data_generation_seconds": t1 - t0, "training_seconds": t2 - t1, "final_train_loss": losses[-1],
-            "continuation": "projection space, BF16-stored projections and dose, relaxation 0.5",
+            "continuation": f"thresholded-loss Adam steps (adjoint-driven, step {args.ws_loss_lr:g} x mean "
+                            "projection, d_l 0.9, d_h 1.0), BF16-stored projections and dose",
+            "warm_start": summary("time_ratio"), "no_network_same_continuation": summary("no_network_loss_time_ratio"),
+            "warm_start_projection_space": summary("warm_projection_space_time_ratio"),
+            "relaxed_no_network": summary("relaxed_time_ratio"),
             "network": network,
             "held_out": held, "reached": f"{len(ratios)}/{len(held)}",
             "median_time_ratio_of_reached": float(np.median(ratios)) if ratios else None,
@@ -491,6 +555,25 @@ def run_gpu(args, rank, world):
         except Exception:
             traffic = None
 
+    # ---- the tall build (384 x 384 x 512, 720 angles, 8 rays) with BF16-stored projections
+    # and dose, beside the headline: one timed optimiser iteration after one warm-up ----
+    tall = None
+    if args.tall and world == 1:
+        wt3 = I.WORKLOADS["tall_384x384x512_720ang_8rays"]
+        P3 = vamrt.Projector.from_workload(wt3, I.workload_pupil(wt3))
+        f3 = torch.from_numpy(I.make_target(wt3)).to(dev)
+        m3 = f3.clone()
+        g3 = torch.empty(wt3.proj_shape, device=dev, dtype=torch.bfloat16)
+        d3 = torch.empty(wt3.vol_shape, device=dev, dtype=torch.bfloat16)
+        spp3 = P3.sample_count()
+        for it in range(2):
+            r3 = P3.optimize(f3, model=m3, max_iter=1, tol=0.0, proj=g3, dose=d3, timing=True)
+        tall = {"workload": wt3.name, "storage": "bf16 projections and dose, fp32 sums",
+                "samples_per_pass": spp3, "adjoint_ms": r3["adjoint_ms"], "forward_ms": r3["forward_ms"],
+                "samples_per_s": 2 * spp3 / ((r3["adjoint_ms"] + r3["forward_ms"] + r3["update_ms"]) / 1e3),
+                "adjoint_samples_per_s": spp3 / (r3["adjoint_ms"] / 1e3)}
+        del P3, f3, m3, g3, d3
+
     # ---- time to target, on its own (smaller) workload: plain FP32 optimiser vs variants ----
     ttt = None
     if args.ttt_iters > 0:
@@ -511,11 +594,15 @@ def run_gpu(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, dt, threads = oracle_sample(w, pupil, target_np, sample_rows(w, args.cpu_rows))
+        S = OracleSampler(w, pupil, target_np)
+        rows = sample_rows(w, args.cpu_rows)
+        n = S.samples(rows)
+        dt, threads = S.run(rows)
+        S.close()
         cpu = {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_rows} pixel rows x {w.nu} columns x {w.rays_per_pixel} rays of angle 0 "
                          f"(of {w.nv} rows x {w.n_angles} angles), projection then dose, FP64 oracle on "
-                         f"{threads} threads ({n} samples, {dt:.1f} s)"}
+                         f"{threads} worker processes ({n} samples, {dt:.1f} s)"}
 
     if dist:
         dist.barrier()
@@ -551,6 +638,7 @@ def run_gpu(args, rank, world):
                              "peak_kind": peak_kind}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": host_target.numel() * 4,
                 "d2h_bytes_per_step": host_proj.numel() * 4 + 8},
+        "tall_build_bf16": tall,
         "time_to_target": ttt,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -569,8 +657,10 @@ def main():
     ap.add_argument("--angles", type=int, default=0, help="override the angle count (small profiling cases)")
     ap.add_argument("--nz", type=int, default=0, help="override the grid's plane count (small profiling cases)")
     ap.add_argument("--nv", type=int, default=0, help="override the pixel row count (small profiling cases)")
-    ap.add_argument("--cpu-rows", type=int, default=128)
-    ap.add_argument("--ref-rows", type=int, default=32)
+    ap.add_argument("--cpu-rows", type=int, default=64)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--no-tall", dest="tall", action="store_false",
+                    help="skip the BF16-storage iteration on the 384x384x512 tall-build workload")
     ap.add_argument("--ttt-workload", default=TTT_WORKLOAD,
                     help="workload of the time-to-target comparison (its own projector)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -585,6 +675,10 @@ def main():
     ap.add_argument("--ws-train", type=int, default=64, help="warm-start training targets (0 = skip)")
     ap.add_argument("--ws-epochs", type=int, default=8)
     ap.add_argument("--ws-eval", type=int, default=4, help="held-out targets for the warm-start comparison")
+    ap.add_argument("--ws-loss-lr", type=float, default=0.2,
+                    help="Adam step of the warm start's thresholded-loss continuation (x mean projection)")
+    ap.add_argument("--ws-loss-iters", type=int, default=20,
+                    help="iterations of the warm start's thresholded-loss continuation")
     ap.add_argument("--network-only", action="store_true",
                     help="time the warm-start network's convolutions alone and print their JSON")
     ap.add_argument("--warmstart-only", action="store_true",

@@ -416,6 +416,12 @@ vamrt_status vamrt_conv3d_wgrad_plan(int32_t d, int32_t h, int32_t wd, int32_t c
  *   dz (BF16, layout of z, may be NULL) = dloss/dz.
  * vamrt_nn_add: y += x (BF16, n elements).
  * vamrt_projected_step: g <- max(0, g - eta grad) (FP32, n elements).
+ * vamrt_projected_adam: one Adam step on projections, kept non-negative:
+ *   m <- b1 m + (1-b1) grad; v <- b2 v + (1-b2) grad^2;
+ *   g <- max(0, g - lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps)),
+ *   and g_bf16 (may be NULL) <- g rounded to BF16 (the storage the operators then read).
+ *   FP32 g, grad, m, v of n elements; step >= 1.  The adjoint-driven continuation of the
+ *   warm start: grad = A^T dL/dD of the thresholded dose loss.
  * vamrt_nn_absmax: *out = max |x| over n FP32 elements (out: device float).
  * Errors: EINVAL (NULL or bad sizes), ECUDA.
  */
@@ -437,6 +443,8 @@ vamrt_status vamrt_nn_head_mse(const float *z, int32_t cz, const float *base, fl
                                int32_t nv, int32_t nu, int32_t d_padded, double *loss, void *stream);
 vamrt_status vamrt_nn_add(const void *x, void *y, int64_t n, void *stream);
 vamrt_status vamrt_projected_step(float *g, const float *grad, float eta, int64_t n, void *stream);
+vamrt_status vamrt_projected_adam(float *g, const float *grad, float *m, float *v, void *g_bf16, int64_t n, float lr,
+                                  float beta1, float beta2, float eps, int32_t step, void *stream);
 vamrt_status vamrt_nn_absmax(const float *x, int64_t n, float *out, void *stream);
 
 /*

@@ -21,7 +21,7 @@ constexpr int kRedBlocks = 1024;
 constexpr int kTileU = 8;
 constexpr int kTileV = 32;
 constexpr int kThreads = kTileU * kTileV;
-constexpr int kChunkVox = 16;
+constexpr int kChunkVox = 20;
 constexpr int kBoxFloats = 18 * 1024;
 constexpr int kBlocksPerSm = 3;
 
@@ -162,7 +162,7 @@ cudaError_t nn_relu_bwd(const void *y, void *dy, int64_t n, cudaStream_t s);
 cudaError_t nn_bias_grad(const void *dy, float *db, int64_t npos, int C, cudaStream_t s);
 cudaError_t nn_flip_weights(const void *w, void *wt, int cout, int taps, int cin, cudaStream_t s);
 cudaError_t nn_adam(float *p, const float *g, float *m, float *v, void *pb, int64_t n, float lr, float b1, float b2,
-                    float eps, int step, cudaStream_t s);
+                    float eps, int step, bool nonneg, cudaStream_t s);
 cudaError_t nn_prepare_input(const float *proj, void *x, int A, int V, int U, int Dp, float scale, cudaStream_t s);
 cudaError_t nn_head_mse(const float *z, int cz, const float *base, float in_scale, const float *target,
                         float target_scale, float *out, float out_scale, void *dz, int A, int V, int U, int Dp,

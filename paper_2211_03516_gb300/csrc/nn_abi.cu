@@ -101,7 +101,16 @@ vamrt_status vamrt_nn_adam(float *param, const float *grad, float *m, float *v, 
                            float beta1, float beta2, float eps, int32_t step, void *stream)
 {
     if (!param || !grad || !m || !v || n < 0 || step < 1) return einval("bad argument");
-    return cuda_status(vamrt::nn_adam(param, grad, m, v, param_bf16, n, lr, beta1, beta2, eps, step,
+    return cuda_status(vamrt::nn_adam(param, grad, m, v, param_bf16, n, lr, beta1, beta2, eps, step, false,
+                                      (cudaStream_t)stream));
+}
+
+vamrt_status vamrt_projected_adam(float *g, const float *grad, float *m, float *v, void *g_bf16, int64_t n, float lr,
+                                  float beta1, float beta2, float eps, int32_t step, void *stream)
+{
+    if (!g || !grad || !m || !v || n < 0 || step < 1) return einval("bad argument");
+    if (!(lr >= 0.f) || !(eps > 0.f)) return einval("lr must be >= 0 and eps > 0");
+    return cuda_status(vamrt::nn_adam(g, grad, m, v, g_bf16, n, lr, beta1, beta2, eps, step, true,
                                       (cudaStream_t)stream));
 }
 

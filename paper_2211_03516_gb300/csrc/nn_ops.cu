@@ -288,9 +288,10 @@ __global__ void flip_weights_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bf
 }
 
 // Adam on FP32 master parameters; refreshes their BF16 copy
+// Adam step; lo bounds the parameters from below (-INFINITY: none; 0: projections)
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, __nv_bfloat16 *__restrict__ pb, int64_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2)
+                            float eps, float c1, float c2, float lo)
 {
     GRID_STRIDE(i, n)
     {
@@ -299,7 +300,7 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float pi = fmaxf(lo, p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps));
         p[i] = pi;
         if (pb) pb[i] = tobf(pi);
     }
@@ -472,10 +473,11 @@ cudaError_t nn_flip_weights(const void *w, void *wt, int cout, int taps, int cin
 }
 
 cudaError_t nn_adam(float *p, const float *g, float *m, float *v, void *pb, int64_t n, float lr, float b1, float b2,
-                    float eps, int step, cudaStream_t s)
+                    float eps, int step, bool nonneg, cudaStream_t s)
 {
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-    adam_kernel<<<grid_n(n), kT, 0, s>>>(p, g, m, v, (__nv_bfloat16 *)pb, n, lr, b1, b2, eps, c1, c2);
+    adam_kernel<<<grid_n(n), kT, 0, s>>>(p, g, m, v, (__nv_bfloat16 *)pb, n, lr, b1, b2, eps, c1, c2,
+                                         nonneg ? 0.f : -INFINITY);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -124,8 +124,12 @@ struct Ray {
     float w;                  // T1 T2 delta_mm / M
     float ey, dy;             // theta = 0 frame: y(j) = ey + (j + 1/2) dy (voxels)
     float inv_dy;             // 1 / dy
+    int d23x, d23y, d23z;     // the advance rounded to Q9.23 (box walks)
     int jlo, jhi;
 };
+
+// the Q32.32 step rounded to Q9.23 (any fixed integer step keeps the walk linear in j)
+__device__ __forceinline__ long long step23(long long s) { return (s + 256) >> 9; }
 
 // Q32.32 z of sample j lies in [0, pz - 1): its cell and the cell above are inside the
 // padded grid.
@@ -161,6 +165,9 @@ __device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 
     R.ey = (float)A.y;
     R.dy = (float)(A.w * B.y);
     R.inv_dy = 1.0f / R.dy;
+    R.d23x = (int)step23(R.sx);
+    R.d23y = (int)step23(R.sy);
+    R.d23z = (int)step23(R.sz);
     // The traced sample range [j_lo, j_hi) keeps -1 < q_z < nz in FP64; the FP32 table's
     // rounding can put an end sample a hair outside.  Drop such end samples (their
     // in-grid weight is ~1e-5 of a sample's) so that no sample needs a clamp later.
@@ -375,8 +382,6 @@ struct Q23 {
     int x, y, z;
 };
 
-// the Q32.32 step rounded to Q9.23 (any fixed integer step keeps the walk linear in j)
-__device__ __forceinline__ long long step23(long long s) { return (s + 256) >> 9; }
 
 // Absolute Q9.23 position of a chunk's last sample jh-1: the walk's exact anchor.
 struct Anchor {
@@ -398,7 +403,7 @@ __device__ __forceinline__ float walk_gather_box(const Ray &R, const Anchor &an,
     int qx = (int)(an.x - ((long long)ox << 23));
     int qy = (int)(an.y - ((long long)oy << 23));
     int qz = (int)(an.z - ((long long)oz << 23));
-    const int dx = (int)step23(R.sx), dy = (int)step23(R.sy), dz = (int)step23(R.sz);
+    const int dx = R.d23x, dy = R.d23y, dz = R.d23z;
     const float ratio = exp2f(R.att);
     float acc = 0.f;
 #pragma unroll 2
@@ -425,7 +430,7 @@ __device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an,
     int qx = (int)(an.x - ((long long)ox << 23));
     int qy = (int)(an.y - ((long long)oy << 23));
     int qz = (int)(an.z - ((long long)oz << 23));
-    const int dx = (int)step23(R.sx), dy = (int)step23(R.sy), dz = (int)step23(R.sz);
+    const int dx = R.d23x, dy = R.d23y, dz = R.d23z;
     // weight of sample jh-1, then one division by the per-sample factor per step down
     float w = wray * scale * exp2f(R.att * ((float)(jh - 1) + 0.5f));
     const float inv_ratio = exp2f(-R.att);
@@ -467,7 +472,7 @@ __device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an,
 __device__ __forceinline__ void chunk_bounds(const Ray &R, const Anchor &an, int jl, int jh, int lo[3], int hi[3])
 {
     const long long n = (long long)(jh - 1 - jl);
-    const long long bx = an.x - n * step23(R.sx), by = an.y - n * step23(R.sy), bz = an.z - n * step23(R.sz);
+    const long long bx = an.x - n * R.d23x, by = an.y - n * R.d23y, bz = an.z - n * R.d23z;
     const int c0x = (int)(an.x >> 23), c0y = (int)(an.y >> 23), c0z = (int)(an.z >> 23);
     const int c1x = (int)(bx >> 23), c1y = (int)(by >> 23), c1z = (int)(bz >> 23);
     lo[0] = min(c0x, c1x); hi[0] = max(c0x, c1x) + 1;
@@ -617,6 +622,8 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
                         int zz = fdiv(r0, inv_ey), yy = r0 - zz * ey;
                         const int dq = fdiv(per, inv_ey), dr = per - dq * ey;
                         const VT *src = vol + (int64_t)bz0 * pxy + (int64_t)by0 * P.px + bx0 + 4 * x4;
+                        // unrolled so that several rows' loads are in flight before their stores
+#pragma unroll 4
                         for (int r = r0; r < rows; r += per) {
                             const float4 q = ld4(src + (int64_t)zz * pxy + (int64_t)yy * P.px);
                             float *b = box + zz * sxy + yy * sx + 4 * x4;

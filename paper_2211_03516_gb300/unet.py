@@ -96,10 +96,12 @@ def _setup_nn(L):
     L.vamrt_nn_head_mse.argtypes = [vp, i32, vp, f32, vp, f32, vp, f32, vp, i32, i32, i32, i32, vp, vp]
     L.vamrt_nn_add.argtypes = [vp, vp, i64, vp]
     L.vamrt_projected_step.argtypes = [vp, vp, f32, i64, vp]
+    L.vamrt_projected_adam.argtypes = [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp]
     L.vamrt_nn_absmax.argtypes = [vp, i64, vp, vp]
     for n in ("vamrt_conv3d_wgrad_bf16", "vamrt_nn_resample", "vamrt_nn_concat", "vamrt_nn_relu_backward",
               "vamrt_nn_bias_grad", "vamrt_nn_flip_weights", "vamrt_nn_adam", "vamrt_nn_prepare_input",
-              "vamrt_nn_head_mse", "vamrt_nn_add", "vamrt_projected_step", "vamrt_nn_absmax"):
+              "vamrt_nn_head_mse", "vamrt_nn_add", "vamrt_projected_step", "vamrt_projected_adam",
+              "vamrt_nn_absmax"):
         getattr(L, n).restype = ctypes.c_int
     L._nn_ready = True
     return L

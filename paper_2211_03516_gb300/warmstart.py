@@ -4,8 +4,10 @@ The network (unet.UNet3D, tensor-core convolutions) maps a target's projections
 A^T f -- the optimiser's own first projections -- to the projections the plain
 optimiser reaches after many iterations.  Training pairs come from the plain ray-traced
 optimiser itself (object-space iterations from m = f).  At inference the predicted
-projections start the projection-space iteration of vamrt_optimize, and the plain
-optimiser's voxel error rate (VER) judges the result.  Both inputs and targets are
+projections start an adjoint-driven continuation -- projected Adam steps on the thresholded
+dose loss, gradients from the projection kernel (loss_curve) -- or the projection-space
+iteration of vamrt_optimize, and the plain optimiser's voxel error rate (VER) judges the
+result.  Both inputs and targets are
 scaled by 1 / max(A^T f) so the network sees values in [0, 1].
 """
 from __future__ import annotations
@@ -103,13 +105,59 @@ def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.
     return np.array(vers), np.array(times)
 
 
+def loss_curve(P: V.Projector, f: torch.Tensor, g0: torch.Tensor, iters: int, lr: float = 0.2, d_l: float = 0.9,
+               d_h: float = 1.0, dtype=torch.bfloat16, goal=None):
+    """Adjoint-driven continuation from g0: projected Adam steps on the thresholded dose
+    loss L(D), D = A g, L = mean_P relu(d_h - D)^2 + mean_Q relu(D - d_l)^2 (the
+    differentiable path: the gradient A^T dL/dD comes from the projection kernel).  g0 is
+    first scaled so that the part's mean dose is 1; projections and dose are stored in
+    `dtype` (FP32 master projections and moments); the Adam step is lr times the mean
+    positive projection.  Returns (VER after each iteration, cumulative device seconds),
+    stopping early once VER <= goal."""
+    L = U._nn()
+    n = P.proj_shape[0] * P.proj_shape[1] * P.proj_shape[2]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g = g0.float().clone()
+    D = P.forward_dose(g.to(dtype), dose_dtype=dtype)
+    g *= 1.0 / D.float()[f > 0.5].mean()
+    gb = g.to(dtype)
+    m = torch.zeros_like(g)
+    v = torch.zeros_like(g)
+    grad = torch.empty_like(g)
+    step = lr * float(g[g > 0].mean())
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    vers, times = [], []
+    for k in range(iters):
+        e0.record()
+        P.forward_dose(gb, out=D)
+        _, gD = P.threshold_loss(D, f, d_l, d_h, grad=True, grad_dtype=dtype)
+        P.adjoint(gD, out=grad)
+        V._check(L.vamrt_projected_adam(g.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), gb.data_ptr(), n,
+                                        step, 0.9, 0.999, 1e-12, k + 1, V._stream(None)), "vamrt_projected_adam")
+        vers.append(P.voxel_error_rate(D, f)[0])     # the stop check is part of the loop's time
+        e1.record()
+        e1.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        times.append(t)
+        if goal is not None and vers[-1] <= goal:
+            break
+    return np.array(vers), np.array(times)
+
+
 def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iters: int, device="cuda:0", kind="csg",
-            step=0.5, dtype=torch.float32, beta=4.0, mu=0.5):
-    """Per held-out target: the plain run's final VER, and for the warm start, for the
-    same continuation started from g0 = max(0, A^T f) (no network), and for the
-    over-relaxed object-space loop (model step beta, momentum mu, from m = f, storage
-    dtype): the
-    iterations and device time to reach 1.01 x the plain final VER."""
+            step=0.5, dtype=torch.float32, beta=4.0, mu=0.5, loss_iters=20, loss_lr=0.2):
+    """Per held-out target: the plain FP32 run's final VER, and the iterations and device
+    time to reach 1.01 x that VER for
+      - the warm start (network inference, its time included) continued by the
+        thresholded-loss Adam steps of loss_curve (BF16 storage), and the same continuation
+        from g0 = max(0, A^T f) (no network);
+      - the warm start continued by the projection-space iteration (relaxation `step`,
+        storage dtype), and the same from g0 = max(0, A^T f);
+      - the over-relaxed object-space loop (model step beta, momentum mu, from m = f,
+        storage dtype), no network."""
     rows = []
     for seed in seeds:
         f = torch.from_numpy(I.make_target(w, kind=kind, seed=int(seed))).to(device)
@@ -128,6 +176,8 @@ def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iter
         g_cold = P.adjoint(f, clamp_nonneg=True)
         v_cold, t_cold = ver_curve(P, f, cont_iters, g0=g_cold, step=step, dtype=dtype)
         v_rel, t_rel = ver_curve(P, f, plain_iters, dtype=dtype, beta=beta, goal=goal, mu=mu)
+        v_wl, t_wl = loss_curve(P, f, g_ws, loss_iters, lr=loss_lr, goal=goal)
+        v_cl, t_cl = loss_curve(P, f, g_cold, loss_iters, lr=loss_lr, goal=goal)
 
         def hit(v, t, extra=0.0):
             k = next((i for i, x in enumerate(v) if x <= goal), None)
@@ -136,7 +186,12 @@ def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iter
         k_ws, s_ws = hit(v_ws, t_ws, t_inf)
         k_cold, s_cold = hit(v_cold, t_cold)
         k_rel, s_rel = hit(v_rel, t_rel)
+        k_wl, s_wl = hit(v_wl, t_wl, t_inf)
+        k_cl, s_cl = hit(v_cl, t_cl)
         rows.append(dict(seed=int(seed), plain_final_ver=float(v_plain[-1]), plain_seconds=float(t_plain[-1]),
+                         warm_loss_ver=v_wl.tolist(), warm_loss_iters_to_target=k_wl,
+                         warm_loss_seconds_to_target=s_wl, cold_loss_ver=v_cl.tolist(),
+                         cold_loss_iters_to_target=k_cl, cold_loss_seconds_to_target=s_cl,
                          warm_ver=v_ws.tolist(), cold_ver=v_cold.tolist(), plain_ver=v_plain.tolist(),
                          warm_iters_to_target=k_ws, warm_seconds_to_target=s_ws, inference_seconds=t_inf,
                          cold_iters_to_target=k_cold, cold_seconds_to_target=s_cold,

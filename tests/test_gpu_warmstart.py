@@ -52,3 +52,8 @@ def test_warm_start_beats_the_method_without_it(trained):
     assert warm_first < 0.9 * cold_first
     assert warm_best < cold_best
     assert warm_best < plain_at6
+    # the adjoint-driven continuation (thresholded-loss Adam steps, BF16 storage) from the
+    # network's projections stays ahead of the same continuation from A^T f
+    warm_loss = np.mean([min(r["warm_loss_ver"]) for r in rows])
+    cold_loss = np.mean([min(r["cold_loss_ver"]) for r in rows])
+    assert warm_loss < cold_loss
