@@ -390,7 +390,7 @@ def warm_start_time_to_target(args):
     t2 = time.perf_counter()
     rows = WS.compare(P, net, w, range(100000, 100000 + args.ws_eval), plain_iters=w.osmo_iters,
                       cont_iters=12, step=0.5, dtype=torch.bfloat16, beta=args.ttt_beta, mu=args.ttt_mu,
-                      loss_iters=args.ws_loss_iters, loss_lr=args.ws_loss_lr)
+                      loss_iters=args.ws_loss_iters, loss_lr=args.ws_loss_lr, loss_dl=args.ws_loss_dl)
     network = network_throughput(net, pairs[0][1], pairs[0][2], 1.0)
 
     def ratio_of(x, r):
@@ -422,7 +422,7 @@ def warm_start_time_to_target(args):
             "train_pairs": len(pairs), "pair_iterations": w.osmo_iters, "epochs": args.ws_epochs,
             "data_generation_seconds": t1 - t0, "training_seconds": t2 - t1, "final_train_loss": losses[-1],
             "continuation": f"thresholded-loss Adam steps (adjoint-driven, step {args.ws_loss_lr:g} x mean "
-                            "projection, d_l 0.9, d_h 1.0), BF16-stored projections and dose",
+                            f"projection, d_l {args.ws_loss_dl:g}, d_h 1), BF16-stored projections and dose",
             "warm_start": summary("time_ratio"), "no_network_same_continuation": summary("no_network_loss_time_ratio"),
             "warm_start_projection_space": summary("warm_projection_space_time_ratio"),
             "relaxed_no_network": summary("relaxed_time_ratio"),
@@ -675,8 +675,10 @@ def main():
     ap.add_argument("--ws-train", type=int, default=64, help="warm-start training targets (0 = skip)")
     ap.add_argument("--ws-epochs", type=int, default=8)
     ap.add_argument("--ws-eval", type=int, default=4, help="held-out targets for the warm-start comparison")
-    ap.add_argument("--ws-loss-lr", type=float, default=0.2,
+    ap.add_argument("--ws-loss-lr", type=float, default=0.8,
                     help="Adam step of the warm start's thresholded-loss continuation (x mean projection)")
+    ap.add_argument("--ws-loss-dl", type=float, default=0.8,
+                    help="lower dose threshold d_l of the warm start's thresholded-loss continuation (d_h = 1)")
     ap.add_argument("--ws-loss-iters", type=int, default=20,
                     help="iterations of the warm start's thresholded-loss continuation")
     ap.add_argument("--network-only", action="store_true",

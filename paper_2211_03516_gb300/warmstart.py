@@ -105,7 +105,7 @@ def ver_curve(P: V.Projector, f: torch.Tensor, iters: int, g0=None, dtype=torch.
     return np.array(vers), np.array(times)
 
 
-def loss_curve(P: V.Projector, f: torch.Tensor, g0: torch.Tensor, iters: int, lr: float = 0.2, d_l: float = 0.9,
+def loss_curve(P: V.Projector, f: torch.Tensor, g0: torch.Tensor, iters: int, lr: float = 0.8, d_l: float = 0.8,
                d_h: float = 1.0, dtype=torch.bfloat16, goal=None):
     """Adjoint-driven continuation from g0: projected Adam steps on the thresholded dose
     loss L(D), D = A g, L = mean_P relu(d_h - D)^2 + mean_Q relu(D - d_l)^2 (the
@@ -148,7 +148,7 @@ def loss_curve(P: V.Projector, f: torch.Tensor, g0: torch.Tensor, iters: int, lr
 
 
 def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iters: int, device="cuda:0", kind="csg",
-            step=0.5, dtype=torch.float32, beta=4.0, mu=0.5, loss_iters=20, loss_lr=0.2):
+            step=0.5, dtype=torch.float32, beta=4.0, mu=0.5, loss_iters=20, loss_lr=0.8, loss_dl=0.8):
     """Per held-out target: the plain FP32 run's final VER, and the iterations and device
     time to reach 1.01 x that VER for
       - the warm start (network inference, its time included) continued by the
@@ -176,8 +176,8 @@ def compare(P: V.Projector, net: U.UNet3D, w, seeds, plain_iters: int, cont_iter
         g_cold = P.adjoint(f, clamp_nonneg=True)
         v_cold, t_cold = ver_curve(P, f, cont_iters, g0=g_cold, step=step, dtype=dtype)
         v_rel, t_rel = ver_curve(P, f, plain_iters, dtype=dtype, beta=beta, goal=goal, mu=mu)
-        v_wl, t_wl = loss_curve(P, f, g_ws, loss_iters, lr=loss_lr, goal=goal)
-        v_cl, t_cl = loss_curve(P, f, g_cold, loss_iters, lr=loss_lr, goal=goal)
+        v_wl, t_wl = loss_curve(P, f, g_ws, loss_iters, lr=loss_lr, d_l=loss_dl, goal=goal)
+        v_cl, t_cl = loss_curve(P, f, g_cold, loss_iters, lr=loss_lr, d_l=loss_dl, goal=goal)
 
         def hit(v, t, extra=0.0):
             k = next((i for i, x in enumerate(v) if x <= goal), None)
