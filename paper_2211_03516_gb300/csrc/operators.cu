@@ -243,9 +243,35 @@ struct BoxAddr {
     __device__ __forceinline__ int operator()(const Cell &c) const { return c.iz * sxy + c.iy * sx + c.ix; }
 };
 
-// i / d for 0 <= i < 2^22 and 1 <= d < 2^10 through an FP32 reciprocal: (i + 1/2) / d
-// lies at least 1/(2d) from an integer, well beyond the product's rounding error.
+// i / d for 0 <= i < 2^22 - 1 and d >= 1 through an FP32 reciprocal: (i + 1/2) / d lies at
+// least 1/(2d) from an integer, while the reciprocal and the product together are off by
+// less than (i + 1/2) / d * 2^-23 < 1/(2d).
 __device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
+
+// A box is visited as slots (pixel row yy, 16-byte group x4) of a z plane, ey * ex4 of
+// them, each slot walked down the planes by a pointer increment.  Thread t takes the items
+// t, t + kThreads, ...: when a plane has fewer slots than the block has threads, the
+// planes are dealt out in `phases` interleaved sets, one item per (set, slot).
+struct SlotWalk {
+    int slots, phases, items;
+    float inv_slots, inv_ex4;
+    __device__ __forceinline__ SlotWalk(int ex4, int ey)
+    {
+        slots = ex4 * ey;
+        phases = max(1, kThreads / slots);
+        items = phases * slots;
+        inv_slots = 1.0f / (float)slots;
+        inv_ex4 = 1.0f / (float)ex4;
+    }
+    // item -> first plane zp, row yy, group x4
+    __device__ __forceinline__ void at(int it, int ex4, int &zp, int &yy, int &x4) const
+    {
+        zp = fdiv(it, inv_slots);
+        const int s = it - zp * slots;
+        yy = fdiv(s, inv_ex4);
+        x4 = s - yy * ex4;
+    }
+};
 
 // Packed FP32 pairs (sm_100 family): one instruction performs two independent
 // round-to-nearest operations, so the results are bit-identical to the scalar forms while
@@ -491,7 +517,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     tiled_kernel(const OpParams P, const VT *__restrict__ vol, PT *__restrict__ proj, float *__restrict__ acc,
                  uint32_t flags)
 {
-    extern __shared__ float box[];
+    extern __shared__ __align__(16) float box[];
     __shared__ int s_box[3][6];   // per chunk (rotating): min x,y,z and max x,y,z of the footprint
     __shared__ int s_rng[3][3];   // per aperture sample (rotating): first and last chunk, max |ray weight| bits
 
@@ -506,11 +532,9 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     const int k = blockIdx.y;
     const int v = blockIdx.z * kTileV + threadIdx.x;
     const bool valid = u < P.nu && v < P.nv;
-    const double2 cs = P.cs[k];
-    const int64_t pix_index = ((int64_t)k * P.nv + v) * P.nu + u;
 
     float g = 0.f;
-    if (FWD && valid) g = to_f(proj[pix_index]);
+    if (FWD && valid) g = to_f(proj[((int64_t)k * P.nv + v) * P.nu + u]);
     if (tid < 18) s_box[tid / 6][tid % 6] = (tid % 6 < 3) ? INT_MAX : INT_MIN;
     if (tid < 9) s_rng[tid / 3][tid % 3] = (tid % 3 == 0) ? INT_MAX : (tid % 3 == 1) ? INT_MIN : 0;
     __syncthreads();
@@ -522,7 +546,8 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
         const int ra = a % 3;
         Ray R;
         bool active = valid && (!FWD || g != 0.f);
-        if (active) active = ray_begin(P, ((int64_t)a * P.nv + v) * P.nu + u, cs, R, !FWD && (flags & VAMRT_UNATTENUATED));
+        if (active)
+            active = ray_begin(P, ((int64_t)a * P.nv + v) * P.nu + u, P.cs[k], R, !FWD && (flags & VAMRT_UNATTENUATED));
         int cf = INT_MAX, cl = INT_MIN;
         if (active) {
             cf = chunk_of(P, R, R.jlo);
@@ -598,8 +623,6 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
             const int ey = hy + 1 - by0, ez = hz + 1 - bz0;
             const int sx = ex + 1, sxy = sx * (ey | 1);       // odd row and plane strides
             const int ex4 = ex >> 2;
-            const int n4 = ex4 * ey * ez;
-            const float inv_ex4 = 1.0f / (float)ex4, inv_ey = 1.0f / (float)ey;
             // the box path needs the box inside the padded grid (the backward walk's truncated
             // step can carry a sample a hair past a grid face: such ranges run on global
             // memory with exact positions) and extents a Q9.23 offset can hold
@@ -612,29 +635,29 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
                 continue;
             }
             if (fits && in_grid) {
+                const SlotWalk sw(ex4, ey);
                 if (!FWD) {
-                    // thread -> (row r0, 16-byte group x4) once; rows advance by `per` (ex4 <= 64
-                    // here: extents are below 256)
-                    const int rows = ey * ez;
-                    const int per = kThreads / ex4;
-                    const int r0 = fdiv(tid, inv_ex4), x4 = tid - r0 * ex4;
-                    if (r0 < per) {
-                        int zz = fdiv(r0, inv_ey), yy = r0 - zz * ey;
-                        const int dq = fdiv(per, inv_ey), dr = per - dq * ey;
-                        const VT *src = vol + (int64_t)bz0 * pxy + (int64_t)by0 * P.px + bx0 + 4 * x4;
-                        // unrolled so that several rows' loads are in flight before their stores
-#pragma unroll 4
-                        for (int r = r0; r < rows; r += per) {
-                            const float4 q = ld4(src + (int64_t)zz * pxy + (int64_t)yy * P.px);
-                            float *b = box + zz * sxy + yy * sx + 4 * x4;
+                    const int64_t gstep = (int64_t)sw.phases * pxy;
+                    const int bstep = sw.phases * sxy;
+                    for (int it = tid; it < sw.items; it += kThreads) {
+                        int zp, yy, x4;
+                        sw.at(it, ex4, zp, yy, x4);
+                        const VT *src = vol + ((int64_t)(bz0 + zp) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
+                        float *b = box + zp * sxy + yy * sx + 4 * x4;
+                        // unrolled so that several planes' loads are in flight before their stores
+#pragma unroll 2
+                        for (int zz = zp; zz < ez; zz += sw.phases) {
+                            const float4 q = ld4(src);
                             b[0] = q.x; b[1] = q.y; b[2] = q.z; b[3] = q.w;
-                            zz += dq;
-                            yy += dr;
-                            if (yy >= ey) { yy -= ey; ++zz; }
+                            src += gstep;
+                            b += bstep;
                         }
                     }
                 } else {
-                    for (int i = tid; i < sxy * ez; i += kThreads) box[i] = 0.f;
+                    // the box base is 16-byte aligned and kBoxFloats a multiple of 4
+                    float4 *b4 = reinterpret_cast<float4 *>(box);
+                    const int n = (sxy * ez + 3) >> 2;
+                    for (int i = tid; i < n; i += kThreads) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 __syncthreads();
                 if (jl < jh) {
@@ -649,14 +672,20 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
                     __syncthreads();
                     const float inv = 1.0f / scale;
                     const int *ib = reinterpret_cast<const int *>(box);
-                    for (int i = tid; i < n4; i += kThreads) {
-                        const int t = fdiv(i, inv_ex4), xq = i - t * ex4;
-                        const int zz = fdiv(t, inv_ey), yy = t - zz * ey;
-                        const int *b = ib + zz * sxy + yy * sx + 4 * xq;
-                        const int b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
-                        if ((b0 | b1 | b2 | b3) != 0)
-                            red_v4(acc + (int64_t)(bz0 + zz) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * xq,
-                                   make_float4((float)b0 * inv, (float)b1 * inv, (float)b2 * inv, (float)b3 * inv));
+                    const int64_t gstep = (int64_t)sw.phases * pxy;
+                    const int bstep = sw.phases * sxy;
+                    for (int it = tid; it < sw.items; it += kThreads) {
+                        int zp, yy, x4;
+                        sw.at(it, ex4, zp, yy, x4);
+                        float *g = acc + ((int64_t)(bz0 + zp) * pxy + (int64_t)(by0 + yy) * P.px + bx0 + 4 * x4);
+                        const int *b = ib + zp * sxy + yy * sx + 4 * x4;
+                        for (int zz = zp; zz < ez; zz += sw.phases) {
+                            const int b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
+                            if ((b0 | b1 | b2 | b3) != 0)
+                                red_v4(g, make_float4((float)b0 * inv, (float)b1 * inv, (float)b2 * inv, (float)b3 * inv));
+                            g += gstep;
+                            b += bstep;
+                        }
                     }
                 }
             } else if (jl < jh) {
@@ -670,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
         if (!FWD && active) pix = fmaf(R.w, ray_acc, pix);
     }
     if (!FWD && valid) {
-        PT *out = proj + pix_index;
+        PT *out = proj + (((int64_t)k * P.nv + v) * P.nu + u);
         if (flags & VAMRT_ACCUMULATE) pix += to_f(*out);
         if (flags & VAMRT_CLAMP_NONNEG) pix = fmaxf(pix, 0.f);
         st_val(out, pix);
