@@ -448,8 +448,15 @@ __device__ __forceinline__ float walk_gather_box(const Ray &R, const Anchor &an,
 
 // Shared-memory box: fixed-point integer accumulation.  Shared-memory integer atomics
 // are native, FP32 ones are not.  `scale` maps the largest ray weight of the block to
-// well under 2^22, so every share rounds exactly through the 1.5 * 2^23 trick, and the
-// bound on shares per voxel and chunk keeps every box sum below 2^31.
+// well under 2^22, and the bound on shares per voxel and chunk keeps every box sum below
+// 2^31.  A share x becomes the integer round(x) in one of two ways:
+//   - any sign: x + 1.5 * 2^23 holds round(x) + 0x4B400000 in its bit pattern (|x| < 2^22),
+//     the offset subtracted before the atomic;
+//   - x >= 0 (warps whose rays all carry non-negative weights, as the optimiser's clamped
+//     projections do): x * 2^-149 is the subnormal whose bit pattern is round(x) itself
+//     (x < 2^23), so no subtraction is needed.
+// Both round to nearest, ties to even: the box sums are identical.
+template <bool kNonNeg>
 __device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an, int jl, int jh, float wray,
                                                  float scale, int ox, int oy, int oz, int *box, int sx, int sxy)
 {
@@ -460,13 +467,13 @@ __device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an,
     // weight of sample jh-1, then one division by the per-sample factor per step down
     float w = wray * scale * exp2f(R.att * ((float)(jh - 1) + 0.5f));
     const float inv_ratio = exp2f(-R.att);
-    const f32x2 magic = pk2(12582912.0f, 12582912.0f);
+    const f32x2 conv = kNonNeg ? pk2(0x1p-149f, 0x1p-149f) : pk2(12582912.0f, 12582912.0f);
+    const int bias = kNonNeg ? 0 : 0x4B400000;
 #pragma unroll 2
     for (int j = jh - 1; j >= jl; --j) {
         const float fx = frac23(qx), fy = frac23(qy), fz = frac23(qz);
         int *p = box + ((qz >> 23) * sxy + (qy >> 23) * sx + (qx >> 23));
-        // the eight shares in pairs (z = 0, z = 1), converted to fixed point by the same
-        // 1.5 * 2^23 addition
+        // the eight shares in pairs (z = 0, z = 1), then to fixed point
         const float wz1 = w * fz, wz0 = w - wz1;
         const f32x2 fx2 = pk2(fx, fx);
         const f32x2 z = pk2(wz0, wz1);
@@ -474,18 +481,25 @@ __device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an,
         const f32x2 w0 = sub2(z, w1);                      // (w00, w10)
         const f32x2 s1a = mul2(w0, fx2), s1b = mul2(w1, fx2);   // (s100, s101), (s110, s111)
         int i000, i001, i100, i101, i010, i011, i110, i111;
-        upk2i(add2(sub2(w0, s1a), magic), i000, i001);
-        upk2i(add2(s1a, magic), i100, i101);
-        upk2i(add2(sub2(w1, s1b), magic), i010, i011);
-        upk2i(add2(s1b, magic), i110, i111);
-        atomicAdd(p, i000 - 0x4B400000);
-        atomicAdd(p + 1, i100 - 0x4B400000);
-        atomicAdd(p + sx, i010 - 0x4B400000);
-        atomicAdd(p + sx + 1, i110 - 0x4B400000);
-        atomicAdd(p + sxy, i001 - 0x4B400000);
-        atomicAdd(p + sxy + 1, i101 - 0x4B400000);
-        atomicAdd(p + sxy + sx, i011 - 0x4B400000);
-        atomicAdd(p + sxy + sx + 1, i111 - 0x4B400000);
+        if (kNonNeg) {
+            upk2i(mul2(sub2(w0, s1a), conv), i000, i001);
+            upk2i(mul2(s1a, conv), i100, i101);
+            upk2i(mul2(sub2(w1, s1b), conv), i010, i011);
+            upk2i(mul2(s1b, conv), i110, i111);
+        } else {
+            upk2i(add2(sub2(w0, s1a), conv), i000, i001);
+            upk2i(add2(s1a, conv), i100, i101);
+            upk2i(add2(sub2(w1, s1b), conv), i010, i011);
+            upk2i(add2(s1b, conv), i110, i111);
+        }
+        atomicAdd(p, i000 - bias);
+        atomicAdd(p + 1, i100 - bias);
+        atomicAdd(p + sx, i010 - bias);
+        atomicAdd(p + sx + 1, i110 - bias);
+        atomicAdd(p + sxy, i001 - bias);
+        atomicAdd(p + sxy + 1, i101 - bias);
+        atomicAdd(p + sxy + sx, i011 - bias);
+        atomicAdd(p + sxy + sx + 1, i111 - bias);
         w *= inv_ratio;
         qx -= dx;
         qy -= dy;
@@ -555,6 +569,8 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
             if (cl < cf) cl = cf;
         }
         const float wray = (FWD && active) ? g * R.w : 0.f;
+        // the warp's shares are all non-negative: the subnormal conversion applies
+        const bool nonneg = FWD && __all_sync(kFull, !(wray < 0.f));
         cf = __reduce_min_sync(kFull, cf);
         cl = __reduce_max_sync(kFull, cl);
         // |weights| >= 0 order like their bit patterns
@@ -664,9 +680,12 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
                     if (!FWD)
                         ray_acc += exp2f(R.att * ((float)jl + 0.5f)) *
                                    walk_gather_box(R, an, jl, jh, bx0, by0, bz0, box, sx, sxy);
+                    else if (nonneg)
+                        walk_scatter_box<true>(R, an, jl, jh, wray, scale, bx0, by0, bz0,
+                                               reinterpret_cast<int *>(box), sx, sxy);
                     else
-                        walk_scatter_box(R, an, jl, jh, wray, scale, bx0, by0, bz0, reinterpret_cast<int *>(box),
-                                         sx, sxy);
+                        walk_scatter_box<false>(R, an, jl, jh, wray, scale, bx0, by0, bz0,
+                                                reinterpret_cast<int *>(box), sx, sxy);
                 }
                 if (FWD) {
                     __syncthreads();

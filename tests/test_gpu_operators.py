@@ -116,10 +116,16 @@ def test_adjoint_and_dose_parity(vamrt, w):
     y_v = P.adjoint(gpu(V))
     g = I.random_projections(w, seed=12)
     d_g = P.forward_dose(gpu(g))
+    # signed projections in the upper half of the rows only: one launch holds warps whose
+    # weights are all non-negative and warps of both signs (two fixed-point conversions)
+    gs = g.copy()
+    gs[:, : w.nv // 2, :] -= 0.5
+    d_s = P.forward_dose(gpu(gs))
     torch.cuda.synchronize()
     assert rel_l2(y_t.cpu().numpy(), O.adjoint(w, f, pupil)) <= FP32_TOL
     assert rel_l2(y_v.cpu().numpy(), O.adjoint(w, V, pupil)) <= FP32_TOL
     assert rel_l2(d_g.cpu().numpy(), O.forward(w, g, pupil)) <= FP32_TOL
+    assert rel_l2(d_s.cpu().numpy(), O.forward(w, gs, pupil)) <= FP32_TOL
 
 
 def test_tiny_forward_of_projection_matches_oracle(vamrt):
