@@ -237,12 +237,6 @@ __device__ __forceinline__ Cell cell_of(long long qx, long long qy, long long qz
     return c;
 }
 
-// Addressing of a sample's corner (0,0,0) in the global padded volume.
-struct BoxAddr {
-    int sx, sxy;
-    __device__ __forceinline__ int operator()(const Cell &c) const { return c.iz * sxy + c.iy * sx + c.ix; }
-};
-
 // i / d for 0 <= i < 2^22 - 1 and d >= 1 through an FP32 reciprocal: (i + 1/2) / d lies at
 // least 1/(2d) from an integer, while the reciprocal and the product together are off by
 // less than (i + 1/2) / d * 2^-23 < 1/(2d).
