@@ -30,8 +30,8 @@ constexpr int kBlocksPerSm = 3;
 // rows are padded to a multiple of 4 floats), so voxel (i,j,k) of the caller's grid
 // sits at (i+1, j+1, k+1).
 struct OpParams {
-    const double4 *A;     // (e_x, e_y, e_z, delta) in voxels, theta = 0 frame, relative to the axis
-    const double4 *B;     // (d_x, d_y, d_z, T1 T2 delta_mm / M)
+    const double4_32a *A; // (e_x, e_y, e_z, delta) in voxels, theta = 0 frame, relative to the axis
+    const double4_32a *B; // (d_x, d_y, d_z, T1 T2 delta_mm / M)
     const int2 *J;        // [j_lo, j_hi) samples whose footprint reaches the grid
     const double2 *cs;    // (cos theta_k, sin theta_k), FP64
     int nu, nv, M, n_angles;
@@ -72,8 +72,8 @@ struct vamrt_projector {
     int64_t rays_in_resin;
     uint64_t samples_per_angle;
     uint64_t device_bytes;
-    double4 *tabA;             // FP64: a large grid's positions need more than FP32's 24 bits
-    double4 *tabB;
+    double4_32a *tabA;         // FP64: a large grid's positions need more than FP32's 24 bits
+    double4_32a *tabB;
     int2 *tabJ;
     double2 *cs;
     float *scratch;            // padded FP32 volume, pad_elems floats
@@ -93,7 +93,7 @@ void count_launches(unsigned n);
 void set_error(const char *msg);
 
 // raytable.cu
-cudaError_t launch_raytable(const TraceParams &T, double4 *A, double4 *B, int2 *J,
+cudaError_t launch_raytable(const TraceParams &T, double4_32a *A, double4_32a *B, int2 *J,
                             unsigned long long *counters, cudaStream_t s);
 
 // static_dose.cu: device address of the allocation-free dose entry point's static

@@ -143,7 +143,7 @@ __device__ __forceinline__ bool ray_begin(const OpParams &P, int64_t r, double2 
 {
     const int2 J = P.J[r];
     if (J.x >= J.y) return false;
-    const double4 A = P.A[r], B = P.B[r];
+    const double4_32a A = P.A[r], B = P.B[r];
     const double c = cs.x, s = cs.y;
     const double ex = A.x, ey = A.y, dl = A.w;
     const double stx = (c * B.x - s * B.y) * dl;

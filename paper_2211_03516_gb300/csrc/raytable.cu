@@ -192,7 +192,7 @@ __device__ void stop_point(const TraceParams &P, int u, int v, int a, double &xi
     }
 }
 
-__global__ void raytable_kernel(TraceParams P, double4 *__restrict__ A, double4 *__restrict__ B,
+__global__ void raytable_kernel(TraceParams P, double4_32a *__restrict__ A, double4_32a *__restrict__ B,
                                 int2 *__restrict__ J, unsigned long long *__restrict__ counters)
 {
     const int64_t n_rays = (int64_t)P.nu * P.nv * P.M;
@@ -202,8 +202,8 @@ __global__ void raytable_kernel(TraceParams P, double4 *__restrict__ A, double4 
     const int v = (int)((r / P.nu) % P.nv);
     const int a = (int)(r / ((int64_t)P.nu * P.nv));
 
-    A[r] = make_double4(0.0, 0.0, 0.0, 0.0);
-    B[r] = make_double4(0.0, 0.0, 0.0, 0.0);
+    A[r] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    B[r] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     J[r] = make_int2(0, 0);
 
     // image point of the pixel in the best-focus plane y = 0
@@ -261,8 +261,8 @@ __global__ void raytable_kernel(TraceParams P, double4 *__restrict__ A, double4 
     if (jhi <= jlo) { jlo = 0; jhi = 0; }
 
     const double inv_h = 1.0 / P.h;
-    A[r] = make_double4(e.x * inv_h, e.y * inv_h, e.z * inv_h, delta * inv_h);
-    B[r] = make_double4(dr.x, dr.y, dr.z, T1 * T2 * delta / P.M);
+    A[r] = make_double4_32a(e.x * inv_h, e.y * inv_h, e.z * inv_h, delta * inv_h);
+    B[r] = make_double4_32a(dr.x, dr.y, dr.z, T1 * T2 * delta / P.M);
     J[r] = make_int2(jlo, jhi);
     atomicAdd(&counters[0], 1ull);
     atomicAdd(&counters[1], (unsigned long long)(jhi - jlo));
@@ -270,7 +270,7 @@ __global__ void raytable_kernel(TraceParams P, double4 *__restrict__ A, double4 
 
 }  // namespace
 
-cudaError_t launch_raytable(const TraceParams &T, double4 *A, double4 *B, int2 *J,
+cudaError_t launch_raytable(const TraceParams &T, double4_32a *A, double4_32a *B, int2 *J,
                             unsigned long long *counters, cudaStream_t s)
 {
     const int64_t n = (int64_t)T.nu * T.nv * T.M;

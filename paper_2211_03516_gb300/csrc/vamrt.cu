@@ -225,8 +225,8 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     const int px = ((g.nx + 2 + 3) / 4) * 4;   // rows padded to 16-byte groups
     p->pad_elems = (int64_t)px * (g.ny + 2) * (g.nz + 2);
 
-    CK(cudaMalloc(&p->tabA, sizeof(double4) * p->n_rays), "cudaMalloc(ray table)");
-    CK(cudaMalloc(&p->tabB, sizeof(double4) * p->n_rays), "cudaMalloc(ray table)");
+    CK(cudaMalloc(&p->tabA, sizeof(double4_32a) * p->n_rays), "cudaMalloc(ray table)");
+    CK(cudaMalloc(&p->tabB, sizeof(double4_32a) * p->n_rays), "cudaMalloc(ray table)");
     CK(cudaMalloc(&p->tabJ, sizeof(int2) * p->n_rays), "cudaMalloc(ray table)");
     CK(cudaMalloc(&p->cs, sizeof(double2) * g.n_angles), "cudaMalloc(angles)");
     CK(cudaMalloc(&p->scratch, sizeof(float) * p->pad_elems), "cudaMalloc(scratch volume)");
@@ -234,7 +234,7 @@ vamrt_status vamrt_make_projector(const vamrt_geometry *geom, void *stream, vamr
     CK(cudaMalloc(&p->hist, sizeof(double) * vamrt::kMaxHistory), "cudaMalloc(history)");
     CK(cudaMalloc(&p->dmax, sizeof(float) * 4), "cudaMalloc(dmax)");
     CK(cudaMallocHost(&p->host_err, 4 * sizeof(double)), "cudaMallocHost");   // E and the 3 VER counts
-    p->device_bytes = (sizeof(double4) * 2 + sizeof(int2)) * (uint64_t)p->n_rays + sizeof(double2) * g.n_angles +
+    p->device_bytes = (sizeof(double4_32a) * 2 + sizeof(int2)) * (uint64_t)p->n_rays + sizeof(double2) * g.n_angles +
                       sizeof(float) * (uint64_t)p->pad_elems;
 
     // angle table, FP64 on the host then rounded
@@ -576,17 +576,17 @@ vamrt_status vamrt_copy_ray_table(const vamrt_projector *p, float *a4, float *b4
     if (!p) return fail(VAMRT_EINVAL, "NULL projector");
     CK(cudaDeviceSynchronize(), "sync");
     // the table is FP64 on the device; this call hands out its FP32 rounding
-    const double4 *src[2] = {p->tabA, p->tabB};
+    const double4_32a *src[2] = {p->tabA, p->tabB};
     float *dst[2] = {a4, b4};
     for (int t = 0; t < 2; ++t) {
         if (!dst[t]) continue;
-        std::vector<double4> h;
+        std::vector<double4_32a> h;
         try {
             h.resize((size_t)p->n_rays);
         } catch (...) {
             return fail(VAMRT_ENOMEM, "host allocation failed");
         }
-        CK(cudaMemcpy(h.data(), src[t], sizeof(double4) * p->n_rays, cudaMemcpyDeviceToHost), "copy");
+        CK(cudaMemcpy(h.data(), src[t], sizeof(double4_32a) * p->n_rays, cudaMemcpyDeviceToHost), "copy");
         for (int64_t r = 0; r < p->n_rays; ++r) {
             dst[t][4 * r] = (float)h[r].x;
             dst[t][4 * r + 1] = (float)h[r].y;
