@@ -44,7 +44,9 @@ typedef enum {
 
 typedef enum {
     VAMRT_F32 = 0,             /* float */
-    VAMRT_BF16 = 1             /* bfloat16 storage; all sums are FP32 */
+    VAMRT_BF16 = 1,            /* bfloat16 storage; all sums are FP32 */
+    VAMRT_F16 = 2              /* IEEE binary16 storage; all sums are FP32.  Values beyond 65504
+                                  in magnitude round to infinity: scale inputs to its range */
 } vamrt_dtype;
 
 /* Operator flags */

@@ -5,6 +5,7 @@
 // (population sigma over all pixels of all angles), computed in FP64.  The dequantised
 // projections code * c / 255 can be written for the final dose simulation.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "internal.cuh"
@@ -16,6 +17,7 @@ constexpr int kEx = 256;
 
 __device__ __forceinline__ double ldg_d(const float *p, int64_t i) { return (double)p[i]; }
 __device__ __forceinline__ double ldg_d(const __nv_bfloat16 *p, int64_t i) { return (double)__bfloat162float(p[i]); }
+__device__ __forceinline__ double ldg_d(const __half *p, int64_t i) { return (double)__half2float(p[i]); }
 
 template <typename T>
 __global__ void moments_kernel(const T *__restrict__ g, int64_t n, double *__restrict__ partials)
@@ -96,7 +98,8 @@ cudaError_t launch_export_u8(const vamrt_projector *p, const void *proj, vamrt_d
 {
     const int64_t n = (int64_t)p->g.n_angles * p->g.nv * p->g.nu;
     if (dt == VAMRT_F32) return launch_export_t(p, (const float *)proj, n, codes, dequant, clip, s);
-    return launch_export_t(p, (const __nv_bfloat16 *)proj, n, codes, dequant, clip, s);
+    if (dt == VAMRT_BF16) return launch_export_t(p, (const __nv_bfloat16 *)proj, n, codes, dequant, clip, s);
+    return launch_export_t(p, (const __half *)proj, n, codes, dequant, clip, s);
 }
 
 }  // namespace vamrt

@@ -6,6 +6,7 @@
 // Three launches: per-block FP64 partial sums (counts and squared violations), one block
 // that adds them in a fixed order (deterministic L), and the elementwise gradient.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 
@@ -18,6 +19,8 @@ __device__ __forceinline__ float ldv(const float *p) { return *p; }
 __device__ __forceinline__ float ldv(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void stv(float *p, float x) { *p = x; }
 __device__ __forceinline__ void stv(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+__device__ __forceinline__ float ldv(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void stv(__half *p, float x) { *p = __float2half_rn(x); }
 
 __device__ double block_sum_d(double x, double *sh)
 {
@@ -102,9 +105,11 @@ cudaError_t launch_loss_t(const vamrt_projector *p, const DT *dose, const float 
     if (grad) {
         if (grad_dt == VAMRT_F32)
             loss_grad_kernel<DT, float><<<g, kLossThreads, 0, s>>>(dose, target, n, d_l, d_h, loss3, (float *)grad);
-        else
+        else if (grad_dt == VAMRT_BF16)
             loss_grad_kernel<DT, __nv_bfloat16><<<g, kLossThreads, 0, s>>>(dose, target, n, d_l, d_h, loss3,
                                                                            (__nv_bfloat16 *)grad);
+        else
+            loss_grad_kernel<DT, __half><<<g, kLossThreads, 0, s>>>(dose, target, n, d_l, d_h, loss3, (__half *)grad);
         count_launches(1);
     }
     count_launches(2);
@@ -119,7 +124,9 @@ cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, va
 {
     if (dose_dt == VAMRT_F32)
         return launch_loss_t(p, (const float *)dose, target, d_l, d_h, loss3, grad, grad_dt, s);
-    return launch_loss_t(p, (const __nv_bfloat16 *)dose, target, d_l, d_h, loss3, grad, grad_dt, s);
+    if (dose_dt == VAMRT_BF16)
+        return launch_loss_t(p, (const __nv_bfloat16 *)dose, target, d_l, d_h, loss3, grad, grad_dt, s);
+    return launch_loss_t(p, (const __half *)dose, target, d_l, d_h, loss3, grad, grad_dt, s);
 }
 
 }  // namespace vamrt

@@ -40,7 +40,10 @@
 // padding outside the grid, Sec. 2.2's weights then need no bounds tests).  Each ray's
 // sample range is trimmed once so that every sample's cell lies inside the padded grid.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <limits.h>
+
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -54,6 +57,8 @@ __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ void st_val(float *p, float x) { *p = x; }
 __device__ __forceinline__ void st_val(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ void st_val(__half *p, float x) { *p = __float2half_rn(x); }
 
 __device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
@@ -65,11 +70,19 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p)
     const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
     return make_float4(bf16_lo(w.x), bf16_hi(w.x), bf16_lo(w.y), bf16_hi(w.y));
 }
+__device__ __forceinline__ float4 ld4(const __half *p)
+{
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&w.x));
+    const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&w.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
 __device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld1(const __nv_bfloat16 *p)
 {
     return __uint_as_float(((unsigned)__ldg(reinterpret_cast<const unsigned short *>(p))) << 16);
 }
+__device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldg(p)); }
 
 __device__ __forceinline__ void red_v4(float *p, float4 v)
 {
@@ -748,57 +761,36 @@ cudaError_t launch_tiled(const OpParams &P, const VT *vol, PT *proj, float *acc,
 
 }  // namespace
 
+// Storage types: FP32, BF16 or FP16 (every sum is FP32 whatever the storage).
+template <typename F>
+cudaError_t with_storage(vamrt_dtype dt, void *ptr, F &&f)
+{
+    if (dt == VAMRT_F32) return f((float *)ptr);
+    if (dt == VAMRT_BF16) return f((__nv_bfloat16 *)ptr);
+    return f((__half *)ptr);
+}
+
 cudaError_t launch_pad(const vamrt_projector *p, const void *vol, vamrt_dtype dt, cudaStream_t s)
 {
     const OpParams &P = p->op;
     const unsigned grid = grid_for(p, p->pad_elems, 256);
-    if (dt == VAMRT_F32)
-        pad_kernel<float><<<grid, 256, 0, s>>>((const float *)vol, p->scratch, P.nx, P.ny, P.nz, P.px, P.py,
-                                               p->pad_elems);
-    else
-        pad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)p->scratch,
-                                                       P.nx, P.ny, P.nz, P.px, P.py, p->pad_elems);
-    count_launches(1);
-    return cudaGetLastError();
+    return with_storage(dt, const_cast<void *>(vol), [&](auto *v) {
+        using VT = std::remove_pointer_t<decltype(v)>;
+        pad_kernel<VT><<<grid, 256, 0, s>>>(v, (VT *)p->scratch, P.nx, P.ny, P.nz, P.px, P.py, p->pad_elems);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_adjoint(const vamrt_projector *p, vamrt_dtype vol_dt, void *proj, vamrt_dtype proj_dt,
                            uint32_t flags, cudaStream_t s)
 {
     const OpParams &P = p->op;
-    if (vol_dt == VAMRT_F32) {
-        const float *vol = p->scratch;
-        if (proj_dt == VAMRT_F32) return launch_tiled<false>(P, vol, (float *)proj, nullptr, flags, s);
-        return launch_tiled<false>(P, vol, (__nv_bfloat16 *)proj, nullptr, flags, s);
-    }
-    const __nv_bfloat16 *vol = (const __nv_bfloat16 *)p->scratch;
-    if (proj_dt == VAMRT_F32) return launch_tiled<false>(P, vol, (float *)proj, nullptr, flags, s);
-    return launch_tiled<false>(P, vol, (__nv_bfloat16 *)proj, nullptr, flags, s);
-}
-
-cudaError_t launch_forward(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, cudaStream_t s)
-{
-    cudaError_t e = cudaMemsetAsync(p->scratch, 0, sizeof(float) * p->pad_elems, s);
-    if (e != cudaSuccess) return e;
-    const OpParams &P = p->op;
-    const float *none = nullptr;
-    if (proj_dt == VAMRT_F32)
-        return launch_tiled<true>(P, none, (float *)proj, p->scratch, 0u, s);
-    return launch_tiled<true>(P, none, (__nv_bfloat16 *)proj, p->scratch, 0u, s);
-}
-
-cudaError_t launch_unpad(const vamrt_projector *p, void *dose, vamrt_dtype dt, uint32_t flags, cudaStream_t s)
-{
-    const OpParams &P = p->op;
-    const unsigned grid = grid_for(p, (int64_t)P.nx * P.ny * P.nz, 256);
-    const int accumulate = (flags & VAMRT_ACCUMULATE) ? 1 : 0;
-    if (dt == VAMRT_F32)
-        unpad_kernel<float><<<grid, 256, 0, s>>>(p->scratch, (float *)dose, P.nx, P.ny, P.nz, P.px, P.py, accumulate);
-    else
-        unpad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p->scratch, (__nv_bfloat16 *)dose, P.nx, P.ny, P.nz, P.px,
-                                                         P.py, accumulate);
-    count_launches(1);
-    return cudaGetLastError();
+    return with_storage(vol_dt, p->scratch, [&](auto *vol) {
+        return with_storage(proj_dt, proj, [&](auto *pr) {
+            return launch_tiled<false>(P, (const std::remove_pointer_t<decltype(vol)> *)vol, pr, nullptr, flags, s);
+        });
+    });
 }
 
 cudaError_t launch_forward_acc(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, float *acc,
@@ -806,8 +798,15 @@ cudaError_t launch_forward_acc(const vamrt_projector *p, const void *proj, vamrt
 {
     const OpParams &P = p->op;
     const float *none = nullptr;
-    if (proj_dt == VAMRT_F32) return launch_tiled<true>(P, none, (float *)proj, acc, 0u, s);
-    return launch_tiled<true>(P, none, (__nv_bfloat16 *)proj, acc, 0u, s);
+    return with_storage(proj_dt, const_cast<void *>(proj),
+                        [&](auto *pr) { return launch_tiled<true>(P, none, pr, acc, 0u, s); });
+}
+
+cudaError_t launch_forward(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dt, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(p->scratch, 0, sizeof(float) * p->pad_elems, s);
+    if (e != cudaSuccess) return e;
+    return launch_forward_acc(p, proj, proj_dt, p->scratch, s);
 }
 
 cudaError_t launch_unpad_acc(const vamrt_projector *p, const float *acc, void *dose, vamrt_dtype dt, uint32_t flags,
@@ -816,13 +815,17 @@ cudaError_t launch_unpad_acc(const vamrt_projector *p, const float *acc, void *d
     const OpParams &P = p->op;
     const unsigned grid = grid_for(p, (int64_t)P.nx * P.ny * P.nz, 256);
     const int accumulate = (flags & VAMRT_ACCUMULATE) ? 1 : 0;
-    if (dt == VAMRT_F32)
-        unpad_kernel<float><<<grid, 256, 0, s>>>(acc, (float *)dose, P.nx, P.ny, P.nz, P.px, P.py, accumulate);
-    else
-        unpad_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(acc, (__nv_bfloat16 *)dose, P.nx, P.ny, P.nz, P.px, P.py,
-                                                         accumulate);
-    count_launches(1);
-    return cudaGetLastError();
+    return with_storage(dt, dose, [&](auto *d) {
+        using DT = std::remove_pointer_t<decltype(d)>;
+        unpad_kernel<DT><<<grid, 256, 0, s>>>(acc, d, P.nx, P.ny, P.nz, P.px, P.py, accumulate);
+        count_launches(1);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_unpad(const vamrt_projector *p, void *dose, vamrt_dtype dt, uint32_t flags, cudaStream_t s)
+{
+    return launch_unpad_acc(p, p->scratch, dose, dt, flags, s);
 }
 
 }  // namespace vamrt

@@ -6,6 +6,7 @@
 // per-block FP64 partial sums of |dn - f|; a single block adds the partials in a fixed
 // order, so the error E is deterministic.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 
@@ -16,6 +17,7 @@ constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ void st_dose(float *p, float x) { *p = x; }
 __device__ __forceinline__ void st_dose(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+__device__ __forceinline__ void st_dose(__half *p, float x) { *p = __float2half_rn(x); }
 
 template <typename T>
 __device__ T block_sum(T x, T *sh)
@@ -144,10 +146,13 @@ cudaError_t launch_osmo_step(const vamrt_projector *p, const float *target, floa
     if (dose_dt == VAMRT_F32)
         osmo_update_kernel<float><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model, (float *)dose,
                                                          nx, ny, nz, px, py, p->red, residual, alpha, mu, prev);
-    else
+    else if (dose_dt == VAMRT_BF16)
         osmo_update_kernel<__nv_bfloat16><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model,
                                                                  (__nv_bfloat16 *)dose, nx, ny, nz, px, py, p->red, residual, alpha,
                                                                  mu, prev);
+    else
+        osmo_update_kernel<__half><<<G, kRedThreads, 0, s>>>(p->scratch, p->dmax, target, model, (__half *)dose, nx,
+                                                          ny, nz, px, py, p->red, residual, alpha, mu, prev);
     finish_sum_kernel<<<1, kRedThreads, 0, s>>>(p->red, G, fsum, err_out);
     count_launches(3);
     return cudaGetLastError();

@@ -137,7 +137,7 @@ vamrt_status validate(const vamrt_geometry *g)
 
 vamrt_status check_dtype(vamrt_dtype d)
 {
-    if (d != VAMRT_F32 && d != VAMRT_BF16) return fail(VAMRT_EINVAL, "unknown dtype %d", (int)d);
+    if (d != VAMRT_F32 && d != VAMRT_BF16 && d != VAMRT_F16) return fail(VAMRT_EINVAL, "unknown dtype %d", (int)d);
     return VAMRT_OK;
 }
 

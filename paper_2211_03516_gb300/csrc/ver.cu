@@ -9,6 +9,7 @@
 // (in-part, out-of-part) give every threshold's mismatch count by prefix sums.  Resin =
 // voxel centres within r_inner of the axis (decided in FP64).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 
@@ -20,6 +21,7 @@ constexpr int kVerThreads = 256;
 
 __device__ __forceinline__ float ldd(const float *p) { return *p; }
 __device__ __forceinline__ float ldd(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ldd(const __half *p) { return __half2float(*p); }
 
 // maximum over the resin voxels (the same FP64 test as the histogram below)
 template <typename DT>
@@ -107,6 +109,10 @@ cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype d
                                                           p->dmax);
         ver_hist_kernel<float><<<g, kVerThreads, 0, s>>>((const float *)dose, target, nx, ny, nz, p->g.voxel_mm, r2,
                                                           p->dmax, hist);
+    } else if (dt == VAMRT_F16) {
+        dose_max_kernel<__half><<<g, kVerThreads, 0, s>>>((const __half *)dose, nx, ny, nz, p->g.voxel_mm, r2, p->dmax);
+        ver_hist_kernel<__half><<<g, kVerThreads, 0, s>>>((const __half *)dose, target, nx, ny, nz, p->g.voxel_mm, r2,
+                                                           p->dmax, hist);
     } else {
         dose_max_kernel<__nv_bfloat16><<<g, kVerThreads, 0, s>>>((const __nv_bfloat16 *)dose, nx, ny, nz,
                                                                   p->g.voxel_mm, r2, p->dmax);

@@ -20,12 +20,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvamrt.so")
 
 VAMRT_OK, VAMRT_EINVAL, VAMRT_EUNSUPPORTED, VAMRT_ECUDA, VAMRT_ENOMEM, VAMRT_NOT_CONVERGED, VAMRT_NUMERIC = range(7)
-VAMRT_F32, VAMRT_BF16 = 0, 1
+VAMRT_F32, VAMRT_BF16, VAMRT_F16 = 0, 1, 2
 VAMRT_ACCUMULATE, VAMRT_CLAMP_NONNEG, VAMRT_UNATTENUATED = 1, 2, 4
 VAMRT_APERTURE = {"list": 0, "chief": 1, "stratified": 2, "sunflower": 3, "hex13": 4}
 VAMRT_JITTER_PER_PIXEL = 1
 
-_DTYPES = {torch.float32: VAMRT_F32, torch.bfloat16: VAMRT_BF16}
+_DTYPES = {torch.float32: VAMRT_F32, torch.bfloat16: VAMRT_BF16, torch.float16: VAMRT_F16}
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
@@ -137,7 +137,7 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev_ptr(t: torch.Tensor, shape, name: str, dtypes=(torch.float32, torch.bfloat16)) -> int:
+def _dev_ptr(t: torch.Tensor, shape, name: str, dtypes=(torch.float32, torch.bfloat16, torch.float16)) -> int:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if tuple(t.shape) != tuple(shape):

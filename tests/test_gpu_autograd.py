@@ -65,6 +65,21 @@ def test_loss_kernel_matches_oracle(setup):
     assert rel_l2(grad.cpu().numpy(), g_ref) <= 1e-6
 
 
+def test_loss_kernel_fp16_storage(setup):
+    """Thresholded loss on an FP16-stored dose: the oracle on the same (FP16-rounded) dose
+    gives the same loss to 1e-6; a gradient written as FP16 carries one FP16 rounding
+    (unit roundoff 2^-11), held to 1e-3."""
+    s = setup
+    rng = np.random.default_rng(1)
+    D = (rng.random(s["w"].vol_shape) * 1.5).astype(np.float16)
+    L_ref, g_ref = OS.threshold_loss(D.astype(np.float64), s["f"], D_L, D_H)
+    loss, grad = s["P"].threshold_loss(torch.from_numpy(D).to(DEV), torch.from_numpy(s["f"]).to(DEV), D_L, D_H,
+                                       grad_dtype=torch.float16)
+    assert grad.dtype == torch.float16
+    assert abs(loss.item() - L_ref) <= 1e-6 * L_ref
+    assert rel_l2(grad.float().cpu().numpy(), g_ref) <= 1e-3
+
+
 def test_autograd_gradient_matches_oracle_fp32(setup):
     s = setup
     proj = torch.from_numpy(s["g"].astype(np.float32)).to(DEV).requires_grad_(True)

@@ -1,7 +1,9 @@
 """GPU parity of the CUDA operators (through the C ABI) against the FP64 oracle.
 
 Tolerance: 1e-5 relative L2 for the FP32 path; BF16 storage 2e-3 (dose) and 1e-3
-(projections / gradient), the bounds stated for the reduced-precision path.  Integer
+(projections / gradient), the bounds stated for the reduced-precision path; FP16 storage
+1e-3 (its unit roundoff is 2^-11 = 4.9e-4, so one rounding of each stored value stays
+within half the bound).  Integer
 results (sample counts, per-ray sample ranges) are compared exactly.
 """
 import math
@@ -19,6 +21,7 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 1e-5
 BF16_DOSE_TOL = 2e-3
 BF16_PROJ_TOL = 1e-3
+F16_TOL = 1e-3
 
 DEV = torch.device("cuda:0")
 
@@ -211,6 +214,49 @@ def test_bf16_storage_error_bounds(vamrt):
     assert rel_l2(d32.cpu().numpy(), d_ref) <= BF16_PROJ_TOL
 
 
+def test_f16_storage_error_bounds(vamrt):
+    """FP16 storage (IEEE binary16, sums in FP32): projections and dose written as FP16,
+    and FP32 results computed from FP16-stored inputs, all within 1e-3 of the FP64 oracle."""
+    w = MID_CROP
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    y_ref = O.adjoint(w, f, pupil)
+    d_ref = O.forward(w, y_ref, pupil)
+    assert max(np.abs(y_ref).max(), np.abs(d_ref).max()) < 6e4          # inside FP16's range
+    yh = P.adjoint(gpu(f, torch.float16), proj_dtype=torch.float16)
+    dh = P.forward_dose(gpu(y_ref, torch.float16), dose_dtype=torch.float16)
+    V = I.random_volume(w, seed=8)
+    grad32 = P.adjoint(gpu(V, torch.float16), proj_dtype=torch.float32)
+    d32 = P.forward_dose(gpu(y_ref, torch.float16), dose_dtype=torch.float32)
+    yh_from32 = P.adjoint(gpu(f), proj_dtype=torch.float16)
+    torch.cuda.synchronize()
+    assert yh.dtype == torch.float16 and dh.dtype == torch.float16
+    assert rel_l2(yh.float().cpu().numpy(), y_ref) <= F16_TOL
+    assert rel_l2(dh.float().cpu().numpy(), d_ref) <= F16_TOL
+    assert rel_l2(grad32.cpu().numpy(), O.adjoint(w, V, pupil)) <= F16_TOL
+    assert rel_l2(d32.cpu().numpy(), d_ref) <= F16_TOL
+    assert rel_l2(yh_from32.float().cpu().numpy(), y_ref) <= F16_TOL
+
+
+def test_optimizer_f16_storage_within_bound(vamrt):
+    """Projections and dose stored in FP16 (sums in FP32): the optimiser's iterates stay
+    within 1e-3 of the FP64 oracle's iteration over 10 iterations."""
+    w = I.TINY
+    pupil = I.workload_pupil(w)
+    P = vamrt.Projector.from_workload(w, pupil)
+    f = I.make_target(w)
+    res = P.optimize(gpu(f), max_iter=w.osmo_iters, tol=0.0, proj_dtype=torch.float16, dose_dtype=torch.float16)
+    g_ref, dn_ref, m_ref, e_ref, v_ref = OS.osmo(f, lambda m: O.adjoint(w, m, pupil),
+                                                 lambda g: O.forward(w, g, pupil), n_iter=w.osmo_iters, tol=0.0,
+                                                 resin=resin_mask(w))
+    assert res["proj"].dtype == torch.float16 and res["dose"].dtype == torch.float16
+    np.testing.assert_allclose(res["errors"], e_ref, rtol=F16_TOL)
+    assert rel_l2(res["proj"].float().cpu().numpy(), g_ref) <= F16_TOL
+    assert rel_l2(res["dose"].float().cpu().numpy(), dn_ref) <= F16_TOL
+    assert rel_l2(res["model"].cpu().numpy(), m_ref) <= F16_TOL
+
+
 def test_optimizer_matches_oracle_per_iteration(vamrt):
     w = I.TINY
     pupil = I.workload_pupil(w)
@@ -371,7 +417,7 @@ def test_voxel_error_rate_matches_oracle_exactly(vamrt):
     Z, Y, X = I.voxel_centres(w)
     resin = X ** 2 + Y ** 2 <= w.r_inner_mm ** 2
     res = P.optimize(gpu(f), max_iter=3, tol=0.0)
-    for dose in (res["dose"], res["dose"].to(torch.bfloat16)):
+    for dose in (res["dose"], res["dose"].to(torch.bfloat16), res["dose"].to(torch.float16)):
         ver, idx = P.voxel_error_rate(dose, gpu(f))
         ver_ref, idx_ref = OS.voxel_error_rate(dose.float().cpu().numpy(), f, resin)
         assert (ver, idx) == (ver_ref, idx_ref)
