@@ -680,9 +680,9 @@ def main():
                     help="heavy-ball momentum of the over-relaxed optimiser variant")
     ap.add_argument("--ttt-iters", type=int, default=30,
                     help="optimiser iterations of the time-to-target comparison (0 = skip)")
-    ap.add_argument("--ws-train", type=int, default=64, help="warm-start training targets (0 = skip)")
+    ap.add_argument("--ws-train", type=int, default=256, help="warm-start training targets (0 = skip)")
     ap.add_argument("--ws-epochs", type=int, default=8)
-    ap.add_argument("--ws-eval", type=int, default=4, help="held-out targets for the warm-start comparison")
+    ap.add_argument("--ws-eval", type=int, default=10, help="held-out targets for the warm-start comparison")
     ap.add_argument("--ws-loss-lr", type=float, default=0.8,
                     help="Adam step of the warm start's thresholded-loss continuation (x mean projection)")
     ap.add_argument("--ws-loss-dl", type=float, default=0.8,

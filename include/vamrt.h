@@ -220,7 +220,7 @@ vamrt_status vamrt_forward_dose(vamrt_projector *p, const void *proj, vamrt_dtyp
  *     address up again, which loads the array anew (16 MiB): make that call before any
  *     CUDA stream capture, or make a new projector first.
  *   - The current device must be the projector's device.
- * Errors: EINVAL (NULL, dtype, flags, grid too large, wrong device), ECUDA.
+ * Errors: EINVAL (NULL, dtype other than F32 / BF16, flags, grid too large, wrong device), ECUDA.
  */
 vamrt_status vamrt_forward_dose_static(const vamrt_projector *p, const void *proj, vamrt_dtype proj_dtype,
                                        void *dose, vamrt_dtype dose_dtype, uint32_t flags, void *stream);
