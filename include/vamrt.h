@@ -261,11 +261,13 @@ typedef struct {
     vamrt_dtype proj_dtype;    /* storage of g */
     vamrt_dtype dose_dtype;    /* storage of dn */
     int32_t timing;            /* nonzero: time each phase with CUDA events on `stream` */
-    int32_t mode;              /* VAMRT_OPT_OBJECT (the reading above) or VAMRT_OPT_PROJECTIONS */
-    double step;               /* object mode: beta in [0, 64] (0 = 1); projection mode: alpha in (0, 1] */
+    int32_t mode;              /* VAMRT_OPT_OBJECT (the reading above), VAMRT_OPT_PROJECTIONS or VAMRT_OPT_GRADIENT */
+    double step;               /* object mode: beta in [0, 64] (0 = 1); projection mode: alpha in (0, 1];
+                                  gradient mode: Adam step factor in (0, 16] (0 = 0.8) */
     double momentum;           /* object mode: mu in [0, 1) (0 = none) */
     float *prev_model;         /* device f32 [nz][ny][nx], required when momentum > 0; see above */
     int32_t stop;              /* VAMRT_STOP_VER (0) or VAMRT_STOP_ERROR */
+    double d_l, d_h;           /* gradient mode: the loss thresholds (both 0 = 0.8 and 1.0) */
 } vamrt_opt_params;
 
 #define VAMRT_STOP_VER 0
@@ -279,6 +281,19 @@ typedef struct {
  * (out = alpha (f - dn)). */
 #define VAMRT_OPT_OBJECT 0
 #define VAMRT_OPT_PROJECTIONS 1
+/* VAMRT_OPT_GRADIENT: the differentiable path (not in the paper) -- projected Adam steps
+ * on the thresholded dose loss of vamrt_threshold_loss, starting from proj (in = g0 >= 0,
+ * e.g. a learned warm start; proj_dtype F32 or BF16, else EUNSUPPORTED).  g0 is first
+ * scaled so that the part's mean dose is 1 (the thresholds' scale), then per iteration
+ *   D = A g (stored in dose_dtype);  L, dL/dD (FP32, in the model buffer: volume workspace);
+ *   grad = A^T dL/dD;  Adam step on an FP32 master copy of g (step size params.step x the
+ *   mean positive projection after scaling, 0 = 0.8; moments 0.9 / 0.999), g >= 0;
+ * E = L; V = the voxel error rate of D, each read every check_every iterations and
+ * compared with tol as above.  Out: proj = g after the last step, dose = D of the last
+ * iteration (before its step).  Allocates its FP32 state (3 or 4 projection-sized arrays)
+ * for the call.  adjoint_ms times the gradient's projection, forward_ms the doses (and the
+ * scaling), update_ms the loss and the Adam steps. */
+#define VAMRT_OPT_GRADIENT 2
 
 typedef struct {
     int32_t iterations;        /* iterations run */

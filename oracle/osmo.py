@@ -113,6 +113,36 @@ def osmo_projections(target, g0, project, dose, n_iter, alpha=1.0, resin=None):
     return g, dn, np.array(errors)
 
 
+def threshold_adam(target, g0, project, dose, n_iter, step=0.8, d_l=0.8, d_h=1.0, b1=0.9, b2=0.999, eps=1e-12):
+    """Adjoint-driven continuation from g0 >= 0 (reading; not in the paper): projected
+    Adam steps on the thresholded dose loss, the gradient coming from the projection.
+      g = g0 / mean_{v in P}(A g0)        the part's mean dose becomes 1 (the thresholds' scale)
+      lr = step * mean_{g > 0}(g)
+      iteration k = 1, 2, ...:
+        D = A g;  L, G = threshold_loss(D);  grad = P G          P: projection (adjoint)
+        m <- b1 m + (1 - b1) grad;  v <- b2 v + (1 - b2) grad^2
+        g <- max(0, g - lr (m / (1 - b1^k)) / (sqrt(v / (1 - b2^k)) + eps))
+    (Adam, Kingma and Ba: first-order steps scaled by bias-corrected moment estimates.)
+    Returns (g after the last step, D of the last iteration, losses L per iteration)."""
+    f = np.asarray(target, dtype=np.float64)
+    g = np.asarray(g0, dtype=np.float64).copy()
+    D = dose(g)
+    g = g / D[f > 0.5].mean()
+    lr = step * g[g > 0.0].mean()
+    m = np.zeros_like(g)
+    v = np.zeros_like(g)
+    losses = []
+    for k in range(1, n_iter + 1):
+        D = dose(g)
+        L, G = threshold_loss(D, f, d_l, d_h)
+        losses.append(L)
+        grad = project(G)
+        m = b1 * m + (1.0 - b1) * grad
+        v = b2 * v + (1.0 - b2) * grad * grad
+        g = np.maximum(0.0, g - lr * (m / (1.0 - b1 ** k)) / (np.sqrt(v / (1.0 - b2 ** k)) + eps))
+    return g, D, np.array(losses)
+
+
 def export_u8(proj):
     """8-bit export (Sec. 2.7, reading: upper clip at mean + 3 sigma, projections >= 0):
     codes = round-half-even(255 min(max(g, 0), c) / c), c = mean + 3 sigma (population)."""

@@ -119,6 +119,14 @@ cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, va
                                   const float *target, float d_l, float d_h, double *loss3, void *grad,
                                   vamrt_dtype grad_dt, cudaStream_t s);
 
+// loss.cu: out2 = device {count, sum} of x over target > 1/2 (target given) or over x > 0
+// (target NULL), summed in a fixed order
+cudaError_t launch_masked_sum(const vamrt_projector *p, const void *x, vamrt_dtype dt, const float *target,
+                              int64_t n, double *out2, cudaStream_t s);
+// loss.cu: master = sc * x in FP32; x (in dt) rewritten from master when it is not master itself
+cudaError_t launch_scale_master(const vamrt_projector *p, void *x, vamrt_dtype dt, float *master, int64_t n, float sc,
+                                cudaStream_t s);
+
 // ver.cu: out3 = device {best mismatch count, best threshold index, resin voxels}
 cudaError_t launch_ver(const vamrt_projector *p, const void *dose, vamrt_dtype dt, const float *target,
                        long long *out3, cudaStream_t s);

@@ -129,4 +129,95 @@ cudaError_t launch_threshold_loss(const vamrt_projector *p, const void *dose, va
     return launch_loss_t(p, (const __half *)dose, target, d_l, d_h, loss3, grad, grad_dt, s);
 }
 
+// ---- the gradient optimiser's normalisations ------------------------------------------
+namespace {
+
+// partials[2 b + {0, 1}] = (count, sum) of x over the elements selected by target > 1/2
+// (target given) or by x > 0 (target NULL)
+template <typename T>
+__global__ void masked_sum_kernel(const T *__restrict__ x, const float *__restrict__ target, int64_t n,
+                                  double *__restrict__ partials)
+{
+    __shared__ double sh[kLossThreads / 32];
+    double c = 0.0, t = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float xi = ldv(x + i);
+        if (target ? target[i] > 0.5f : xi > 0.f) {
+            c += 1.0;
+            t += (double)xi;
+        }
+    }
+    const double a = block_sum_d(c, sh), b = block_sum_d(t, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// out[0] = count, out[1] = sum, added in a fixed order
+__global__ void masked_sum_finish_kernel(const double *__restrict__ partials, int nb, double *__restrict__ out)
+{
+    __shared__ double sh[kLossThreads / 32];
+    double c = 0.0, t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        c += partials[2 * b];
+        t += partials[2 * b + 1];
+    }
+    const double a = block_sum_d(c, sh), b = block_sum_d(t, sh);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+// master = s x (FP32), and the storage copy of it when x is not the master itself
+template <typename T>
+__global__ void scale_master_kernel(T *__restrict__ x, float *__restrict__ master, int64_t n, float s)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float m = s * ldv(x + i);
+        master[i] = m;
+        if ((void *)x != (void *)master) stv(x + i, m);
+    }
+}
+
+template <typename T>
+cudaError_t masked_sum_t(const vamrt_projector *p, const T *x, const float *target, int64_t n, double *out2,
+                         cudaStream_t s)
+{
+    int64_t nb = (n + kLossThreads - 1) / kLossThreads;
+    if (nb > kRedBlocks / 2) nb = kRedBlocks / 2;
+    if (nb < 1) nb = 1;
+    masked_sum_kernel<T><<<(unsigned)nb, kLossThreads, 0, s>>>(x, target, n, p->red);
+    masked_sum_finish_kernel<<<1, kLossThreads, 0, s>>>(p->red, (int)nb, out2);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_masked_sum(const vamrt_projector *p, const void *x, vamrt_dtype dt, const float *target,
+                              int64_t n, double *out2, cudaStream_t s)
+{
+    if (dt == VAMRT_F32) return masked_sum_t(p, (const float *)x, target, n, out2, s);
+    if (dt == VAMRT_BF16) return masked_sum_t(p, (const __nv_bfloat16 *)x, target, n, out2, s);
+    return masked_sum_t(p, (const __half *)x, target, n, out2, s);
+}
+
+cudaError_t launch_scale_master(const vamrt_projector *p, void *x, vamrt_dtype dt, float *master, int64_t n, float sc,
+                                cudaStream_t s)
+{
+    unsigned g = (unsigned)((n + kLossThreads - 1) / kLossThreads);
+    if (g > (unsigned)p->num_sms * 16u) g = (unsigned)p->num_sms * 16u;
+    if (g < 1) g = 1;
+    if (dt == VAMRT_F32)
+        scale_master_kernel<float><<<g, kLossThreads, 0, s>>>((float *)x, master, n, sc);
+    else if (dt == VAMRT_BF16)
+        scale_master_kernel<__nv_bfloat16><<<g, kLossThreads, 0, s>>>((__nv_bfloat16 *)x, master, n, sc);
+    else
+        scale_master_kernel<__half><<<g, kLossThreads, 0, s>>>((__half *)x, master, n, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace vamrt

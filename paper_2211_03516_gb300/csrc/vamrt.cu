@@ -364,6 +364,152 @@ vamrt_status vamrt_forward_dose(vamrt_projector *p, const void *proj, vamrt_dtyp
     return VAMRT_OK;
 }
 
+namespace {
+
+// VAMRT_OPT_GRADIENT: projected Adam steps on the thresholded dose loss, the gradient
+// A^T dL/dD from the projection operator (the differentiable path), from the caller's
+// starting projections.  Validation common to all modes is done by the caller.
+vamrt_status optimize_gradient(vamrt_projector *p, const float *target, float *model, void *proj, void *dose,
+                               const vamrt_opt_params *params, vamrt_opt_report *report, cudaStream_t s)
+{
+    const vamrt_dtype pdt = params->proj_dtype, ddt = params->dose_dtype;
+    if (pdt == VAMRT_F16) return fail(VAMRT_EUNSUPPORTED, "gradient mode stores projections as F32 or BF16");
+    if (params->momentum != 0.0) return fail(VAMRT_EINVAL, "momentum is not used in gradient mode");
+    const bool dflt = params->d_l == 0.0 && params->d_h == 0.0;
+    const double d_l = dflt ? 0.8 : params->d_l, d_h = dflt ? 1.0 : params->d_h;
+    if (!(d_l >= 0.0 && d_h > d_l)) return fail(VAMRT_EINVAL, "thresholds must satisfy 0 <= d_l < d_h");
+    const double step = params->step == 0.0 ? 0.8 : params->step;
+    if (!(step > 0.0 && step <= 16.0)) return fail(VAMRT_EINVAL, "gradient-mode step must be in (0, 16] (0 = 0.8)");
+    const vamrt_geometry &g = p->g;
+    const int64_t n = (int64_t)g.n_angles * g.nv * g.nu;
+    const int64_t nvox = (int64_t)g.nx * g.ny * g.nz;
+
+    // FP32 state for this call: Adam moments, the projection gradient and (BF16 storage)
+    // the master projections
+    float *state = nullptr;
+    const int64_t n_state = (pdt == VAMRT_F32 ? 3 : 4) * n;
+    if (cudaMalloc(&state, sizeof(float) * n_state) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VAMRT_ENOMEM, "gradient mode: %lld bytes of optimiser state", (long long)(sizeof(float) * n_state));
+    }
+    struct Free {
+        float *q;
+        ~Free() { cudaFree(q); }
+    } free_state{state};
+    float *mom1 = state, *mom2 = state + n, *gradp = state + 2 * n;
+    float *master = pdt == VAMRT_F32 ? (float *)proj : state + 3 * n;
+    CK(cudaMemsetAsync(mom1, 0, sizeof(float) * 2 * n, s), "cudaMemsetAsync");
+
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() { for (int i = 0; i < 5; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+    } evguard{ev};
+    if (params->timing)
+        for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]), "cudaEventCreate");
+    double *sc2 = p->red + vamrt::kRedBlocks + 1;     // {count, sum}
+    double *loss3 = p->red + vamrt::kRedBlocks + 1;   // {L, 1/|P|, 1/|Q|}
+    long long *ver3 = reinterpret_cast<long long *>(p->red + vamrt::kRedBlocks + 5);
+    struct Checked {
+        double err;
+        long long ver3[3];
+    };
+    Checked *host = reinterpret_cast<Checked *>(p->host_err);
+    double t_adj = 0.0, t_fwd = 0.0, t_upd = 0.0;
+    if (params->timing) CK(cudaEventRecord(ev[0], s), "cudaEventRecord");
+
+    // scale the start so that the part's mean dose is 1 (the thresholds' scale)
+    CK(vamrt::launch_forward(p, proj, pdt, s), "forward kernel");
+    CK(vamrt::launch_unpad(p, dose, ddt, 0u, s), "unpad kernel");
+    CK(vamrt::launch_masked_sum(p, dose, ddt, target, nvox, sc2, s), "masked sum");
+    double cnt[2];
+    CK(cudaMemcpyAsync(cnt, sc2, sizeof(cnt), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (!(cnt[0] > 0.0)) return fail(VAMRT_EINVAL, "gradient mode: the target has no part voxels");
+    if (!(cnt[1] > 0.0) || !isfinite(cnt[1]))
+        return fail(VAMRT_NUMERIC, "gradient mode: the starting projections give the part no dose");
+    CK(vamrt::launch_scale_master(p, proj, pdt, master, n, (float)(cnt[0] / cnt[1]), s), "scale kernel");
+    // Adam step: `step` times the mean positive projection
+    CK(vamrt::launch_masked_sum(p, master, VAMRT_F32, nullptr, n, sc2, s), "masked sum");
+    CK(cudaMemcpyAsync(cnt, sc2, sizeof(cnt), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (!(cnt[0] > 0.0)) return fail(VAMRT_NUMERIC, "gradient mode: no positive starting projection");
+    const float lr = (float)(step * cnt[1] / cnt[0]);
+    if (params->timing) {
+        CK(cudaEventRecord(ev[1], s), "cudaEventRecord");
+        CK(cudaEventSynchronize(ev[1]), "cudaEventSynchronize");
+        float ms;
+        CK(cudaEventElapsedTime(&ms, ev[0], ev[1]), "cudaEventElapsedTime");
+        t_fwd += ms;
+    }
+
+    int it = 0;
+    double err = NAN, ver = NAN;
+    bool converged = false;
+    std::vector<double> vers((size_t)params->max_iter, NAN);
+    for (; it < params->max_iter;) {
+        if (params->timing) CK(cudaEventRecord(ev[0], s), "cudaEventRecord");
+        // D = A g (stored in dose_dtype); L and dL/dD (FP32, in the model buffer)
+        CK(vamrt::launch_forward(p, proj, pdt, s), "forward kernel");
+        CK(vamrt::launch_unpad(p, dose, ddt, 0u, s), "unpad kernel");
+        if (params->timing) CK(cudaEventRecord(ev[1], s), "cudaEventRecord");
+        CK(vamrt::launch_threshold_loss(p, dose, ddt, target, (float)d_l, (float)d_h, loss3, model, VAMRT_F32, s),
+           "threshold loss");
+        CK(cudaMemcpyAsync(p->hist + it, loss3, sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        if (params->timing) CK(cudaEventRecord(ev[2], s), "cudaEventRecord");
+        // the projections' gradient A^T dL/dD
+        CK(vamrt::launch_pad(p, model, VAMRT_F32, s), "pad kernel");
+        CK(vamrt::launch_adjoint(p, VAMRT_F32, gradp, VAMRT_F32, 0u, s), "adjoint kernel");
+        if (params->timing) CK(cudaEventRecord(ev[3], s), "cudaEventRecord");
+        // projected Adam step on the FP32 master (g >= 0), storage copy refreshed
+        CK(vamrt::nn_adam(master, gradp, mom1, mom2, pdt == VAMRT_BF16 ? proj : nullptr, n, lr, 0.9f, 0.999f, 1e-12f,
+                          it + 1, true, s),
+           "adam kernel");
+        if (params->timing) {
+            CK(cudaEventRecord(ev[4], s), "cudaEventRecord");
+            CK(cudaEventSynchronize(ev[4]), "cudaEventSynchronize");
+            float ms[4];
+            for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]), "cudaEventElapsedTime");
+            t_fwd += ms[0];
+            t_upd += ms[1] + ms[3];
+            t_adj += ms[2];
+        }
+        ++it;
+        if (it % params->check_every == 0 || it == params->max_iter) {
+            // the voxel error rate of this iteration's dose (before its Adam step), and L
+            CK(vamrt::launch_ver(p, dose, ddt, target, ver3, s), "voxel error rate kernels");
+            CK(cudaMemcpyAsync(&host->err, p->hist + it - 1, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaMemcpyAsync(host->ver3, ver3, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+            err = host->err;
+            ver = host->ver3[2] > 0 ? (double)host->ver3[0] / (double)host->ver3[2] : 0.0;
+            vers[it - 1] = ver;
+            if (!isfinite(err)) {
+                if (report) { report->iterations = it; report->final_error = err; report->final_ver = ver; }
+                return fail(VAMRT_NUMERIC, "loss is not finite at iteration %d", it);
+            }
+            if ((params->stop == VAMRT_STOP_VER ? ver : err) < params->tol) { converged = true; break; }
+        }
+    }
+    if (report) {
+        report->iterations = it;
+        report->final_error = err;
+        report->adjoint_ms = t_adj;
+        report->forward_ms = t_fwd;
+        report->update_ms = t_upd;
+        report->final_ver = ver;
+        if (report->ver_history)
+            for (int i = 0; i < it; ++i) report->ver_history[i] = vers[(size_t)i];
+        if (report->error_history) {
+            CK(cudaMemcpyAsync(report->error_history, p->hist, sizeof(double) * it, cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+        }
+    }
+    return converged ? VAMRT_OK : VAMRT_NOT_CONVERGED;
+}
+
+}  // namespace
+
 vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *model, void *proj, void *dose,
                             const vamrt_opt_params *params, vamrt_opt_report *report, void *stream)
 {
@@ -373,8 +519,12 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
     if (params->check_every < 1) return fail(VAMRT_EINVAL, "check_every must be >= 1");
     if (!(params->tol >= 0.0)) return fail(VAMRT_EINVAL, "tol must be >= 0");
     if (check_dtype(params->proj_dtype) || check_dtype(params->dose_dtype)) return VAMRT_EINVAL;
-    if (params->mode != VAMRT_OPT_OBJECT && params->mode != VAMRT_OPT_PROJECTIONS)
+    if (params->mode != VAMRT_OPT_OBJECT && params->mode != VAMRT_OPT_PROJECTIONS && params->mode != VAMRT_OPT_GRADIENT)
         return fail(VAMRT_EINVAL, "unknown optimiser mode %d", params->mode);
+    if (params->stop != VAMRT_STOP_VER && params->stop != VAMRT_STOP_ERROR)
+        return fail(VAMRT_EINVAL, "unknown stop criterion %d", params->stop);
+    if (params->mode == VAMRT_OPT_GRADIENT)
+        return optimize_gradient(p, target, model, proj, dose, params, report, (cudaStream_t)stream);
     if (params->mode == VAMRT_OPT_PROJECTIONS && !(params->step > 0.0 && params->step <= 1.0))
         return fail(VAMRT_EINVAL, "projection-space step must be in (0, 1]");
     if (params->mode == VAMRT_OPT_OBJECT && !(params->step >= 0.0 && params->step <= 64.0))
@@ -385,8 +535,6 @@ vamrt_status vamrt_optimize(vamrt_projector *p, const float *target, float *mode
         return fail(VAMRT_EINVAL, "momentum must be in [0, 1)");
     if (params->momentum != 0.0 && (params->mode != VAMRT_OPT_OBJECT || !params->prev_model))
         return fail(VAMRT_EINVAL, "momentum needs object mode and a prev_model buffer");
-    if (params->stop != VAMRT_STOP_VER && params->stop != VAMRT_STOP_ERROR)
-        return fail(VAMRT_EINVAL, "unknown stop criterion %d", params->stop);
     cudaStream_t s = (cudaStream_t)stream;
     double *fsum = p->red + vamrt::kRedBlocks;
     // phase timing: events ev[0..3] bracket adjoint | forward | update of one iteration

@@ -68,7 +68,8 @@ class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("check_every", ctypes.c_int32),
                 ("proj_dtype", ctypes.c_int), ("dose_dtype", ctypes.c_int), ("timing", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("step", ctypes.c_double), ("momentum", ctypes.c_double),
-                ("prev_model", ctypes.c_void_p), ("stop", ctypes.c_int32)]
+                ("prev_model", ctypes.c_void_p), ("stop", ctypes.c_int32), ("d_l", ctypes.c_double),
+                ("d_h", ctypes.c_double)]
 
 
 class OptReport(ctypes.Structure):
@@ -340,20 +341,24 @@ class Projector:
     def optimize(self, target: torch.Tensor, model: Optional[torch.Tensor] = None, max_iter=10, tol=0.005,
                  check_every=1, proj_dtype=torch.float32, dose_dtype=torch.float32, proj=None, dose=None,
                  timing=False, mode="object", step=1.0, momentum=0.0, prev_model=None, stop="ver",
-                 stream=None) -> dict:
+                 d_l=0.0, d_h=0.0, stream=None) -> dict:
         """Projection optimisation (vamrt_optimize).  Returns g, dn, model, errors, converged.
         mode "object": OSMO on the model (model in = m0, default the target), model step
         `step` (1 = the plain update) and heavy-ball `momentum` (0 = none), whose previous
         model lives in prev_model (in: the model before m0 -- a copy of m0 to start at rest,
         made here when prev_model is None; out: updated; pass the same buffer back to keep
         momentum across calls);
-        mode "projections": iterate on proj (in = g0, required), model = workspace.
+        mode "projections": iterate on proj (in = g0, required), model = workspace;
+        mode "gradient": projected Adam steps on the thresholded dose loss (thresholds d_l,
+        d_h; both 0 = 0.8, 1.0) from proj (in = g0, required; Adam step `step` x the mean
+        projection, 0 = 0.8), model = volume workspace, `errors` = the loss per iteration.
         stop: "ver" (the voxel error rate V < tol, the reading of Sec. 2.7's stop) or
-        "error" (the dose's L1 error E < tol); `vers` holds V of the checked iterations."""
-        if mode not in ("object", "projections"):
-            raise ValueError("mode must be 'object' or 'projections'")
-        if mode == "projections" and proj is None:
-            raise ValueError("projection mode needs the starting projections in proj")
+        "error" (E < tol); `vers` holds V of the checked iterations."""
+        modes = {"object": 0, "projections": 1, "gradient": 2}
+        if mode not in modes:
+            raise ValueError("mode must be 'object', 'projections' or 'gradient'")
+        if mode != "object" and proj is None:
+            raise ValueError(f"{mode} mode needs the starting projections in proj")
         if model is None:
             model = target.clone() if mode == "object" else torch.empty_like(target)
         if momentum and prev_model is None:
@@ -369,8 +374,8 @@ class Projector:
         dp = _dev_ptr(dose, self.vol_shape, "dose")
         params = OptParams(max_iter=max_iter, tol=tol, check_every=check_every, proj_dtype=_DTYPES[proj.dtype],
                            dose_dtype=_DTYPES[dose.dtype], timing=1 if timing else 0,
-                           mode=0 if mode == "object" else 1, step=float(step), momentum=float(momentum),
-                           prev_model=pm, stop={"ver": 0, "error": 1}[stop])
+                           mode=modes[mode], step=float(step), momentum=float(momentum),
+                           prev_model=pm, stop={"ver": 0, "error": 1}[stop], d_l=float(d_l), d_h=float(d_h))
         hist = np.zeros(max_iter, dtype=np.float64)
         vhist = np.full(max_iter, np.nan)
         rep = OptReport(iterations=0, final_error=math.nan, error_history=hist.ctypes.data_as(_dp),

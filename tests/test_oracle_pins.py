@@ -545,6 +545,33 @@ def test_osmo_projections_closed_form():
     np.testing.assert_array_equal(err, [0.0, 0.0, 0.0])
 
 
+def test_threshold_adam_by_hand():
+    """Thresholded-loss Adam continuation on the toy printer B = [[2, 1], [1, 1]] (dose B g,
+    projection B^T x), f = (1, 0), g0 = (1, 1), d_l = 1/2, d_h = 1, step 0.8:
+    A g0 = (3, 2), the part's mean dose 3, so g = (1/3, 1/3) and lr = 0.8 / 3 = 4/15.
+    Iteration 1: D = (1, 2/3); only the void voxel is over d_l: L = (1/6)^2 = 1/36,
+    dL/dD = (0, 1/3), grad = B^T (0, 1/3) = (1/3, 1/3).  Adam's first bias-corrected step is
+    lr sign(grad) (m^ = grad, v^ = grad^2), so g1 = (1/3 - 4/15, ...) = (1/15, 1/15).
+    Iteration 2: D = (1/5, 2/15); now the part is under-dosed: L = (4/5)^2 = 16/25,
+    grad = B^T (-8/5, 0) = (-16/5, -8/5); m = (-0.29, -0.13), v = (0.010351, 0.002671),
+    bias corrections 0.19 and 0.001999: g2 = 1/15 + (4/15)(0.670748..., 0.591916...)
+    = (0.2455329..., 0.2245106...)."""
+    B = np.array([[2.0, 1.0], [1.0, 1.0]])
+    project, dose = (lambda x: B.T @ x), (lambda y: B @ y)
+    f = np.array([1.0, 0.0])
+    g, D, L = OS.threshold_adam(f, np.array([1.0, 1.0]), project, dose, n_iter=1, step=0.8, d_l=0.5, d_h=1.0)
+    np.testing.assert_allclose(L, [1.0 / 36.0], rtol=1e-14)
+    np.testing.assert_allclose(D, [1.0, 2.0 / 3.0], rtol=1e-15)
+    np.testing.assert_allclose(g, [1.0 / 15.0, 1.0 / 15.0], rtol=1e-10)
+    g, D, L = OS.threshold_adam(f, np.array([1.0, 1.0]), project, dose, n_iter=2, step=0.8, d_l=0.5, d_h=1.0)
+    np.testing.assert_allclose(L, [1.0 / 36.0, 16.0 / 25.0], rtol=1e-9)
+    np.testing.assert_allclose(D, [0.2, 2.0 / 15.0], rtol=1e-9)
+    np.testing.assert_allclose(g, [0.24553290433, 0.22451061528], rtol=1e-9)
+    # the projection bound: a step that would go below zero stops at zero
+    g, _, _ = OS.threshold_adam(f, np.array([1.0, 1.0]), project, dose, n_iter=1, step=3.0, d_l=0.5, d_h=1.0)
+    np.testing.assert_array_equal(g, [0.0, 0.0])
+
+
 def test_osmo_stops_on_the_voxel_error_rate():
     """The stop reads Sec. 2.7's 'absolute relative error below 0.5 %' as the voxel error
     rate V of the normalised dose: the loop ends after the first iteration whose V is below
