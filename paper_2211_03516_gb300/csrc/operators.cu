@@ -476,7 +476,7 @@ __device__ __forceinline__ void walk_scatter_box(const Ray &R, const Anchor &an,
     const float inv_ratio = exp2f(-R.att);
     const f32x2 conv = kNonNeg ? pk2(0x1p-149f, 0x1p-149f) : pk2(12582912.0f, 12582912.0f);
     const int bias = kNonNeg ? 0 : 0x4B400000;
-#pragma unroll 2
+#pragma unroll 8
     for (int j = jh - 1; j >= jl; --j) {
         const float fx = frac23(qx), fy = frac23(qy), fz = frac23(qz);
         int *p = box + ((qz >> 23) * sxy + (qy >> 23) * sx + (qx >> 23));
