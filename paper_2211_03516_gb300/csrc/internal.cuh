@@ -22,7 +22,7 @@ constexpr int kTileU = 8;
 constexpr int kTileV = 32;
 constexpr int kThreads = kTileU * kTileV;
 constexpr int kChunkVox = 20;
-constexpr int kBoxFloats = 18944;     // 74 KB: three blocks and their static shared memory fit an SM
+constexpr int kBoxFloats = 18 * 1024;
 constexpr int kBlocksPerSm = 3;
 
 // Per-launch constants of the two operators.  Positions are in padded index
