@@ -114,6 +114,31 @@ def reduce_max(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def load_traffic() -> dict:
+    """Per-launch DRAM and L2 bytes of the operators from ncu captures (profiles/traffic.json):
+    '<workload>:<kernel>' = dram__bytes_read + write, '<workload>:<kernel>:l2' =
+    lts__t_bytes, each scaled to a full launch by the samples processed."""
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tf) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def l2_report(traffic: dict, workload: str, kernel: str, ms: float, l2_read_bps: float):
+    """Achieved L2 throughput of one operator launch: its captured L2 bytes over the
+    launch's CUDA-event time, against the L2 read bandwidth measured in the same run;
+    None when no capture of this workload and kernel exists."""
+    b = traffic.get(f"{workload}:{kernel}:l2")
+    if not b or not ms > 0 or not l2_read_bps > 0:
+        return None
+    gbps = b / (ms / 1e3) / 1e9
+    return {"bytes_per_launch": b, "achieved_GBps": gbps, "peak_GBps": l2_read_bps / 1e9,
+            "frac": gbps * 1e9 / l2_read_bps,
+            "source": "ncu lts__t_bytes.sum of a crop capture scaled by samples (profiles/)"}
+
+
 def cpu_threads() -> int:
     """Host cores the oracle sample runs on: one worker process per core."""
     return os.cpu_count() or 1
@@ -547,13 +572,9 @@ def run_gpu(args, rank, world):
     # compulsory DRAM bytes of one launch: volume in + projections out (adjoint) or
     # projections in + dose accumulator out (forward), plus the ray table once per angle
     compulsory = vol_b + proj_b + 72 * n_rays * w.n_angles
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        try:
-            traffic = json.load(open(tf)).get(f"{w.name}:{dom}")
-        except Exception:
-            traffic = None
+    traffic_all = load_traffic()
+    traffic = traffic_all.get(f"{w.name}:{dom}")
+    l2 = l2_report(traffic_all, w.name, dom, dom_ms, l2_read_bps)
 
     # ---- the tall build (384 x 384 x 512, 720 angles, 8 rays) with BF16-stored projections
     # and dose, beside the headline: one timed optimiser iteration after one warm-up ----
@@ -637,6 +658,7 @@ def run_gpu(args, rank, world):
                      "peak_kind": "measured in this run (vamrt_measure_smem_bandwidth)",
                      "bytes_per_sample": BYTES_PER_SAMPLE,
                      "l2_measured": {"read_GBps": l2_read_bps / 1e9, "red_v4_ops_per_s": l2_red_ops},
+                     "l2": l2,
                      "per_kernel": kern,
                      "forward_sample_fraction": fwd_spp / spp,
                      "hbm": {"compulsory_bytes": compulsory, "achieved": compulsory / (dom_ms / 1e3) / 1e9,
