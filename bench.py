@@ -572,7 +572,8 @@ def run_gpu(args, rank, world):
     # compulsory DRAM bytes of one launch: volume in + projections out (adjoint) or
     # projections in + dose accumulator out (forward), plus the ray table once per angle
     compulsory = vol_b + proj_b + 72 * n_rays * w.n_angles
-    traffic_all = load_traffic()
+    # captured counters describe the full workload: none for a reduced (profiling) case
+    traffic_all = {} if (args.angles or args.nz or args.nv) else load_traffic()
     traffic = traffic_all.get(f"{w.name}:{dom}")
     l2 = l2_report(traffic_all, w.name, dom, dom_ms, l2_read_bps)
 
